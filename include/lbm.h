@@ -1,0 +1,163 @@
+/*
+ * lbm.h -- C ABI of the GB300 (sm_103a) D3Q27 central-moment MRT kinetic solver with
+ * direct-forcing immersed boundaries (arXiv 2101.11856, "GPU Optimization for
+ * High-Quality Kinetic Fluid Simulation").
+ *
+ * One context = one simulation on one GPU and one CUDA stream.  The library owns every
+ * device buffer it allocates (populations, immersed-boundary data, scratch); callers
+ * own the arrays they pass in and out.  Array arguments may be host or device pointers
+ * (the library checks with cudaPointerGetAttributes) and are never retained after the
+ * call returns.  Calls on one context are not thread-safe.
+ *
+ * Lattice units throughout: dx = dt = 1, c_s^2 = 1/3.  Fields are stored x-fastest:
+ * cell (x, y, z) has flat index x + nx * (y + ny * z).  Vector fields are
+ * structure-of-arrays: u[0..N) = u_x, u[N..2N) = u_y, u[2N..3N) = u_z.
+ *
+ * Every function returns LBM_OK (0) or a negative error code; lbm_last_error() gives
+ * a message for the last failure on a context.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes --------------------------------------------------------------- */
+#define LBM_OK         0
+#define LBM_EINVAL    -1   /* bad argument: dims < 2, nu <= 0, non-finite or out-of-domain samples, ... */
+#define LBM_ENOMEM    -2   /* a device or host allocation failed                                      */
+#define LBM_ECUDA     -3   /* a CUDA runtime call failed                                              */
+#define LBM_EUNSTABLE -4   /* non-finite density or velocity detected by lbm_check                   */
+#define LBM_ETIMEOUT  -5   /* a host-side wait exceeded its wall-clock limit                         */
+#define LBM_ESTATE    -6   /* called in the wrong state (e.g. step before set_state)                 */
+
+/* ---- population storage ---------------------------------------------------------- */
+#define LBM_STORE_F32  0   /* deviations f_i - w_i rho0 stored as float     (216 B per cell update) */
+#define LBM_STORE_F16  1   /* deviations stored as IEEE half, math in FP32   (108 B per cell update) */
+#define LBM_STORE_BF16 2   /* deviations stored as bfloat16, math in FP32    (108 B per cell update) */
+
+/* ---- domain faces (order -x, +x, -y, +y, -z, +z) --------------------------------- */
+#define LBM_FACE_PERIODIC 0  /* both faces of an axis must be periodic together            */
+#define LBM_FACE_NOSLIP   1  /* half-way bounce-back (the paper's Algorithm 1)             */
+#define LBM_FACE_INLET    2  /* -x only: moving-wall bounce-back at u_in(y, z, t)          */
+#define LBM_FACE_OUTLET   3  /* +x only: zero-gradient ghost layer                         */
+
+typedef struct lbm_ctx lbm_ctx;
+
+typedef struct lbm_config {
+    int storage;                 /* LBM_STORE_*                                                */
+    int face_type[6];            /* LBM_FACE_* for -x, +x, -y, +y, -z, +z                      */
+    double rho0;                 /* reference density of the deviation storage and the inlet  */
+    double u_in;                 /* inlet base velocity (x component)                          */
+    double inlet_noise;          /* relative amplitude of the seeded uniform inlet noise       */
+    unsigned long long seed;     /* SplitMix64 seed of the inlet noise                         */
+    double inflow_coef[16];      /* a_mn, m, n = 1..4 (row-major in m) of the inflow profile   */
+    double omega_bulk;           /* rate of the trace of the second-order central moments     */
+    double omega_hi[4];          /* rates of the third-, fourth-, fifth-, sixth-order moments */
+    void *cuda_stream;           /* cudaStream_t the context launches on (NULL = legacy)       */
+} lbm_config;
+
+/* Fill *cfg with defaults: FP32 storage, all faces periodic, rho0 = 1, no inlet, no noise,
+ * seed 2101, zero inflow coefficients, omega_bulk = omega_hi[*] = 1, default stream. */
+void lbm_config_default(lbm_config *cfg);
+
+/* Create a solver on an nx * ny * nz D3Q27 lattice (Eq. 1) with kinematic viscosity nu
+ * (shear rate omega_s = 1 / (3 nu + 1/2), the low-order rate set by nu in Eq. 5) and the
+ * uniform body force forcing[3] (Guo-style force term G of Eq. 4; NULL = no force).
+ * cfg = NULL takes lbm_config_default.  Allocates the population array (27 planes of
+ * nx*ny*nz values of the storage type, AA in-place layout) on the current CUDA device.
+ * Errors: LBM_EINVAL (dims < 2, nu <= 0, bad faces), LBM_ENOMEM, LBM_ECUDA. */
+int lbm_create(lbm_ctx **out, int nx, int ny, int nz, double nu,
+               const double forcing[3], const lbm_config *cfg);
+
+/* Release every buffer of the context (NULL is accepted). */
+int lbm_destroy(lbm_ctx *h);
+
+/* Initialise the populations to the equilibrium of the given fields, f_i = f_eq_i(rho, u)
+ * (product-form discrete Maxwellian), and reset the step counter to 0.
+ * rho: N floats; u: 3N floats (SoA).  Host or device pointers. */
+int lbm_set_state(lbm_ctx *h, const float *rho, const float *u);
+
+/* Install the immersed solid (Sec. 3.1): count samples at positions samples[3*s+a]
+ * (x, y, z interleaved, lattice units), per-sample area weights area[s] (NULL = 1) and
+ * boundary velocities u_b[3*s+a] (NULL = 0).  Every sample must satisfy
+ * 0 <= X_a < n_a - 1 on each axis (its 2x2x2 interpolation stencil lies in the domain);
+ * otherwise LBM_EINVAL and the previous solid is kept.  The library sorts the samples by
+ * base cell and builds the band of nodes the 2x2x2 kernel touches (Eqs. 6-8).
+ * count = 0 removes the solid.  Host or device pointers. */
+int lbm_set_solids(lbm_ctx *h, const float *samples, long long count,
+                   const float *area, const float *u_b);
+
+/* Advance n time steps (Algorithm 2: streaming, moments, immersed boundary, collision
+ * with forcing, domain faces), asynchronously on the context's stream.  Each step is one
+ * fused stream+collide kernel over all cells plus three small immersed-boundary kernels
+ * when a solid is installed.  Errors: LBM_ESTATE before lbm_set_state, LBM_ECUDA. */
+int lbm_step(lbm_ctx *h, int n);
+
+/* Density and Guo-shifted velocity u = (sum c f + F/2)/rho used by the most recent
+ * collision (Eq. 2); before any step, the fields given to lbm_set_state.
+ * rho: N floats, u: 3N floats (SoA); either may be NULL.  Host or device pointers;
+ * with host pointers the call returns after the copy completed. */
+int lbm_macroscopic(lbm_ctx *h, float *rho, float *u);
+
+/* FP64 global diagnostics of the most recent step: total mass sum rho, total momentum
+ * sum rho u, and the drag on the solid -sum_s g_s (Algorithm 2, total force).
+ * Any pointer may be NULL.  Host pointers; the call waits for the stream. */
+int lbm_reductions(lbm_ctx *h, double *mass, double mom[3], double drag[3]);
+
+/* Penalty forces g_s = rho_s (u_b - u_s) dA_s (Eq. 7) of the most recent step, in the
+ * caller's sample order: g[3*s+a].  Host or device pointer. */
+int lbm_ib_forces(lbm_ctx *h, float *g);
+
+/* Post-collision populations f_i(x) of the current time in canonical (non-AA) layout,
+ * converted to float: f[i*N + cell], i in the library's velocity order (lbm_velocity).
+ * Host or device pointer. */
+int lbm_populations(lbm_ctx *h, float *f);
+
+/* Velocity c_i of the library's direction i (0 <= i < 27); returns LBM_EINVAL otherwise. */
+int lbm_velocity(int i, int c[3]);
+
+/* Number of time steps taken since lbm_set_state / lbm_load. */
+long long lbm_time(const lbm_ctx *h);
+
+/* Scan the most recent macroscopic state for non-finite values: LBM_OK or LBM_EUNSTABLE. */
+int lbm_check(lbm_ctx *h);
+
+/* Wait for the context's stream with a wall-clock limit in seconds (<= 0: no limit),
+ * polling with cudaEventQuery: LBM_OK, LBM_ETIMEOUT or LBM_ECUDA. */
+int lbm_synchronize(lbm_ctx *h, double timeout_s);
+
+/* Checkpoint: serialise the state (header + populations in canonical layout in the
+ * storage type + outlet ghost plane + step counter) into buf.  With buf = NULL only
+ * *bytes is set to the required size.  Host pointer. */
+int lbm_save(lbm_ctx *h, void *buf, size_t *bytes);
+
+/* Restore a checkpoint written by lbm_save for the same dims and storage. */
+int lbm_load(lbm_ctx *h, const void *buf, size_t bytes);
+
+/* Per-kernel device timing (CUDA events on the context's stream around every launch).
+ * lbm_profile(h, 1) enables and clears the counters; lbm_profile(h, 0) disables. */
+#define LBM_KERNEL_STEP        0   /* fused stream + collide                  */
+#define LBM_KERNEL_BAND        1   /* immersed-boundary band moments          */
+#define LBM_KERNEL_INTERP      2   /* interpolation + penalty (Eqs. 6-7)       */
+#define LBM_KERNEL_SPREAD      3   /* spreading (Eq. 8)                        */
+#define LBM_KERNEL_OTHER       4   /* init, macroscopic, reductions, copies   */
+#define LBM_NUM_KERNEL_KINDS   5
+int lbm_profile(lbm_ctx *h, int enable);
+/* ms[k], launches[k] for k < LBM_NUM_KERNEL_KINDS; waits for the stream. */
+int lbm_kernel_times(lbm_ctx *h, double ms[LBM_NUM_KERNEL_KINDS], long long launches[LBM_NUM_KERNEL_KINDS]);
+
+/* Number of band nodes (nodes within the 2x2x2 stencil of a sample) of the solid. */
+long long lbm_band_size(const lbm_ctx *h);
+
+/* Message of the last error on h (or of the last failed lbm_create when h is NULL). */
+const char *lbm_last_error(const lbm_ctx *h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

@@ -1,0 +1,743 @@
+// C ABI of the solver (include/lbm.h): context, device buffers, the immersed-boundary
+// set-up on the host, the per-step launch sequence, diagnostics and checkpoints.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "lbm.h"
+#include "lbm_internal.h"
+
+using namespace lbm;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct EventRec {
+    int kind;
+    cudaEvent_t a, b;
+};
+
+}  // namespace
+
+struct lbm_ctx {
+    int nx = 0, ny = 0, nz = 0;
+    long long N = 0, plane = 0;
+    int storage = 0;
+    size_t esize = 4;
+    double nu = 0, forcing[3] = {0, 0, 0};
+    lbm_config cfg{};
+    cudaStream_t stream = nullptr;
+
+    void *f = nullptr;          // 27 * plane elements of the storage type
+    void *outlet = nullptr;     // 2 * 9 * ny * nz elements
+    float *inlet_profile = nullptr;
+    long long t = 0;
+    bool has_state = false;
+
+    // immersed solid (samples sorted by base cell)
+    long long S = 0, nband = 0, ntiles = 0;
+    float *X = nullptr, *area = nullptr, *ub = nullptr, *g = nullptr;
+    int *corner_band = nullptr, *band_cell = nullptr, *base_nbr = nullptr, *cstart = nullptr, *ccount = nullptr;
+    float *band_rho = nullptr, *band_u = nullptr, *bandF = nullptr;
+    uint32_t *tile_mask = nullptr;
+    int *tile_off = nullptr;
+    std::vector<long long> order;   // sorted position -> caller's sample index
+
+    // scratch of the reductions
+    double *partial = nullptr;
+    size_t partial_cap = 0;         // doubles
+    double *red = nullptr;          // 8 doubles
+    int *flag = nullptr;
+
+    // profiling
+    bool prof = false;
+    std::vector<EventRec> recs;
+    std::vector<cudaEvent_t> pool;
+    double ms[LBM_NUM_KERNEL_KINDS] = {};
+    long long launches[LBM_NUM_KERNEL_KINDS] = {};
+
+    std::string err;
+};
+
+namespace {
+
+int fail(lbm_ctx *h, int code, const std::string &msg) {
+    if (h) h->err = msg;
+    else g_create_error = msg;
+    return code;
+}
+
+#define CK(call)                                                                                 \
+    do {                                                                                         \
+        cudaError_t e_ = (call);                                                                 \
+        if (e_ != cudaSuccess) return fail(h, LBM_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+bool is_device_ptr(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <typename T>
+int dev_alloc(lbm_ctx *h, T **p, size_t count) {
+    *p = nullptr;
+    if (count == 0) return LBM_OK;
+    cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(h, LBM_ENOMEM, std::string("cudaMalloc of ") + std::to_string(count * sizeof(T)) + " bytes failed");
+    }
+    return LBM_OK;
+}
+
+template <typename T> void dev_free(T *&p) {
+    if (p) cudaFree((void *)p);
+    p = nullptr;
+}
+
+cudaEvent_t pool_event(lbm_ctx *h) {
+    if (!h->pool.empty()) {
+        cudaEvent_t e = h->pool.back();
+        h->pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+struct Timed {
+    lbm_ctx *h;
+    int kind;
+    cudaEvent_t a = nullptr;
+    Timed(lbm_ctx *h_, int k) : h(h_), kind(k) {
+        h->launches[kind]++;
+        if (h->prof) {
+            a = pool_event(h);
+            cudaEventRecord(a, h->stream);
+        }
+    }
+    ~Timed() {
+        if (h->prof) {
+            cudaEvent_t b = pool_event(h);
+            cudaEventRecord(b, h->stream);
+            h->recs.push_back({kind, a, b});
+        }
+    }
+};
+
+StepParams make_params(const lbm_ctx *h, long long t) {
+    StepParams P{};
+    P.f = h->f;
+    P.outlet = h->outlet;
+    Geometry &g = P.g;
+    g.nx = h->nx; g.ny = h->ny; g.nz = h->nz;
+    g.nxy = h->nx * h->ny;
+    g.ncell = (int)h->N;
+    g.nyz = h->ny * h->nz;
+    g.plane = h->plane;
+    for (int a = 0; a < 3; ++a) g.periodic[a] = h->cfg.face_type[2 * a] == LBM_FACE_PERIODIC;
+    for (int k = 0; k < 6; ++k) g.face[k] = h->cfg.face_type[k];
+    P.rho0 = (float)h->cfg.rho0;
+    P.Fx = (float)h->forcing[0];
+    P.Fy = (float)h->forcing[1];
+    P.Fz = (float)h->forcing[2];
+    const double ws = 1.0 / (3.0 * h->nu + 0.5);
+    P.rs = (float)(1.0 - ws);
+    P.rb = (float)(1.0 - h->cfg.omega_bulk);
+    P.r3 = (float)(1.0 - h->cfg.omega_hi[0]);
+    P.r4 = (float)(1.0 - h->cfg.omega_hi[1]);
+    P.r5 = (float)(1.0 - h->cfg.omega_hi[2]);
+    P.r6 = (float)(1.0 - h->cfg.omega_hi[3]);
+    P.q3 = (float)(1.0 - 0.5 * h->cfg.omega_hi[0]);
+    P.q5 = (float)(1.0 - 0.5 * h->cfg.omega_hi[2]);
+    P.u_in = (float)h->cfg.u_in;
+    P.noise = (float)h->cfg.inlet_noise;
+    P.seed = h->cfg.seed;
+    P.t = t;
+    P.inlet_profile = h->inlet_profile;
+    P.tile_mask = h->tile_mask;
+    P.tile_off = h->tile_off;
+    P.bandF = h->bandF;
+    P.nband = h->nband;
+    return P;
+}
+
+int ensure_partial(lbm_ctx *h, size_t doubles) {
+    if (doubles <= h->partial_cap) return LBM_OK;
+    dev_free(h->partial);
+    h->partial_cap = 0;
+    int rc = dev_alloc(h, &h->partial, doubles);
+    if (rc) return rc;
+    h->partial_cap = doubles;
+    return LBM_OK;
+}
+
+void free_solid(lbm_ctx *h) {
+    dev_free(h->X); dev_free(h->area); dev_free(h->ub); dev_free(h->g);
+    dev_free(h->corner_band); dev_free(h->band_cell); dev_free(h->base_nbr);
+    dev_free(h->cstart); dev_free(h->ccount);
+    dev_free(h->band_rho); dev_free(h->band_u); dev_free(h->bandF);
+    dev_free(h->tile_mask); dev_free(h->tile_off);
+    h->S = h->nband = h->ntiles = 0;
+    h->order.clear();
+}
+
+// copy n floats from a host or device pointer into a host vector
+int fetch_floats(lbm_ctx *h, const float *src, size_t n, std::vector<float> &dst) {
+    dst.resize(n);
+    if (n == 0) return LBM_OK;
+    if (is_device_ptr(src)) {
+        CK(cudaMemcpyAsync(dst.data(), src, n * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+    } else {
+        std::memcpy(dst.data(), src, n * sizeof(float));
+    }
+    return LBM_OK;
+}
+
+template <typename T> int upload(lbm_ctx *h, T **dst, const std::vector<T> &src) {
+    int rc = dev_alloc(h, dst, src.size());
+    if (rc) return rc;
+    if (!src.empty()) CK(cudaMemcpyAsync(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, h->stream));
+    return LBM_OK;
+}
+
+// deliver n floats from device buffer `src` to a caller pointer (host or device)
+int deliver(lbm_ctx *h, float *dst, const float *src, size_t n) {
+    CK(cudaMemcpyAsync(dst, src, n * sizeof(float), cudaMemcpyDefault, h->stream));
+    return LBM_OK;
+}
+
+int require_state(lbm_ctx *h) {
+    if (!h) return fail(nullptr, LBM_EINVAL, "null context");
+    if (!h->has_state) return fail(h, LBM_ESTATE, "lbm_set_state (or lbm_load) has not been called");
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void lbm_config_default(lbm_config *cfg) {
+    if (!cfg) return;
+    std::memset(cfg, 0, sizeof(*cfg));
+    cfg->storage = LBM_STORE_F32;
+    for (int k = 0; k < 6; ++k) cfg->face_type[k] = LBM_FACE_PERIODIC;
+    cfg->rho0 = 1.0;
+    cfg->seed = 2101ull;
+    cfg->omega_bulk = 1.0;
+    for (int k = 0; k < 4; ++k) cfg->omega_hi[k] = 1.0;
+    cfg->cuda_stream = nullptr;
+}
+
+int lbm_create(lbm_ctx **out, int nx, int ny, int nz, double nu, const double forcing[3], const lbm_config *cfg) {
+    lbm_ctx *h = nullptr;
+    if (!out) return fail(nullptr, LBM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (nx < 1 || ny < 1 || nz < 1) return fail(nullptr, LBM_EINVAL, "dimensions must be >= 1");
+    const long long N = (long long)nx * ny * nz;
+    if (N > 2000000000LL) return fail(nullptr, LBM_EINVAL, "more than 2e9 cells");
+    if (!(nu > 0.0) || !std::isfinite(nu)) return fail(nullptr, LBM_EINVAL, "nu must be positive and finite");
+    lbm_config c;
+    if (cfg) c = *cfg;
+    else lbm_config_default(&c);
+    if (c.storage < 0 || c.storage > 2) return fail(nullptr, LBM_EINVAL, "unknown storage type");
+    for (int k = 0; k < 6; ++k)
+        if (c.face_type[k] < 0 || c.face_type[k] > 3) return fail(nullptr, LBM_EINVAL, "unknown face type");
+    for (int a = 0; a < 3; ++a)
+        if ((c.face_type[2 * a] == LBM_FACE_PERIODIC) != (c.face_type[2 * a + 1] == LBM_FACE_PERIODIC))
+            return fail(nullptr, LBM_EINVAL, "periodic faces must come in pairs");
+    for (int k = 0; k < 6; ++k) {
+        if (c.face_type[k] == LBM_FACE_INLET && k != 0) return fail(nullptr, LBM_EINVAL, "the inlet must be the -x face");
+        if (c.face_type[k] == LBM_FACE_OUTLET && k != 1) return fail(nullptr, LBM_EINVAL, "the outlet must be the +x face");
+    }
+    if (!(c.rho0 > 0.0)) return fail(nullptr, LBM_EINVAL, "rho0 must be positive");
+
+    h = new (std::nothrow) lbm_ctx();
+    if (!h) return fail(nullptr, LBM_ENOMEM, "host allocation failed");
+    h->nx = nx; h->ny = ny; h->nz = nz;
+    h->N = N;
+    h->plane = (N + 63) / 64 * 64;
+    h->storage = c.storage;
+    h->esize = c.storage == LBM_STORE_F32 ? 4 : 2;
+    h->nu = nu;
+    if (forcing) for (int a = 0; a < 3; ++a) h->forcing[a] = forcing[a];
+    h->cfg = c;
+    h->stream = (cudaStream_t)c.cuda_stream;
+
+    auto bail = [&](int rc) {
+        std::string msg = h->err;
+        lbm_destroy(h);
+        g_create_error = msg;
+        return rc;
+    };
+    cudaError_t e = cudaMalloc(&h->f, (size_t)27 * h->plane * h->esize);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        h->f = nullptr;
+        h->err = "cannot allocate the population array (" + std::to_string((size_t)27 * h->plane * h->esize) + " bytes)";
+        return bail(LBM_ENOMEM);
+    }
+    if (cudaMemsetAsync(h->f, 0, (size_t)27 * h->plane * h->esize, h->stream) != cudaSuccess) {
+        h->err = "cudaMemsetAsync failed";
+        return bail(LBM_ECUDA);
+    }
+    if (c.face_type[1] == LBM_FACE_OUTLET) {
+        if (cudaMalloc(&h->outlet, (size_t)2 * 9 * ny * nz * h->esize) != cudaSuccess) {
+            cudaGetLastError();
+            h->outlet = nullptr;
+            h->err = "cannot allocate the outlet plane";
+            return bail(LBM_ENOMEM);
+        }
+    }
+    bool any_coef = false;
+    for (int k = 0; k < 16; ++k) any_coef |= c.inflow_coef[k] != 0.0;
+    if (any_coef && c.face_type[0] == LBM_FACE_INLET) {
+        std::vector<float> prof((size_t)ny * nz);
+        for (int z = 0; z < nz; ++z)
+            for (int y = 0; y < ny; ++y) {
+                double v = 0.0;
+                for (int m = 1; m <= 4; ++m)
+                    for (int n = 1; n <= 4; ++n)
+                        v += c.inflow_coef[(m - 1) * 4 + (n - 1)] * std::sin(m * M_PI * (y + 0.5) / ny) *
+                             std::sin(n * M_PI * (z + 0.5) / nz);
+                prof[y + (size_t)ny * z] = (float)v;
+            }
+        if (upload(h, &h->inlet_profile, prof) != LBM_OK) return bail(LBM_ENOMEM);
+    }
+    if (dev_alloc(h, &h->red, 8) != LBM_OK || dev_alloc(h, &h->flag, 1) != LBM_OK) return bail(LBM_ENOMEM);
+    *out = h;
+    return LBM_OK;
+}
+
+int lbm_destroy(lbm_ctx *h) {
+    if (!h) return LBM_OK;
+    if (h->f) cudaStreamSynchronize(h->stream);
+    free_solid(h);
+    dev_free(h->f);
+    dev_free(h->outlet);
+    dev_free(h->inlet_profile);
+    dev_free(h->partial);
+    dev_free(h->red);
+    dev_free(h->flag);
+    for (auto &r : h->recs) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (auto e : h->pool) cudaEventDestroy(e);
+    delete h;
+    return LBM_OK;
+}
+
+int lbm_set_state(lbm_ctx *h, const float *rho, const float *u) {
+    if (!h) return fail(nullptr, LBM_EINVAL, "null context");
+    if (!rho || !u) return fail(h, LBM_EINVAL, "rho and u are required");
+    const float *drho = rho, *du = u;
+    float *tmp = nullptr;
+    const bool dev = is_device_ptr(rho) && is_device_ptr(u);
+    if (!dev) {
+        int rc = dev_alloc(h, &tmp, (size_t)4 * h->N);
+        if (rc) return rc;
+        CK(cudaMemcpyAsync(tmp, rho, (size_t)h->N * sizeof(float), cudaMemcpyDefault, h->stream));
+        CK(cudaMemcpyAsync(tmp + h->N, u, (size_t)3 * h->N * sizeof(float), cudaMemcpyDefault, h->stream));
+        drho = tmp;
+        du = tmp + h->N;
+    }
+    StepParams P = make_params(h, 0);
+    {
+        Timed tm(h, LBM_KERNEL_OTHER);
+        CK(launch_init(h->storage, P, drho, du, h->stream));
+    }
+    if (tmp) {
+        CK(cudaStreamSynchronize(h->stream));
+        dev_free(tmp);
+    }
+    h->t = 0;
+    h->has_state = true;
+    return LBM_OK;
+}
+
+int lbm_set_solids(lbm_ctx *h, const float *samples, long long count, const float *area, const float *u_b) {
+    if (!h) return fail(nullptr, LBM_EINVAL, "null context");
+    if (count < 0) return fail(h, LBM_EINVAL, "negative sample count");
+    if (count == 0) {
+        CK(cudaStreamSynchronize(h->stream));
+        free_solid(h);
+        return LBM_OK;
+    }
+    if (!samples) return fail(h, LBM_EINVAL, "samples is NULL");
+    if (count > 1000000000LL) return fail(h, LBM_EINVAL, "more than 1e9 samples");
+    const size_t S = (size_t)count;
+    std::vector<float> pos, ar, vb;
+    int rc;
+    if ((rc = fetch_floats(h, samples, 3 * S, pos))) return rc;
+    if (area) { if ((rc = fetch_floats(h, area, S, ar))) return rc; }
+    else ar.assign(S, 1.0f);
+    if (u_b) { if ((rc = fetch_floats(h, u_b, 3 * S, vb))) return rc; }
+    else vb.assign(3 * S, 0.0f);
+
+    const int n[3] = {h->nx, h->ny, h->nz};
+    std::vector<long long> key(S);
+    for (size_t s = 0; s < S; ++s) {
+        int b[3];
+        for (int a = 0; a < 3; ++a) {
+            const float v = pos[3 * s + a];
+            if (!std::isfinite(v) || !(v >= 0.0f) || !(v < (float)(n[a] - 1)))
+                return fail(h, LBM_EINVAL, "sample " + std::to_string(s) + " outside [0, n-1) or not finite");
+            b[a] = (int)std::floor(v);
+        }
+        if (!std::isfinite(ar[s]) || !std::isfinite(vb[3 * s]) || !std::isfinite(vb[3 * s + 1]) || !std::isfinite(vb[3 * s + 2]))
+            return fail(h, LBM_EINVAL, "non-finite area or boundary velocity");
+        key[s] = b[0] + (long long)h->nx * (b[1] + (long long)h->ny * b[2]);
+    }
+    std::vector<long long> ord(S);
+    std::iota(ord.begin(), ord.end(), 0LL);
+    std::stable_sort(ord.begin(), ord.end(), [&](long long a, long long b) { return key[a] < key[b]; });
+
+    // band: every node within the 2x2x2 stencil of a sample, as a bitmap over the cells
+    const long long ntiles = (h->N + 31) / 32;
+    std::vector<uint32_t> mask(ntiles, 0u);
+    const long long cstep[8] = {0, 1, h->nx, (long long)h->nx + 1, (long long)h->nx * h->ny,
+                                (long long)h->nx * h->ny + 1, (long long)h->nx * h->ny + h->nx,
+                                (long long)h->nx * h->ny + h->nx + 1};
+    for (size_t s = 0; s < S; ++s)
+        for (int c = 0; c < 8; ++c) {
+            const long long cell = key[s] + cstep[c];
+            mask[cell >> 5] |= 1u << (cell & 31);
+        }
+    std::vector<int> toff(ntiles);
+    long long nb = 0;
+    for (long long w = 0; w < ntiles; ++w) {
+        toff[w] = (int)nb;
+        nb += __builtin_popcount(mask[w]);
+    }
+    if (nb > 2000000000LL) return fail(h, LBM_EINVAL, "band too large");
+    auto band_index = [&](long long cell) -> int {
+        const uint32_t m = mask[cell >> 5];
+        const int l = (int)(cell & 31);
+        if (!((m >> l) & 1u)) return -1;
+        return toff[cell >> 5] + __builtin_popcount(m & ((1u << l) - 1u));
+    };
+    std::vector<int> bcell(nb);
+    for (long long w = 0, k = 0; w < ntiles; ++w)
+        for (int l = 0; l < 32; ++l)
+            if ((mask[w] >> l) & 1u) bcell[k++] = (int)(w * 32 + l);
+    std::vector<int> cst(nb, 0), ccnt(nb, 0);
+    for (size_t i = 0; i < S; ++i) {
+        const int bi = band_index(key[ord[i]]);
+        if (ccnt[bi] == 0) cst[bi] = (int)i;
+        ccnt[bi]++;
+    }
+    std::vector<int> bnbr((size_t)8 * nb);
+    for (long long k = 0; k < nb; ++k) {
+        const long long cell = bcell[k];
+        const int x = (int)(cell % h->nx), y = (int)((cell / h->nx) % h->ny), z = (int)(cell / ((long long)h->nx * h->ny));
+        for (int c = 0; c < 8; ++c) {
+            const int bx = x - (c & 1), by = y - ((c >> 1) & 1), bz = z - ((c >> 2) & 1);
+            int v = -1;
+            if (bx >= 0 && by >= 0 && bz >= 0) {
+                const int bi = band_index(bx + (long long)h->nx * (by + (long long)h->ny * bz));
+                if (bi >= 0 && ccnt[bi] > 0) v = bi;
+            }
+            bnbr[(size_t)c * nb + k] = v;
+        }
+    }
+    std::vector<int> cb((size_t)8 * S);
+    std::vector<float> Xs(3 * S), As(S), Us(3 * S);
+    for (size_t i = 0; i < S; ++i) {
+        const long long s = ord[i];
+        for (int c = 0; c < 8; ++c) cb[(size_t)c * S + i] = band_index(key[s] + cstep[c]);
+        for (int a = 0; a < 3; ++a) {
+            Xs[a * S + i] = pos[3 * s + a];
+            Us[a * S + i] = vb[3 * s + a];
+        }
+        As[i] = ar[s];
+    }
+
+    CK(cudaStreamSynchronize(h->stream));
+    free_solid(h);
+    h->S = (long long)S;
+    h->nband = nb;
+    h->ntiles = ntiles;
+    h->order = ord;
+    if ((rc = upload(h, &h->X, Xs)) || (rc = upload(h, &h->area, As)) || (rc = upload(h, &h->ub, Us)) ||
+        (rc = upload(h, &h->corner_band, cb)) || (rc = upload(h, &h->band_cell, bcell)) ||
+        (rc = upload(h, &h->base_nbr, bnbr)) || (rc = upload(h, &h->cstart, cst)) || (rc = upload(h, &h->ccount, ccnt)) ||
+        (rc = upload(h, &h->tile_mask, mask)) || (rc = upload(h, &h->tile_off, toff))) {
+        free_solid(h);
+        return rc;
+    }
+    if ((rc = dev_alloc(h, &h->g, 3 * S)) || (rc = dev_alloc(h, &h->band_rho, (size_t)nb)) ||
+        (rc = dev_alloc(h, &h->band_u, (size_t)3 * nb)) || (rc = dev_alloc(h, &h->bandF, (size_t)3 * nb))) {
+        free_solid(h);
+        return rc;
+    }
+    CK(cudaMemsetAsync(h->g, 0, 3 * S * sizeof(float), h->stream));
+    CK(cudaMemsetAsync(h->bandF, 0, (size_t)3 * nb * sizeof(float), h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+int lbm_step(lbm_ctx *h, int n) {
+    int rc = require_state(h);
+    if (rc) return rc;
+    if (n < 0) return fail(h, LBM_EINVAL, "negative step count");
+    for (int k = 0; k < n; ++k) {
+        const long long t = h->t + 1;
+        StepParams P = make_params(h, t);
+        const bool band = h->S > 0;
+        if (band) {
+            { Timed tm(h, LBM_KERNEL_BAND); CK(launch_band_moments(h->storage, P, h->band_cell, h->band_rho, h->band_u, h->stream)); }
+            { Timed tm(h, LBM_KERNEL_INTERP); CK(launch_ib_interp(h->S, h->nband, h->X, h->area, h->ub, h->corner_band, h->band_rho, h->band_u, h->g, h->stream)); }
+            { Timed tm(h, LBM_KERNEL_SPREAD); CK(launch_ib_spread(h->S, h->nband, h->X, h->g, h->base_nbr, h->cstart, h->ccount, h->bandF, h->stream)); }
+        }
+        { Timed tm(h, LBM_KERNEL_STEP); CK(launch_step(h->storage, P, band, h->stream)); }
+        h->t = t;
+    }
+    return LBM_OK;
+}
+
+int lbm_macroscopic(lbm_ctx *h, float *rho, float *u) {
+    int rc = require_state(h);
+    if (rc) return rc;
+    if (!rho && !u) return LBM_OK;
+    const bool dr = !rho || is_device_ptr(rho), du = !u || is_device_ptr(u);
+    float *tmp = nullptr;
+    float *drho = rho, *duu = u;
+    if (!dr || !du) {
+        if ((rc = dev_alloc(h, &tmp, (size_t)4 * h->N))) return rc;
+        if (!dr) drho = tmp;
+        if (!du) duu = tmp + h->N;
+    }
+    StepParams P = make_params(h, h->t);
+    {
+        Timed tm(h, LBM_KERNEL_OTHER);
+        CK(launch_macro(h->storage, P, h->S > 0, h->t > 0, drho, duu, nullptr, nullptr, nullptr, h->stream));
+    }
+    if (!dr) CK(cudaMemcpyAsync(rho, drho, (size_t)h->N * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    if (!du) CK(cudaMemcpyAsync(u, duu, (size_t)3 * h->N * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    if (tmp) {
+        CK(cudaStreamSynchronize(h->stream));
+        dev_free(tmp);
+    }
+    return LBM_OK;
+}
+
+int lbm_reductions(lbm_ctx *h, double *mass, double mom[3], double drag[3]) {
+    int rc = require_state(h);
+    if (rc) return rc;
+    StepParams P = make_params(h, h->t);
+    const long long nblk = macro_blocks(P);
+    const int fblk = force_sum_blocks();
+    if ((rc = ensure_partial(h, (size_t)std::max<long long>(4 * nblk, 3 * fblk)))) return rc;
+    {
+        Timed tm(h, LBM_KERNEL_OTHER);
+        CK(launch_macro(h->storage, P, h->S > 0, h->t > 0, nullptr, nullptr, nullptr, h->partial, nullptr, h->stream));
+        CK(launch_finalize(h->partial, nblk, 4, h->red, h->stream));
+    }
+    if (h->S > 0 && h->t > 0) {
+        Timed tm(h, LBM_KERNEL_OTHER);
+        CK(launch_sum_forces(h->S, h->g, h->partial, h->stream));
+        CK(launch_finalize(h->partial, fblk, 3, h->red + 4, h->stream));
+    } else {
+        CK(cudaMemsetAsync(h->red + 4, 0, 3 * sizeof(double), h->stream));
+    }
+    double r[7];
+    CK(cudaMemcpyAsync(r, h->red, 7 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (mass) *mass = r[0];
+    if (mom) for (int a = 0; a < 3; ++a) mom[a] = r[1 + a];
+    if (drag) for (int a = 0; a < 3; ++a) drag[a] = -r[4 + a];
+    return LBM_OK;
+}
+
+int lbm_ib_forces(lbm_ctx *h, float *g) {
+    int rc = require_state(h);
+    if (rc) return rc;
+    if (!g) return fail(h, LBM_EINVAL, "g is NULL");
+    const size_t S = (size_t)h->S;
+    if (S == 0) return LBM_OK;
+    std::vector<float> sorted(3 * S), out(3 * S);
+    CK(cudaMemcpyAsync(sorted.data(), h->g, 3 * S * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    for (size_t i = 0; i < S; ++i)
+        for (int a = 0; a < 3; ++a) out[3 * h->order[i] + a] = sorted[a * S + i];
+    CK(cudaMemcpyAsync(g, out.data(), 3 * S * sizeof(float), cudaMemcpyDefault, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+int lbm_populations(lbm_ctx *h, float *f) {
+    int rc = require_state(h);
+    if (rc) return rc;
+    if (!f) return fail(h, LBM_EINVAL, "f is NULL");
+    float *df = f, *tmp = nullptr;
+    const bool dev = is_device_ptr(f);
+    if (!dev) {
+        if ((rc = dev_alloc(h, &tmp, (size_t)27 * h->N))) return rc;
+        df = tmp;
+    }
+    StepParams P = make_params(h, h->t);
+    {
+        Timed tm(h, LBM_KERNEL_OTHER);
+        CK(launch_macro(h->storage, P, h->S > 0, h->t > 0, nullptr, nullptr, df, nullptr, nullptr, h->stream));
+    }
+    if (!dev) {
+        CK(cudaMemcpyAsync(f, tmp, (size_t)27 * h->N * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        dev_free(tmp);
+    }
+    return LBM_OK;
+}
+
+int lbm_velocity(int i, int c[3]) {
+    if (i < 0 || i >= 27 || !c) return LBM_EINVAL;
+    c[0] = cx(i);
+    c[1] = cy(i);
+    c[2] = cz(i);
+    return LBM_OK;
+}
+
+long long lbm_time(const lbm_ctx *h) { return h ? h->t : -1; }
+
+long long lbm_band_size(const lbm_ctx *h) { return h ? h->nband : -1; }
+
+int lbm_check(lbm_ctx *h) {
+    int rc = require_state(h);
+    if (rc) return rc;
+    CK(cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream));
+    StepParams P = make_params(h, h->t);
+    {
+        Timed tm(h, LBM_KERNEL_OTHER);
+        CK(launch_macro(h->storage, P, h->S > 0, h->t > 0, nullptr, nullptr, nullptr, nullptr, h->flag, h->stream));
+    }
+    int bad = 0;
+    CK(cudaMemcpyAsync(&bad, h->flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (bad) return fail(h, LBM_EUNSTABLE, "non-finite density or velocity at step " + std::to_string(h->t));
+    return LBM_OK;
+}
+
+int lbm_synchronize(lbm_ctx *h, double timeout_s) {
+    if (!h) return fail(nullptr, LBM_EINVAL, "null context");
+    cudaEvent_t e;
+    CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    CK(cudaEventRecord(e, h->stream));
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        cudaError_t q = cudaEventQuery(e);
+        if (q == cudaSuccess) break;
+        if (q != cudaErrorNotReady) {
+            cudaEventDestroy(e);
+            return fail(h, LBM_ECUDA, std::string("stream failed: ") + cudaGetErrorString(q));
+        }
+        const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (timeout_s > 0 && el > timeout_s) {
+            cudaEventDestroy(e);
+            return fail(h, LBM_ETIMEOUT, "stream did not finish within the time limit");
+        }
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+    cudaEventDestroy(e);
+    return LBM_OK;
+}
+
+// checkpoint layout: header (8 int64) | populations (27 planes of N elements) | outlet plane
+static const long long kMagic = 0x4c424d4741413031LL;   // "LBMGAA01"
+
+int lbm_save(lbm_ctx *h, void *buf, size_t *bytes) {
+    int rc = require_state(h);
+    if (rc) return rc;
+    if (!bytes) return fail(h, LBM_EINVAL, "bytes is NULL");
+    const size_t pop = (size_t)27 * h->N * h->esize;
+    const size_t outl = h->outlet ? (size_t)2 * 9 * h->ny * h->nz * h->esize : 0;
+    const size_t need = 8 * sizeof(long long) + pop + outl;
+    if (!buf) {
+        *bytes = need;
+        return LBM_OK;
+    }
+    if (*bytes < need) return fail(h, LBM_EINVAL, "buffer too small");
+    long long hdr[8] = {kMagic, h->nx, h->ny, h->nz, h->storage, h->t, (long long)outl, 0};
+    char *p = static_cast<char *>(buf);
+    std::memcpy(p, hdr, sizeof(hdr));
+    p += sizeof(hdr);
+    for (int d = 0; d < 27; ++d)
+        CK(cudaMemcpyAsync(p + (size_t)d * h->N * h->esize, static_cast<char *>(h->f) + (size_t)d * h->plane * h->esize,
+                           (size_t)h->N * h->esize, cudaMemcpyDefault, h->stream));
+    if (outl) CK(cudaMemcpyAsync(p + pop, h->outlet, outl, cudaMemcpyDefault, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    *bytes = need;
+    return LBM_OK;
+}
+
+int lbm_load(lbm_ctx *h, const void *buf, size_t bytes) {
+    if (!h) return fail(nullptr, LBM_EINVAL, "null context");
+    if (!buf || bytes < 8 * sizeof(long long)) return fail(h, LBM_EINVAL, "bad checkpoint buffer");
+    long long hdr[8];
+    std::memcpy(hdr, buf, sizeof(hdr));
+    const size_t pop = (size_t)27 * h->N * h->esize;
+    const size_t outl = h->outlet ? (size_t)2 * 9 * h->ny * h->nz * h->esize : 0;
+    if (hdr[0] != kMagic || hdr[1] != h->nx || hdr[2] != h->ny || hdr[3] != h->nz || hdr[4] != h->storage ||
+        hdr[6] != (long long)outl || bytes < sizeof(hdr) + pop + outl)
+        return fail(h, LBM_EINVAL, "checkpoint does not match this context");
+    const char *p = static_cast<const char *>(buf) + sizeof(hdr);
+    for (int d = 0; d < 27; ++d)
+        CK(cudaMemcpyAsync(static_cast<char *>(h->f) + (size_t)d * h->plane * h->esize, p + (size_t)d * h->N * h->esize,
+                           (size_t)h->N * h->esize, cudaMemcpyDefault, h->stream));
+    if (outl) CK(cudaMemcpyAsync(h->outlet, p + pop, outl, cudaMemcpyDefault, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    h->t = hdr[5];
+    h->has_state = true;
+    return LBM_OK;
+}
+
+int lbm_profile(lbm_ctx *h, int enable) {
+    if (!h) return fail(nullptr, LBM_EINVAL, "null context");
+    CK(cudaStreamSynchronize(h->stream));
+    for (auto &r : h->recs) {
+        h->pool.push_back(r.a);
+        h->pool.push_back(r.b);
+    }
+    h->recs.clear();
+    for (int k = 0; k < LBM_NUM_KERNEL_KINDS; ++k) {
+        h->ms[k] = 0.0;
+        h->launches[k] = 0;
+    }
+    h->prof = enable != 0;
+    return LBM_OK;
+}
+
+int lbm_kernel_times(lbm_ctx *h, double ms[LBM_NUM_KERNEL_KINDS], long long launches[LBM_NUM_KERNEL_KINDS]) {
+    if (!h) return fail(nullptr, LBM_EINVAL, "null context");
+    CK(cudaStreamSynchronize(h->stream));
+    for (auto &r : h->recs) {
+        float t = 0.0f;
+        CK(cudaEventElapsedTime(&t, r.a, r.b));
+        h->ms[r.kind] += t;
+        h->pool.push_back(r.a);
+        h->pool.push_back(r.b);
+    }
+    h->recs.clear();
+    for (int k = 0; k < LBM_NUM_KERNEL_KINDS; ++k) {
+        if (ms) ms[k] = h->ms[k];
+        if (launches) launches[k] = h->launches[k];
+    }
+    return LBM_OK;
+}
+
+const char *lbm_last_error(const lbm_ctx *h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,271 @@
+// Device-side building blocks of the fused D3Q27 step: lattice tables, population
+// storage types, the AA-pattern addressing with the domain faces, and the
+// central-moment MRT collision with Guo forcing computed in registers.
+//
+// Direction order (this library's own): d = (cx+1) + 3 (cy+1) + 9 (cz+1), so the 27
+// populations of a node form a 3x3x3 tensor and the central-moment transform of Eq. 5
+// factorises into three sweeps of nine 3-point transforms.  opp(d) = 26 - d.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbm {
+
+__host__ __device__ constexpr int cx(int d) { return d % 3 - 1; }
+__host__ __device__ constexpr int cy(int d) { return (d / 3) % 3 - 1; }
+__host__ __device__ constexpr int cz(int d) { return d / 9 - 1; }
+__host__ __device__ constexpr int opp(int d) { return 26 - d; }
+__host__ __device__ constexpr float w1(int c) { return c == 0 ? 2.0f / 3.0f : 1.0f / 6.0f; }
+// lattice weight of direction d (8/27, 2/27, 1/54, 1/216)
+__host__ __device__ constexpr float wgt(int d) { return w1(cx(d)) * w1(cy(d)) * w1(cz(d)); }
+// index of central moment kappa_pqr in the in-place moment tensor
+__host__ __device__ constexpr int K(int p, int q, int r) { return p + 3 * q + 9 * r; }
+
+enum FaceType { FACE_PERIODIC = 0, FACE_NOSLIP = 1, FACE_INLET = 2, FACE_OUTLET = 3 };
+// bits of a crossing classification
+enum { CROSS_NOSLIP = 1, CROSS_INLET = 2, CROSS_OUTLET = 4 };
+
+__host__ __device__ constexpr int face_bit(int t) {
+    return t == FACE_NOSLIP ? CROSS_NOSLIP : t == FACE_INLET ? CROSS_INLET : t == FACE_OUTLET ? CROSS_OUTLET : 0;
+}
+
+// ---- population storage: deviations h_i = f_i - w_i rho0 ---------------------------
+
+template <typename T> struct Store;
+template <> struct Store<float> {
+    static __device__ __forceinline__ float ld(const float *p) { return *p; }
+    static __device__ __forceinline__ void st(float *p, float v) { *p = v; }
+};
+template <> struct Store<__half> {
+    static __device__ __forceinline__ float ld(const __half *p) { return __half2float(*p); }
+    static __device__ __forceinline__ void st(__half *p, float v) { *p = __float2half_rn(v); }
+};
+template <> struct Store<__nv_bfloat16> {
+    static __device__ __forceinline__ float ld(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
+    static __device__ __forceinline__ void st(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
+};
+
+// ---- launch parameters -----------------------------------------------------------------
+
+struct Geometry {
+    int nx, ny, nz;
+    int nxy;             // nx * ny
+    int ncell;           // nx * ny * nz
+    int nyz;             // ny * nz (outlet plane)
+    long long plane;     // elements between consecutive direction planes (>= ncell)
+    int periodic[3];
+    int face[6];         // FaceType of -x, +x, -y, +y, -z, +z
+};
+
+struct StepParams {
+    void *f;                     // populations, 27 planes (AA in place)
+    void *outlet;                // outlet ghost plane, [2][9][nyz] (ping-pong by step parity)
+    Geometry g;
+    float rho0;
+    float Fx, Fy, Fz;            // body force
+    float rs, rb, r3, r4, r5, r6;   // 1 - omega of shear, bulk, orders 3..6
+    float q3, q5;                // 1 - omega/2 of orders 3 and 5 (their force moments)
+    float u_in, noise;           // inlet velocity and relative noise amplitude
+    unsigned long long seed;
+    long long t;                 // index of the step being computed (1-based)
+    const float *inlet_profile;  // [nyz] Fourier part of the inflow, or nullptr
+    const uint32_t *tile_mask;   // bit l of word w: cell 32 w + l is a band node
+    const int *tile_off;         // band index of the first band node of word w
+    const float *bandF;          // [3][nband] immersed-boundary force of the band nodes
+    long long nband;
+};
+
+// ---- inlet noise: counter-based SplitMix64 (Steele, Lea, Flood 2014) ------------------
+
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long seed, unsigned long long n) {
+    unsigned long long z = seed + (n + 1ull) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// inlet wall velocity u_in (1 + noise xi) + profile at inlet node (y, z) and step t
+__device__ __forceinline__ float inlet_velocity(const StepParams &P, int y, int z) {
+    double u = P.u_in;
+    if (P.noise != 0.0f) {
+        unsigned long long n = ((unsigned long long)P.t * P.g.ny + y) * P.g.nz + z;
+        double xi = 2.0 * ((double)(splitmix64(P.seed, n) >> 11) * 0x1.0p-53) - 1.0;
+        u = (double)P.u_in * (1.0 + (double)P.noise * xi);
+    }
+    float uw = (float)u;
+    if (P.inlet_profile) uw += P.inlet_profile[y + P.g.ny * z];
+    return uw;
+}
+
+// ---- neighbour classification with the domain faces ----------------------------------
+
+struct Nbr {
+    int idx;    // flat index of the (wrapped) node, valid when kind == 0 or for lateral wraps
+    int y, z;   // wrapped lateral coordinates
+    int kind;   // CROSS_* bits of the non-periodic faces crossed
+};
+
+// node x + S c_D (S = -1: pull source, S = +1: push target); D is a constant after unrolling
+template <int S>
+__device__ __forceinline__ Nbr neighbour(const Geometry &g, int D, int x, int y, int z) {
+    int sx = x + S * cx(D), sy = y + S * cy(D), sz = z + S * cz(D);
+    int kind = 0;
+    if (cx(D) != 0) {
+        if (sx < 0) { if (g.periodic[0]) sx += g.nx; else kind |= face_bit(g.face[0]); }
+        else if (sx >= g.nx) { if (g.periodic[0]) sx -= g.nx; else kind |= face_bit(g.face[1]); }
+    }
+    if (cy(D) != 0) {
+        if (sy < 0) { if (g.periodic[1]) sy += g.ny; else kind |= face_bit(g.face[2]); }
+        else if (sy >= g.ny) { if (g.periodic[1]) sy -= g.ny; else kind |= face_bit(g.face[3]); }
+    }
+    if (cz(D) != 0) {
+        if (sz < 0) { if (g.periodic[2]) sz += g.nz; else kind |= face_bit(g.face[4]); }
+        else if (sz >= g.nz) { if (g.periodic[2]) sz -= g.nz; else kind |= face_bit(g.face[5]); }
+    }
+    Nbr n;
+    n.idx = sx + g.nx * (sy + g.ny * sz);
+    n.y = sy;
+    n.z = sz;
+    n.kind = kind;
+    return n;
+}
+
+// ---- the 3-point transforms of the factorised central-moment basis -------------------
+// A triplet holds (v(c=-1), v(c=0), v(c=+1)) of one axis; after a forward transform the
+// same slots hold the moments of order 0, 1, 2 along that axis.
+
+// populations -> raw moments (sum v, sum c v, sum c^2 v)
+__device__ __forceinline__ void raw3(float &a, float &b, float &c) {
+    const float s = a + c, d = c - a;
+    a = s + b;
+    b = d;
+    c = s;
+}
+// raw -> central moments about u
+__device__ __forceinline__ void shift3(float &m0, float &m1, float &m2, float u) {
+    const float t = fmaf(u, m0, -2.0f * m1);
+    m1 = fmaf(-u, m0, m1);
+    m2 = fmaf(u, t, m2);
+}
+// central moments about u -> populations
+__device__ __forceinline__ void inv3(float &m0, float &m1, float &m2, float u) {
+    const float r1 = fmaf(u, m0, m1);
+    const float r2 = fmaf(u, m1 + r1, m2);
+    const float hr = 0.5f * r1;
+    const float b = m0 - r2;
+    m0 = fmaf(0.5f, r2, -hr);
+    m2 = fmaf(0.5f, r2, hr);
+    m1 = b;
+}
+
+// base index of the k-th triplet along the axis with stride S (1: x, 3: y, 9: z)
+template <int S> __host__ __device__ constexpr int tri_base(int k) {
+    return S == 1 ? 3 * k : S == 3 ? (k % 3) + 9 * (k / 3) : k;
+}
+
+template <int S> __device__ __forceinline__ void sweep_raw(float (&h)[27]) {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) raw3(h[tri_base<S>(k)], h[tri_base<S>(k) + S], h[tri_base<S>(k) + 2 * S]);
+}
+template <int S> __device__ __forceinline__ void sweep_shift(float (&h)[27], float u) {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) shift3(h[tri_base<S>(k)], h[tri_base<S>(k) + S], h[tri_base<S>(k) + 2 * S], u);
+}
+template <int S> __device__ __forceinline__ void sweep_inv(float (&h)[27], float u) {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) inv3(h[tri_base<S>(k)], h[tri_base<S>(k) + S], h[tri_base<S>(k) + 2 * S], u);
+}
+
+// ---- collision (Eqs. 4-5) ---------------------------------------------------------------
+// In: h = streamed deviations f*_i - w_i rho0 (tensor order), F = total force.
+// Out: h = post-collision deviations; rho, u = density and Guo-shifted velocity.
+//
+// With kappa the central moments of f about u, kappa_eq = rho m_p m_q m_r (m = 1, 0, 1/3)
+// and R^F the force moments, every moment is relaxed as
+//     kappa' = kappa - omega (kappa - kappa_eq) + (1 - omega/2) R^F,
+// the diagonal second-order moments through their trace (omega_b) and two deviators
+// (omega_s).  The transform acts on the deviations h; the rest-weight part w rho0 has the
+// central moments rho0 t_p(u_x) t_q(u_y) t_r(u_z), t = (1, -u, 1/3 + u^2), so with
+// e = kappa_eq - rho0 t t t the update reads h' = e + (1 - omega)(h - e) + (1 - omega/2) R^F
+// in moment space, every term small; the e are expanded to avoid cancellation.
+__device__ __forceinline__ void collide(float (&h)[27], float Fx, float Fy, float Fz, const StepParams &P,
+                                        float &rho, float &ux, float &uy, float &uz) {
+    sweep_raw<1>(h);
+    sweep_raw<3>(h);
+    sweep_raw<9>(h);
+    const float rhop = h[K(0, 0, 0)];            // rho - rho0
+    rho = P.rho0 + rhop;
+    const float inv = __frcp_rn(rho);
+    ux = (h[K(1, 0, 0)] + 0.5f * Fx) * inv;
+    uy = (h[K(0, 1, 0)] + 0.5f * Fy) * inv;
+    uz = (h[K(0, 0, 1)] + 0.5f * Fz) * inv;
+    sweep_shift<1>(h, ux);
+    sweep_shift<3>(h, uy);
+    sweep_shift<9>(h, uz);
+
+    const float r0 = P.rho0;
+    const float ux2 = ux * ux, uy2 = uy * uy, uz2 = uz * uz;
+    const float tx = (1.0f / 3.0f) + ux2, ty = (1.0f / 3.0f) + uy2, tz = (1.0f / 3.0f) + uz2;
+    const float third = 1.0f / 3.0f, ninth = 1.0f / 9.0f;
+
+    // order 1: conserved, kappa'_100 = F_x / 2  (stored as deviation moment rho0 u_x + F_x/2)
+    h[K(1, 0, 0)] = fmaf(r0, ux, 0.5f * Fx);
+    h[K(0, 1, 0)] = fmaf(r0, uy, 0.5f * Fy);
+    h[K(0, 0, 1)] = fmaf(r0, uz, 0.5f * Fz);
+
+    // order 2, off-diagonal (shear)
+#define RELAX(idx, e, r) { const float e_ = (e); h[idx] = fmaf((r), h[idx] - e_, e_); }
+#define RELAXF(idx, e, r, fr) { const float e_ = (e); h[idx] = fmaf((r), h[idx] - e_, e_ + (fr)); }
+    RELAX(K(1, 1, 0), -r0 * ux * uy, P.rs);
+    RELAX(K(1, 0, 1), -r0 * ux * uz, P.rs);
+    RELAX(K(0, 1, 1), -r0 * uy * uz, P.rs);
+    // order 2, diagonal: trace (bulk) and two deviators (shear)
+    {
+        const float e200 = fmaf(third, rhop, -r0 * ux2);
+        const float e020 = fmaf(third, rhop, -r0 * uy2);
+        const float e002 = fmaf(third, rhop, -r0 * uz2);
+        const float a = h[K(2, 0, 0)] - e200, b = h[K(0, 2, 0)] - e020, c = h[K(0, 0, 2)] - e002;
+        const float tr = P.rb * (a + b + c);
+        const float d1 = P.rs * (a - b);
+        const float d2 = P.rs * (a - c);
+        h[K(2, 0, 0)] = e200 + third * (tr + d1 + d2);
+        h[K(0, 2, 0)] = e020 + third * (tr - 2.0f * d1 + d2);
+        h[K(0, 0, 2)] = e002 + third * (tr + d1 - 2.0f * d2);
+    }
+    // order 3 (force moments F/3 on 210, 201, 120, 021, 102, 012)
+    RELAXF(K(2, 1, 0), r0 * uy * tx, P.r3, P.q3 * third * Fy);
+    RELAXF(K(2, 0, 1), r0 * uz * tx, P.r3, P.q3 * third * Fz);
+    RELAXF(K(1, 2, 0), r0 * ux * ty, P.r3, P.q3 * third * Fx);
+    RELAXF(K(0, 2, 1), r0 * uz * ty, P.r3, P.q3 * third * Fz);
+    RELAXF(K(1, 0, 2), r0 * ux * tz, P.r3, P.q3 * third * Fx);
+    RELAXF(K(0, 1, 2), r0 * uy * tz, P.r3, P.q3 * third * Fy);
+    RELAX(K(1, 1, 1), r0 * ux * uy * uz, P.r3);
+    // order 4
+    RELAX(K(2, 2, 0), fmaf(ninth, rhop, -r0 * fmaf(ux2, uy2, third * (ux2 + uy2))), P.r4);
+    RELAX(K(2, 0, 2), fmaf(ninth, rhop, -r0 * fmaf(ux2, uz2, third * (ux2 + uz2))), P.r4);
+    RELAX(K(0, 2, 2), fmaf(ninth, rhop, -r0 * fmaf(uy2, uz2, third * (uy2 + uz2))), P.r4);
+    RELAX(K(2, 1, 1), -r0 * tx * uy * uz, P.r4);
+    RELAX(K(1, 2, 1), -r0 * ty * ux * uz, P.r4);
+    RELAX(K(1, 1, 2), -r0 * tz * ux * uy, P.r4);
+    // order 5 (force moments F/9 on 221, 212, 122)
+    RELAXF(K(2, 2, 1), r0 * uz * tx * ty, P.r5, P.q5 * ninth * Fz);
+    RELAXF(K(2, 1, 2), r0 * uy * tx * tz, P.r5, P.q5 * ninth * Fy);
+    RELAXF(K(1, 2, 2), r0 * ux * ty * tz, P.r5, P.q5 * ninth * Fx);
+    // order 6
+    {
+        const float s1 = ux2 + uy2 + uz2;
+        const float s2 = ux2 * uy2 + ux2 * uz2 + uy2 * uz2;
+        const float s3 = ux2 * uy2 * uz2;
+        RELAX(K(2, 2, 2), (1.0f / 27.0f) * rhop - r0 * (ninth * s1 + third * s2 + s3), P.r6);
+    }
+#undef RELAX
+#undef RELAXF
+    sweep_inv<9>(h, uz);
+    sweep_inv<3>(h, uy);
+    sweep_inv<1>(h, ux);
+}
+
+}  // namespace lbm

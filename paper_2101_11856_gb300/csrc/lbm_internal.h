@@ -1,0 +1,26 @@
+// Launchers of the CUDA kernels (lbm_kernels.cu), used by the C-ABI host code (lbm_api.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "lbm_device.cuh"
+
+namespace lbm {
+
+cudaError_t launch_step(int storage, const StepParams &P, bool band, cudaStream_t st);
+cudaError_t launch_init(int storage, const StepParams &P, const float *rho, const float *u, cudaStream_t st);
+long long macro_blocks(const StepParams &P);
+cudaError_t launch_macro(int storage, const StepParams &P, bool band, int force_on, float *rho, float *u, float *f,
+                         double *partial, int *nonfinite, cudaStream_t st);
+cudaError_t launch_finalize(const double *partial, long long n, int count, double *out, cudaStream_t st);
+cudaError_t launch_band_moments(int storage, const StepParams &P, const int *band_cell, float *band_rho, float *band_u,
+                                cudaStream_t st);
+cudaError_t launch_ib_interp(long long S, long long nband, const float *X, const float *area, const float *ub,
+                             const int *corner_band, const float *band_rho, const float *band_u, float *g,
+                             cudaStream_t st);
+cudaError_t launch_ib_spread(long long S, long long nband, const float *X, const float *g, const int *base_nbr,
+                             const int *cstart, const int *ccount, float *bandF, cudaStream_t st);
+int force_sum_blocks();
+cudaError_t launch_sum_forces(long long S, const float *g, double *partial, cudaStream_t st);
+
+}  // namespace lbm

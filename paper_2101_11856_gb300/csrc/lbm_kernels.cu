@@ -1,0 +1,497 @@
+// CUDA kernels of the GB300 path: the fused AA-pattern D3Q27 step, its initialisation,
+// the immersed-boundary band / interpolation / spreading kernels, and the diagnostics.
+//
+// AA pattern (in-place streaming, one population array): with A[d][cell] the storage,
+//  * after an even step (and at t = 0) A[opp(d)][x] holds the post-collision f_d(x);
+//  * an odd step t ("neighbour" step) pulls f*_d(x) = A[opp(d)][x - c_d] and writes the
+//    new f_d(x) to A[d][x + c_d];
+//  * an even step ("local" step) reads f*_d(x) = A[d][x] and writes f_d(x) to A[opp(d)][x].
+// Each node reads and writes the same 27 slots, so one array suffices and no two threads
+// touch a slot.  A population whose source lies behind a non-periodic face is found in
+// the node's own slot A[d][x] (the previous step wrote the reflected value there), which
+// gives half-way bounce-back (the paper's Algorithm 1) and the moving-wall inlet; the
+// outlet reads a ping-pong copy of the outlet plane's previous post-collision values.
+#include "lbm_device.cuh"
+#include "lbm_internal.h"
+
+namespace lbm {
+
+static constexpr int STEP_THREADS = 256;
+
+// ---- loads of the streamed populations f*(x) ------------------------------------------
+
+template <typename St, bool NB>
+__device__ __forceinline__ void load_interior(const StepParams &P, int cell, float (&h)[27]) {
+    const St *A = static_cast<const St *>(P.f);
+    const long long pl = P.g.plane;
+#pragma unroll
+    for (int d = 0; d < 27; ++d) {
+        if (NB) {
+            const int off = cx(d) + cy(d) * P.g.nx + cz(d) * P.g.nxy;
+            h[d] = Store<St>::ld(A + opp(d) * pl + (cell - off));
+        } else {
+            h[d] = Store<St>::ld(A + d * pl + cell);
+        }
+    }
+}
+
+template <typename St, bool NB>
+__device__ __forceinline__ void load_general(const StepParams &P, int x, int y, int z, int cell, float (&h)[27]) {
+    const St *A = static_cast<const St *>(P.f);
+    const St *B = static_cast<const St *>(P.outlet);
+    const long long pl = P.g.plane;
+    const int rpar = (int)((P.t - 1) & 1);
+    const bool inlet_node = (x == 0) && P.g.face[0] == FACE_INLET;
+    const float uw = inlet_node ? inlet_velocity(P, y, z) : 0.0f;
+#pragma unroll
+    for (int d = 0; d < 27; ++d) {
+        const Nbr n = neighbour<-1>(P.g, d, x, y, z);
+        float v;
+        if (n.kind == 0) {
+            v = NB ? Store<St>::ld(A + opp(d) * pl + n.idx) : Store<St>::ld(A + d * pl + cell);
+        } else if (n.kind & CROSS_NOSLIP) {
+            v = Store<St>::ld(A + d * pl + cell);
+        } else if (n.kind & CROSS_INLET) {
+            // moving wall: f*_d = f_opp(d) + 2 w_d rho0 (c_d . u_w) / c_s^2
+            v = Store<St>::ld(A + d * pl + cell) + 6.0f * wgt(d) * P.rho0 * (float)cx(d) * uw;
+        } else {
+            // outlet ghost: post-collision f_d of (nx-1, y - c_dy, z - c_dz) of the previous step
+            v = Store<St>::ld(B + ((long long)(rpar * 9 + d / 3) * P.g.nyz + n.y + P.g.ny * n.z));
+        }
+        h[d] = v;
+    }
+}
+
+// ---- stores of the post-collision populations ------------------------------------------
+
+template <typename St, bool NB>
+__device__ __forceinline__ void store_interior(const StepParams &P, int cell, const float (&h)[27]) {
+    St *A = static_cast<St *>(P.f);
+    const long long pl = P.g.plane;
+#pragma unroll
+    for (int d = 0; d < 27; ++d) {
+        if (NB) {
+            const int off = cx(d) + cy(d) * P.g.nx + cz(d) * P.g.nxy;
+            Store<St>::st(A + d * pl + (cell + off), h[d]);
+        } else {
+            Store<St>::st(A + opp(d) * pl + cell, h[d]);
+        }
+    }
+}
+
+template <typename St, bool NB>
+__device__ __forceinline__ void store_general(const StepParams &P, int x, int y, int z, int cell, const float (&h)[27]) {
+    St *A = static_cast<St *>(P.f);
+    const long long pl = P.g.plane;
+#pragma unroll
+    for (int d = 0; d < 27; ++d) {
+        if (NB) {
+            const Nbr n = neighbour<+1>(P.g, d, x, y, z);
+            if (n.kind == 0) Store<St>::st(A + d * pl + n.idx, h[d]);
+            else Store<St>::st(A + opp(d) * pl + cell, h[d]);
+        } else {
+            Store<St>::st(A + opp(d) * pl + cell, h[d]);
+        }
+    }
+    if (x == P.g.nx - 1 && P.g.face[1] == FACE_OUTLET) {
+        St *B = static_cast<St *>(P.outlet);
+        const int wpar = (int)(P.t & 1);
+#pragma unroll
+        for (int d = 0; d < 27; d += 3)   // the nine directions with c_x = -1
+            Store<St>::st(B + ((long long)(wpar * 9 + d / 3) * P.g.nyz + y + P.g.ny * z), h[d]);
+    }
+}
+
+__device__ __forceinline__ void decompose(const Geometry &g, int cell, int &x, int &y, int &z) {
+    z = cell / g.nxy;
+    const int r = cell - z * g.nxy;
+    y = r / g.nx;
+    x = r - y * g.nx;
+}
+
+// ---- the fused step ---------------------------------------------------------------------
+// One thread per cell: pull the 27 streamed populations (with the face rules), add the
+// band's immersed-boundary force, collide in registers, store in place.  Warps whose 32
+// cells are all interior take the constant-offset path.
+template <typename St, bool NB, bool BAND>
+__global__ void __launch_bounds__(STEP_THREADS, 2) k_step(StepParams P) {
+    const int cell = blockIdx.x * STEP_THREADS + threadIdx.x;
+    const bool active = cell < P.g.ncell;
+    int x = 0, y = 0, z = 0;
+    if (active) decompose(P.g, cell, x, y, z);
+    const bool interior = active && x >= 1 && x <= P.g.nx - 2 && y >= 1 && y <= P.g.ny - 2 &&
+                          z >= 1 && z <= P.g.nz - 2;
+    const bool fast = __all_sync(0xffffffffu, interior);
+    if (!active) return;
+
+    float h[27];
+    if (fast) load_interior<St, NB>(P, cell, h);
+    else load_general<St, NB>(P, x, y, z, cell, h);
+
+    float Fx = P.Fx, Fy = P.Fy, Fz = P.Fz;
+    if (BAND) {
+        const uint32_t mask = P.tile_mask[cell >> 5];
+        const int lane = cell & 31;
+        if ((mask >> lane) & 1u) {
+            const long long b = P.tile_off[cell >> 5] + __popc(mask & ((1u << lane) - 1u));
+            Fx += P.bandF[b];
+            Fy += P.bandF[P.nband + b];
+            Fz += P.bandF[2 * P.nband + b];
+        }
+    }
+    float rho, ux, uy, uz;
+    collide(h, Fx, Fy, Fz, P, rho, ux, uy, uz);
+
+    if (fast) store_interior<St, NB>(P, cell, h);
+    else store_general<St, NB>(P, x, y, z, cell, h);
+}
+
+// ---- initialisation: f = f_eq(rho, u), stored as the post-collision state of t = 0 ------
+
+__device__ __forceinline__ float phi1(int c, float u) {
+    return c == 0 ? (2.0f / 3.0f - u * u) : 0.5f * ((1.0f / 3.0f) + u * u + (float)c * u);
+}
+// deviation of the product-form equilibrium from w rho0, expanded to keep precision
+__device__ __forceinline__ float phi_dev(int c, float u) {
+    // phi(c, u) - w1(c)
+    return c == 0 ? -u * u : 0.5f * (u * u + (float)c * u);
+}
+
+template <typename St>
+__global__ void k_init(StepParams P, const float *__restrict__ rho, const float *__restrict__ u) {
+    const int cell = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= P.g.ncell) return;
+    const float r = rho[cell];
+    const float ux = u[cell], uy = u[P.g.ncell + cell], uz = u[2 * P.g.ncell + cell];
+    St *A = static_cast<St *>(P.f);
+    int x, y, z;
+    decompose(P.g, cell, x, y, z);
+#pragma unroll
+    for (int d = 0; d < 27; ++d) {
+        // f = r prod phi = r prod (w1 + dphi); h = f - rho0 w
+        const float wx = w1(cx(d)), wy = w1(cy(d)), wz = w1(cz(d));
+        const float px = phi_dev(cx(d), ux), py = phi_dev(cy(d), uy), pz = phi_dev(cz(d), uz);
+        // prod(w + p) - prod(w) expanded
+        const float dprod = px * wy * wz + wx * py * wz + wx * wy * pz + px * py * wz + px * wy * pz +
+                            wx * py * pz + px * py * pz;
+        const float hv = (r - P.rho0) * wgt(d) + r * dprod;
+        Store<St>::st(A + opp(d) * P.g.plane + cell, hv);
+        if (x == P.g.nx - 1 && P.g.face[1] == FACE_OUTLET && cx(d) == -1) {
+            St *B = static_cast<St *>(P.outlet);
+            Store<St>::st(B + ((long long)(d / 3) * P.g.nyz + y + P.g.ny * z), hv);
+        }
+    }
+}
+
+// ---- post-collision populations of the current time (canonical layout) ----------------
+
+template <typename St, bool AFTER_NB>
+__device__ __forceinline__ void load_post(const StepParams &P, int x, int y, int z, int cell, float (&h)[27]) {
+    const St *A = static_cast<const St *>(P.f);
+    const long long pl = P.g.plane;
+#pragma unroll
+    for (int d = 0; d < 27; ++d) {
+        if (AFTER_NB) {
+            const Nbr n = neighbour<+1>(P.g, d, x, y, z);
+            h[d] = n.kind == 0 ? Store<St>::ld(A + d * pl + n.idx) : Store<St>::ld(A + opp(d) * pl + cell);
+        } else {
+            h[d] = Store<St>::ld(A + opp(d) * pl + cell);
+        }
+    }
+}
+
+// per-cell rho and Guo-shifted u of the last collision, optional field output and FP64
+// block partial sums (mass, momentum) for the deterministic global reduction
+template <typename St, bool AFTER_NB, bool BAND>
+__global__ void __launch_bounds__(256) k_macro(StepParams P, int force_on, float *__restrict__ rho_out,
+                                               float *__restrict__ u_out, float *__restrict__ f_out,
+                                               double *__restrict__ partial, int *__restrict__ nonfinite) {
+    const int cell = blockIdx.x * blockDim.x + threadIdx.x;
+    double m = 0.0, jx = 0.0, jy = 0.0, jz = 0.0;
+    if (cell < P.g.ncell) {
+        int x, y, z;
+        decompose(P.g, cell, x, y, z);
+        float h[27];
+        load_post<St, AFTER_NB>(P, x, y, z, cell, h);
+        if (f_out) {
+            const float r0 = P.rho0;
+#pragma unroll
+            for (int d = 0; d < 27; ++d) f_out[(long long)d * P.g.ncell + cell] = h[d] + wgt(d) * r0;
+        }
+        float rp = 0.0f, px = 0.0f, py = 0.0f, pz = 0.0f;
+#pragma unroll
+        for (int d = 0; d < 27; ++d) {
+            rp += h[d];
+            if (cx(d)) px += cx(d) * h[d];
+            if (cy(d)) py += cy(d) * h[d];
+            if (cz(d)) pz += cz(d) * h[d];
+        }
+        float Fx = 0.0f, Fy = 0.0f, Fz = 0.0f;
+        if (force_on) {
+            Fx = P.Fx; Fy = P.Fy; Fz = P.Fz;
+            if (BAND) {
+                const uint32_t mask = P.tile_mask[cell >> 5];
+                const int lane = cell & 31;
+                if ((mask >> lane) & 1u) {
+                    const long long b = P.tile_off[cell >> 5] + __popc(mask & ((1u << lane) - 1u));
+                    Fx += P.bandF[b];
+                    Fy += P.bandF[P.nband + b];
+                    Fz += P.bandF[2 * P.nband + b];
+                }
+            }
+        }
+        // post-collision momentum is j + F, so rho u = sum c f_post - F/2
+        const float rho = P.rho0 + rp;
+        const float jxs = px - 0.5f * Fx, jys = py - 0.5f * Fy, jzs = pz - 0.5f * Fz;
+        const float inv = 1.0f / rho;
+        if (rho_out) rho_out[cell] = rho;
+        if (u_out) {
+            u_out[cell] = jxs * inv;
+            u_out[P.g.ncell + cell] = jys * inv;
+            u_out[2 * P.g.ncell + cell] = jzs * inv;
+        }
+        if (nonfinite && !(isfinite(rho) && isfinite(jxs * inv) && isfinite(jys * inv) && isfinite(jzs * inv)))
+            atomicOr(nonfinite, 1);
+        m = (double)rho;
+        jx = (double)jxs;
+        jy = (double)jys;
+        jz = (double)jzs;
+    }
+    if (partial) {
+        // fixed-order block tree reduction in FP64
+        __shared__ double s[4][256];
+        s[0][threadIdx.x] = m; s[1][threadIdx.x] = jx; s[2][threadIdx.x] = jy; s[3][threadIdx.x] = jz;
+        __syncthreads();
+        for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+            if (threadIdx.x < w) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) s[k][threadIdx.x] += s[k][threadIdx.x + w];
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) partial[(long long)k * gridDim.x + blockIdx.x] = s[k][0];
+        }
+    }
+}
+
+// sum `count` rows of `n` doubles each (row k at partial + k * n) in a fixed order
+__global__ void k_finalize(const double *__restrict__ partial, long long n, int count, double *__restrict__ out) {
+    __shared__ double s[256];
+    for (int k = 0; k < count; ++k) {
+        double acc = 0.0;
+        for (long long i = threadIdx.x; i < n; i += blockDim.x) acc += partial[(long long)k * n + i];
+        s[threadIdx.x] = acc;
+        __syncthreads();
+        for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+            if (threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) out[k] = s[0];
+        __syncthreads();
+    }
+}
+
+// ---- immersed boundary ---------------------------------------------------------------
+
+// band moments: rho* and the pre-IB velocity (j + F_body/2)/rho* at every band node
+template <typename St, bool NB>
+__global__ void __launch_bounds__(256) k_band_moments(StepParams P, const int *__restrict__ band_cell,
+                                                      float *__restrict__ band_rho, float *__restrict__ band_u) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= P.nband) return;
+    const int cell = band_cell[k];
+    int x, y, z;
+    decompose(P.g, cell, x, y, z);
+    float h[27];
+    load_general<St, NB>(P, x, y, z, cell, h);
+    float rp = 0.0f, px = 0.0f, py = 0.0f, pz = 0.0f;
+#pragma unroll
+    for (int d = 0; d < 27; ++d) {
+        rp += h[d];
+        if (cx(d)) px += cx(d) * h[d];
+        if (cy(d)) py += cy(d) * h[d];
+        if (cz(d)) pz += cz(d) * h[d];
+    }
+    const float rho = P.rho0 + rp;
+    const float inv = 1.0f / rho;
+    band_rho[k] = rho;
+    band_u[k] = (px + 0.5f * P.Fx) * inv;
+    band_u[P.nband + k] = (py + 0.5f * P.Fy) * inv;
+    band_u[2 * P.nband + k] = (pz + 0.5f * P.Fz) * inv;
+}
+
+// trilinear weight of corner c (bit 0: x, bit 1: y, bit 2: z) for fractions (wx, wy, wz)
+__device__ __forceinline__ float corner_weight(int c, float wx, float wy, float wz) {
+    return ((c & 1) ? wx : 1.0f - wx) * ((c & 2) ? wy : 1.0f - wy) * ((c & 4) ? wz : 1.0f - wz);
+}
+
+// interpolation (Eq. 6) and penalty force (Eq. 7) per sample
+__global__ void __launch_bounds__(256) k_ib_interp(long long S, long long nband, const float *__restrict__ X,
+                                                   const float *__restrict__ area, const float *__restrict__ ub,
+                                                   const int *__restrict__ corner_band, const float *__restrict__ band_rho,
+                                                   const float *__restrict__ band_u, float *__restrict__ g) {
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    const float x = X[s], y = X[S + s], z = X[2 * S + s];
+    const float wx = x - floorf(x), wy = y - floorf(y), wz = z - floorf(z);
+    float rs = 0.0f, us = 0.0f, vs = 0.0f, ws = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const int b = corner_band[(long long)c * S + s];
+        const float K = corner_weight(c, wx, wy, wz);
+        rs = fmaf(K, band_rho[b], rs);
+        us = fmaf(K, band_u[b], us);
+        vs = fmaf(K, band_u[nband + b], vs);
+        ws = fmaf(K, band_u[2 * nband + b], ws);
+    }
+    const float a = rs * area[s];
+    g[s] = a * (ub[s] - us);
+    g[S + s] = a * (ub[S + s] - vs);
+    g[2 * S + s] = a * (ub[2 * S + s] - ws);
+}
+
+// spreading (Eq. 8) as a deterministic gather: band node k sums K g over the samples whose
+// base cell is x_k - c for the 8 corners c, in sample order (samples sorted by base cell)
+__global__ void __launch_bounds__(256) k_ib_spread(long long S, long long nband, const float *__restrict__ X,
+                                                   const float *__restrict__ g, const int *__restrict__ base_nbr,
+                                                   const int *__restrict__ cstart, const int *__restrict__ ccount,
+                                                   float *__restrict__ bandF) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nband) return;
+    float fx = 0.0f, fy = 0.0f, fz = 0.0f;
+#pragma unroll 1
+    for (int c = 0; c < 8; ++c) {
+        const int b = base_nbr[(long long)c * nband + k];
+        if (b < 0) continue;
+        const int s0 = cstart[b], s1 = s0 + ccount[b];
+        for (int s = s0; s < s1; ++s) {
+            const float x = X[s], y = X[S + s], z = X[2 * S + s];
+            const float K = corner_weight(c, x - floorf(x), y - floorf(y), z - floorf(z));
+            fx = fmaf(K, g[s], fx);
+            fy = fmaf(K, g[S + s], fy);
+            fz = fmaf(K, g[2 * S + s], fz);
+        }
+    }
+    bandF[k] = fx;
+    bandF[nband + k] = fy;
+    bandF[2 * nband + k] = fz;
+}
+
+// FP64 block partial sums of the penalty forces (drag = -sum g)
+__global__ void __launch_bounds__(256) k_sum_forces(long long S, const float *__restrict__ g, double *__restrict__ partial) {
+    __shared__ double s[3][256];
+    double a[3] = {0.0, 0.0, 0.0};
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < S; i += (long long)gridDim.x * blockDim.x) {
+        a[0] += g[i];
+        a[1] += g[S + i];
+        a[2] += g[2 * S + i];
+    }
+    for (int k = 0; k < 3; ++k) s[k][threadIdx.x] = a[k];
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+            for (int k = 0; k < 3; ++k) s[k][threadIdx.x] += s[k][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 3; ++k) partial[(long long)k * gridDim.x + blockIdx.x] = s[k][0];
+}
+
+// ---- host launchers ------------------------------------------------------------------
+
+static inline unsigned blocks_for(long long n, int threads) { return (unsigned)((n + threads - 1) / threads); }
+
+template <typename St>
+static cudaError_t launch_step_t(const StepParams &P, bool band, cudaStream_t st) {
+    const bool nb = (P.t & 1) != 0;
+    const unsigned grid = blocks_for(P.g.ncell, STEP_THREADS);
+    if (nb) {
+        if (band) k_step<St, true, true><<<grid, STEP_THREADS, 0, st>>>(P);
+        else k_step<St, true, false><<<grid, STEP_THREADS, 0, st>>>(P);
+    } else {
+        if (band) k_step<St, false, true><<<grid, STEP_THREADS, 0, st>>>(P);
+        else k_step<St, false, false><<<grid, STEP_THREADS, 0, st>>>(P);
+    }
+    return cudaGetLastError();
+}
+
+template <typename F>
+static cudaError_t dispatch_storage(int storage, F &&fn) {
+    switch (storage) {
+        case 0: return fn(float{});
+        case 1: return fn(__half{});
+        default: return fn(__nv_bfloat16{});
+    }
+}
+
+cudaError_t launch_step(int storage, const StepParams &P, bool band, cudaStream_t st) {
+    return dispatch_storage(storage, [&](auto tag) { return launch_step_t<decltype(tag)>(P, band, st); });
+}
+
+cudaError_t launch_init(int storage, const StepParams &P, const float *rho, const float *u, cudaStream_t st) {
+    return dispatch_storage(storage, [&](auto tag) {
+        k_init<decltype(tag)><<<blocks_for(P.g.ncell, 256), 256, 0, st>>>(P, rho, u);
+        return cudaGetLastError();
+    });
+}
+
+long long macro_blocks(const StepParams &P) { return blocks_for(P.g.ncell, 256); }
+
+cudaError_t launch_macro(int storage, const StepParams &P, bool band, int force_on, float *rho, float *u, float *f,
+                         double *partial, int *nonfinite, cudaStream_t st) {
+    // the state after step t was written by a neighbour step when t is odd
+    const bool after_nb = (P.t & 1) != 0;
+    return dispatch_storage(storage, [&](auto tag) {
+        using St = decltype(tag);
+        const unsigned grid = blocks_for(P.g.ncell, 256);
+        if (after_nb) {
+            if (band) k_macro<St, true, true><<<grid, 256, 0, st>>>(P, force_on, rho, u, f, partial, nonfinite);
+            else k_macro<St, true, false><<<grid, 256, 0, st>>>(P, force_on, rho, u, f, partial, nonfinite);
+        } else {
+            if (band) k_macro<St, false, true><<<grid, 256, 0, st>>>(P, force_on, rho, u, f, partial, nonfinite);
+            else k_macro<St, false, false><<<grid, 256, 0, st>>>(P, force_on, rho, u, f, partial, nonfinite);
+        }
+        return cudaGetLastError();
+    });
+}
+
+cudaError_t launch_finalize(const double *partial, long long n, int count, double *out, cudaStream_t st) {
+    k_finalize<<<1, 256, 0, st>>>(partial, n, count, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_band_moments(int storage, const StepParams &P, const int *band_cell, float *band_rho, float *band_u,
+                                cudaStream_t st) {
+    const bool nb = (P.t & 1) != 0;
+    return dispatch_storage(storage, [&](auto tag) {
+        using St = decltype(tag);
+        const unsigned grid = blocks_for(P.nband, 256);
+        if (nb) k_band_moments<St, true><<<grid, 256, 0, st>>>(P, band_cell, band_rho, band_u);
+        else k_band_moments<St, false><<<grid, 256, 0, st>>>(P, band_cell, band_rho, band_u);
+        return cudaGetLastError();
+    });
+}
+
+cudaError_t launch_ib_interp(long long S, long long nband, const float *X, const float *area, const float *ub,
+                             const int *corner_band, const float *band_rho, const float *band_u, float *g,
+                             cudaStream_t st) {
+    k_ib_interp<<<blocks_for(S, 256), 256, 0, st>>>(S, nband, X, area, ub, corner_band, band_rho, band_u, g);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ib_spread(long long S, long long nband, const float *X, const float *g, const int *base_nbr,
+                             const int *cstart, const int *ccount, float *bandF, cudaStream_t st) {
+    k_ib_spread<<<blocks_for(nband, 256), 256, 0, st>>>(S, nband, X, g, base_nbr, cstart, ccount, bandF);
+    return cudaGetLastError();
+}
+
+int force_sum_blocks() { return 1024; }
+
+cudaError_t launch_sum_forces(long long S, const float *g, double *partial, cudaStream_t st) {
+    k_sum_forces<<<force_sum_blocks(), 256, 0, st>>>(S, g, partial);
+    return cudaGetLastError();
+}
+
+}  // namespace lbm

@@ -1,0 +1,277 @@
+"""Thin ctypes binding of liblbm.so (include/lbm.h).
+
+Argument marshalling only: every step of the solver runs in the CUDA library.  The
+module-level functions carry the C names (``lbm_create``, ``lbm_step``, ...); ``Solver``
+bundles them for convenience.  Arrays may be numpy arrays (host) or torch tensors (host
+or CUDA); they are passed to the library by pointer.  The library is required: importing
+works without it, but the first call raises if ``liblbm.so`` has not been built.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "liblbm.so")
+_lib = None
+
+LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ETIMEOUT, LBM_ESTATE = 0, -1, -2, -3, -4, -5, -6
+STORAGE = {"f32": 0, "f16": 1, "bf16": 2}
+FACE = {"periodic": 0, "noslip": 1, "inlet": 2, "outlet": 3}
+KERNEL_KINDS = ("step", "band", "interp", "spread", "other")
+
+
+class LBMError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"lbm error {code}: {msg}")
+        self.code = code
+
+
+class lbm_config(C.Structure):
+    _fields_ = [("storage", C.c_int), ("face_type", C.c_int * 6), ("rho0", C.c_double), ("u_in", C.c_double),
+                ("inlet_noise", C.c_double), ("seed", C.c_ulonglong), ("inflow_coef", C.c_double * 16),
+                ("omega_bulk", C.c_double), ("omega_hi", C.c_double * 4), ("cuda_stream", C.c_void_p)]
+
+
+_SIGS = {
+    "lbm_config_default": (None, [C.POINTER(lbm_config)]),
+    "lbm_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_int, C.c_double,
+                             C.POINTER(C.c_double), C.POINTER(lbm_config)]),
+    "lbm_destroy": (C.c_int, [C.c_void_p]),
+    "lbm_set_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "lbm_set_solids": (C.c_int, [C.c_void_p, C.c_void_p, C.c_longlong, C.c_void_p, C.c_void_p]),
+    "lbm_step": (C.c_int, [C.c_void_p, C.c_int]),
+    "lbm_macroscopic": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "lbm_reductions": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "lbm_ib_forces": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "lbm_populations": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "lbm_velocity": (C.c_int, [C.c_int, C.POINTER(C.c_int)]),
+    "lbm_time": (C.c_longlong, [C.c_void_p]),
+    "lbm_check": (C.c_int, [C.c_void_p]),
+    "lbm_synchronize": (C.c_int, [C.c_void_p, C.c_double]),
+    "lbm_save": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_size_t)]),
+    "lbm_load": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
+    "lbm_profile": (C.c_int, [C.c_void_p, C.c_int]),
+    "lbm_kernel_times": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
+    "lbm_band_size": (C.c_longlong, [C.c_void_p]),
+    "lbm_last_error": (C.c_char_p, [C.c_void_p]),
+}
+
+
+def library(path: str | None = None):
+    """Load liblbm.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        p = path or _LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"{p} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'`")
+        lib = C.CDLL(p)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _check(rc, ctx=None):
+    if rc != LBM_OK:
+        msg = library().lbm_last_error(ctx)
+        raise LBMError(rc, msg.decode() if msg else "")
+
+
+def _ptr(a):
+    """(pointer, keepalive) of a float32 array: numpy (host) or torch tensor (host or CUDA)."""
+    if a is None:
+        return None, None
+    if hasattr(a, "data_ptr"):           # torch tensor
+        import torch
+        t = a.detach()
+        if t.dtype != torch.float32 or not t.is_contiguous():
+            t = t.to(torch.float32).contiguous()
+        return C.c_void_p(t.data_ptr()), t
+    arr = np.ascontiguousarray(a, dtype=np.float32)
+    return C.c_void_p(arr.ctypes.data), arr
+
+
+# ---- the C functions under their own names -------------------------------------------
+
+def lbm_config_default() -> lbm_config:
+    cfg = lbm_config()
+    library().lbm_config_default(C.byref(cfg))
+    return cfg
+
+
+def lbm_create(nx, ny, nz, nu, forcing=(0.0, 0.0, 0.0), cfg: lbm_config | None = None):
+    h = C.c_void_p()
+    f = (C.c_double * 3)(*forcing)
+    _check(library().lbm_create(C.byref(h), nx, ny, nz, nu, f, C.byref(cfg) if cfg is not None else None))
+    return h
+
+
+def lbm_destroy(h):
+    return library().lbm_destroy(h)
+
+
+def lbm_set_state(h, rho, u):
+    pr, kr = _ptr(rho)
+    pu, ku = _ptr(u)
+    _check(library().lbm_set_state(h, pr, pu), h)
+
+
+def lbm_set_solids(h, samples, area=None, u_b=None):
+    count = 0 if samples is None else int(np.prod(samples.shape) // 3)
+    ps, ks = _ptr(samples)
+    pa, ka = _ptr(area)
+    pb, kb = _ptr(u_b)
+    _check(library().lbm_set_solids(h, ps, count, pa, pb), h)
+
+
+def lbm_step(h, n=1):
+    _check(library().lbm_step(h, int(n)), h)
+
+
+def lbm_macroscopic(h, rho, u):
+    pr, kr = _ptr(rho) if rho is not None else (None, None)
+    pu, ku = _ptr(u) if u is not None else (None, None)
+    _check(library().lbm_macroscopic(h, pr, pu), h)
+
+
+def lbm_reductions(h):
+    m = C.c_double()
+    mom = (C.c_double * 3)()
+    drag = (C.c_double * 3)()
+    _check(library().lbm_reductions(h, C.byref(m), mom, drag), h)
+    return m.value, np.array(mom[:]), np.array(drag[:])
+
+
+def lbm_ib_forces(h, out):
+    p, k = _ptr(out)
+    _check(library().lbm_ib_forces(h, p), h)
+
+
+def lbm_populations(h, out):
+    p, k = _ptr(out)
+    _check(library().lbm_populations(h, p), h)
+
+
+def lbm_velocity(i):
+    c = (C.c_int * 3)()
+    _check(library().lbm_velocity(i, c))
+    return tuple(c[:])
+
+
+def lbm_time(h):
+    return library().lbm_time(h)
+
+
+def lbm_check(h):
+    return library().lbm_check(h)
+
+
+def lbm_synchronize(h, timeout_s=0.0):
+    _check(library().lbm_synchronize(h, timeout_s), h)
+
+
+def lbm_save(h) -> bytes:
+    n = C.c_size_t(0)
+    _check(library().lbm_save(h, None, C.byref(n)), h)
+    buf = C.create_string_buffer(n.value)
+    _check(library().lbm_save(h, buf, C.byref(n)), h)
+    return buf.raw[: n.value]
+
+
+def lbm_load(h, data: bytes):
+    _check(library().lbm_load(h, data, len(data)), h)
+
+
+def lbm_profile(h, enable=True):
+    _check(library().lbm_profile(h, 1 if enable else 0), h)
+
+
+def lbm_kernel_times(h):
+    ms = (C.c_double * 5)()
+    n = (C.c_longlong * 5)()
+    _check(library().lbm_kernel_times(h, ms, n), h)
+    return {k: (ms[i], n[i]) for i, k in enumerate(KERNEL_KINDS)}
+
+
+def lbm_band_size(h):
+    return library().lbm_band_size(h)
+
+
+# ---- convenience wrapper -----------------------------------------------------------
+
+class Solver:
+    """One simulation on the current CUDA device (see include/lbm.h)."""
+
+    def __init__(self, nx, ny, nz, nu, forcing=(0.0, 0.0, 0.0), storage="f32", faces=("periodic",) * 6,
+                 rho0=1.0, u_in=0.0, noise=0.0, seed=2101, inflow_coef=None, omega_bulk=1.0,
+                 omega_hi=(1.0, 1.0, 1.0, 1.0), stream=None):
+        cfg = lbm_config_default()
+        cfg.storage = STORAGE[storage]
+        for k, t in enumerate(faces):
+            cfg.face_type[k] = FACE[t]
+        cfg.rho0, cfg.u_in, cfg.inlet_noise, cfg.seed = rho0, u_in, noise, seed
+        if inflow_coef is not None:
+            for k, v in enumerate(np.asarray(inflow_coef, dtype=np.float64).ravel()):
+                cfg.inflow_coef[k] = float(v)
+        cfg.omega_bulk = omega_bulk
+        for k in range(4):
+            cfg.omega_hi[k] = omega_hi[k]
+        if stream is None:
+            try:
+                import torch
+                if torch.cuda.is_available():
+                    stream = torch.cuda.current_stream().cuda_stream
+            except ImportError:
+                stream = None
+        cfg.cuda_stream = stream
+        self.shape = (nz, ny, nx)
+        self.N = nx * ny * nz
+        self.h = lbm_create(nx, ny, nz, nu, forcing, cfg)
+
+    def close(self):
+        if self.h:
+            lbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_state(self, rho, u):
+        lbm_set_state(self.h, rho, u)
+
+    def set_solids(self, X, area=None, u_b=None):
+        lbm_set_solids(self.h, X, area, u_b)
+
+    def step(self, n=1):
+        lbm_step(self.h, n)
+
+    def macroscopic(self):
+        """(rho (nz, ny, nx), u (3, nz, ny, nx)) as float32 numpy arrays."""
+        rho = np.empty(self.shape, np.float32)
+        u = np.empty((3,) + self.shape, np.float32)
+        lbm_macroscopic(self.h, rho, u)
+        return rho, u
+
+    def reductions(self):
+        return lbm_reductions(self.h)
+
+    def ib_forces(self, count):
+        g = np.empty((count, 3), np.float32)
+        lbm_ib_forces(self.h, g)
+        return g
+
+    def populations(self):
+        f = np.empty((27,) + self.shape, np.float32)
+        lbm_populations(self.h, f)
+        return f
+
+    @property
+    def time(self):
+        return lbm_time(self.h)

@@ -1,0 +1,74 @@
+"""The C-ABI library builds, loads without a GPU and exports every function include/lbm.h
+declares; the binding's structure matches the header (no GPU, no compute calls)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for hdr in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not hdr.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", hdr)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_ \*]*?\b(lbm_[a-z0-9_]+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2101_11856_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_api():
+    names = declared_functions()
+    for core in ("lbm_create", "lbm_destroy", "lbm_set_state", "lbm_set_solids", "lbm_step", "lbm_macroscopic",
+                 "lbm_reductions", "lbm_save", "lbm_load", "lbm_last_error"):
+        assert core in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_config_layout_matches_header(lib):
+    from paper_2101_11856_gb300 import lbm
+    cfg = lbm.lbm_config()
+    lib.lbm_config_default(ctypes.byref(cfg))
+    assert cfg.storage == 0 and list(cfg.face_type) == [0] * 6
+    assert cfg.rho0 == 1.0 and cfg.seed == 2101 and cfg.omega_bulk == 1.0 and list(cfg.omega_hi) == [1.0] * 4
+    assert cfg.cuda_stream is None
+
+
+def test_velocity_table_is_d3q27(lib):
+    from paper_2101_11856_gb300 import lbm
+    vel = {lbm.lbm_velocity(i) for i in range(27)}
+    assert vel == {(a, b, c) for a in (-1, 0, 1) for b in (-1, 0, 1) for c in (-1, 0, 1)}
+    with pytest.raises(lbm.LBMError):
+        lbm.lbm_velocity(27)
+
+
+def test_create_rejects_bad_arguments_without_touching_the_gpu(lib):
+    """Argument validation happens before any CUDA call."""
+    from paper_2101_11856_gb300 import lbm
+    cfg = lbm.lbm_config_default()
+    for args in ((0, 4, 4, 0.1), (4, 4, 4, 0.0), (4, 4, 4, -1.0), (4, 4, 4, float("nan"))):
+        with pytest.raises(lbm.LBMError) as e:
+            lbm.lbm_create(*args, cfg=cfg)
+        assert e.value.code == lbm.LBM_EINVAL
+    bad = lbm.lbm_config_default()
+    bad.face_type[0] = lbm.FACE["noslip"]            # -x no-slip with +x periodic
+    with pytest.raises(lbm.LBMError):
+        lbm.lbm_create(4, 4, 4, 0.1, cfg=bad)
+    bad = lbm.lbm_config_default()
+    bad.face_type[2], bad.face_type[3] = lbm.FACE["inlet"], lbm.FACE["noslip"]   # inlet on -y
+    with pytest.raises(lbm.LBMError):
+        lbm.lbm_create(4, 4, 4, 0.1, cfg=bad)

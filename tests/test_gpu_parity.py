@@ -1,0 +1,127 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on seeded inputs.
+
+Tolerances (FP32 arithmetic on deviations f - w rho0, FP64 oracle): relative L2 <= 1e-5 on
+rho and u after 100 steps of the Taylor-Green box (the stated bar); on populations after
+a few steps, max |df| <= 2e-7 (a few FP32 ulps of the O(1) populations over the
+~600-operation collision).  FP16/BF16 storage has no pass bar beyond stability; its
+error is bounded loosely and reported.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import scenes
+from gpu_helpers import compare_fields, compare_populations, need_gpu, rel_l2, run_pair
+
+pytestmark = pytest.mark.gpu
+
+RATES = dict(omega_bulk=1.3, omega_hi=(1.2, 0.9, 1.45, 1.1))
+
+
+@pytest.fixture(autouse=True)
+def _gpu():
+    need_gpu()
+
+
+def test_tgv32_100_steps_fp32():
+    s = scenes.scene_tgv32()
+    g, o = run_pair(32, 32, 32, s["nu"], 100, s["rho"], s["u"])
+    e_rho, e_drho, e_u = compare_fields(g, o)
+    print(f"TGV32 100 steps: rel L2 rho {e_rho:.2e}, rho-1 {e_drho:.2e}, u {e_u:.2e}")
+    assert e_rho <= 1e-5 and e_u <= 1e-5
+    assert e_drho <= 1e-4
+
+
+@pytest.mark.parametrize("steps", [1, 2, 3])
+def test_populations_both_aa_parities(steps):
+    """Odd steps use the neighbour-addressed AA kernel, even steps the local one."""
+    n = (11, 9, 7)
+    rho, u = scenes.taylor_green(*n, 0.05)
+    g, o = run_pair(*n, 0.03, steps, rho, u, forcing=(1e-5, -2e-5, 3e-5), **RATES)
+    err = compare_populations(g, o)
+    assert err <= 2e-7, err
+
+
+def test_matrix_form_oracle_agrees():
+    """Same check against the literal Eq. 5 oracle (explicit M(u) per node)."""
+    n = (6, 5, 4)
+    rho, u = scenes.taylor_green(*n, 0.06)
+    g, o = run_pair(*n, 0.05, 2, rho, u, forcing=(2e-5, 0, 1e-5), oracle_collision="matrix", **RATES)
+    assert compare_populations(g, o) <= 2e-7
+
+
+@pytest.mark.parametrize("dims", [(13, 7, 9), (33, 6, 5), (4, 4, 4)])
+def test_channel_faces_ragged(dims):
+    """Inlet (moving wall + seeded noise + Fourier profile), outlet, no-slip walls, periodic z."""
+    nx, ny, nz = dims
+    rho, u = scenes.uniform_flow(nx, ny, nz, (0.04, 0.0, 0.0))
+    coef = scenes.inflow_coefficients(0.004, seed=5)
+    faces = ("inlet", "outlet", "noslip", "noslip", "periodic", "periodic")
+    for steps in (1, 2, 25):
+        g, o = run_pair(nx, ny, nz, 0.02, steps, rho, u, faces=faces, u_in=0.04, noise=0.01, seed=9,
+                        inflow_coef=coef, forcing=(0, -1e-6, 0), **RATES)
+        err = compare_populations(g, o)
+        assert err <= 3e-7, (steps, err)
+
+
+def test_closed_box_all_noslip():
+    n = (9, 8, 10)
+    rho, u = scenes.taylor_green(*n, 0.05)
+    g, o = run_pair(*n, 0.02, 12, rho, u, faces=("noslip",) * 6)
+    assert compare_populations(g, o) <= 2e-7
+    m_g, mom_g, _ = g.reductions()
+    m_o, mom_o, _ = o.reductions()
+    assert abs(m_g - m_o) <= 1e-6 * abs(m_o)
+
+
+def test_immersed_sphere_periodic_box():
+    n = 16
+    rho, u = scenes.taylor_green(n, n, n, 0.04)
+    X, A = scenes.fibonacci_sphere((7.3, 8.1, 6.6), 3.7, 300)
+    ub = np.tile([0.01, -0.005, 0.0], (300, 1))
+    g, o = run_pair(n, n, n, 0.02, 6, rho, u, forcing=(1e-6, 0, 0), samples=X, area=A, u_b=ub, **RATES)
+    assert compare_populations(g, o) <= 3e-7
+    e_rho, _, e_u = compare_fields(g, o)
+    assert e_rho <= 1e-6 and e_u <= 1e-5
+    gg = g.ib_forces(300)
+    go = o.diag["g"].numpy().T
+    assert np.abs(gg - go).max() <= 1e-6 * np.abs(go).max() + 1e-9
+    m_g, mom_g, drag_g = g.reductions()
+    m_o, mom_o, drag_o = o.reductions()
+    assert abs(m_g - m_o) <= 1e-6 * m_o
+    assert np.abs(mom_g - mom_o.numpy()).max() <= 1e-5 * max(np.abs(mom_o.numpy()).max(), 1e-3)
+    assert np.abs(drag_g - drag_o.numpy()).max() <= 1e-5 * np.abs(drag_o.numpy()).max()
+
+
+def test_sphere_channel_small():
+    """Small version of the sphere channel: inlet noise, outlet, periodic y/z, IB sphere."""
+    nx, ny, nz = 40, 20, 18
+    s = scenes.scene_sphere_channel(nx, ny, nz, radius=4.0, count=400, u_in=0.05, nu=0.02)
+    g, o = run_pair(nx, ny, nz, s["nu"], 30, s["rho"], s["u"], faces=s["faces"], samples=s["samples"],
+                    area=s["area"], u_in=0.05, noise=0.01, seed=2101)
+    e_rho, _, e_u = compare_fields(g, o)
+    assert e_rho <= 1e-6 and e_u <= 1e-5, (e_rho, e_u)
+    _, _, drag_g = g.reductions()
+    _, _, drag_o = o.reductions()
+    assert abs(drag_g[0] - float(drag_o[0])) <= 1e-4 * abs(float(drag_o[0]))
+
+
+def test_samples_on_faces_and_edges_of_cells():
+    """Samples exactly on nodes, cell faces and the last valid coordinate."""
+    n = 10
+    rho, u = scenes.taylor_green(n, n, n, 0.03)
+    X = np.array([[3.0, 4.0, 5.0], [2.5, 7.0, 1.25], [0.0, 0.0, 0.0], [8.999, 8.5, 0.5],
+                  [4.5, 4.5, 4.5], [4.5, 4.5, 4.5]])
+    g, o = run_pair(n, n, n, 0.03, 3, rho, u, samples=X)
+    assert compare_populations(g, o) <= 2e-7
+
+
+@pytest.mark.parametrize("storage,tol", [("f16", 5e-3), ("bf16", 4e-2)])
+def test_reduced_precision_storage(storage, tol):
+    """FP16/BF16 deviation storage, FP32 math: error against the FP64 oracle, reported."""
+    s = scenes.scene_tgv32()
+    g, o = run_pair(32, 32, 32, s["nu"], 50, s["rho"], s["u"], storage=storage)
+    e_rho, e_drho, e_u = compare_fields(g, o)
+    print(f"{storage} TGV32 50 steps: rel L2 rho {e_rho:.2e}, rho-1 {e_drho:.2e}, u {e_u:.2e}")
+    assert np.isfinite(e_u) and e_u <= tol
