@@ -140,12 +140,13 @@ int lbm_load(lbm_ctx *h, const void *buf, size_t bytes);
 
 /* Per-kernel device timing (CUDA events on the context's stream around every launch).
  * lbm_profile(h, 1) enables and clears the counters; lbm_profile(h, 0) disables. */
-#define LBM_KERNEL_STEP        0   /* fused stream + collide                  */
+#define LBM_KERNEL_STEP        0   /* fused stream + collide, interior cells  */
 #define LBM_KERNEL_BAND        1   /* immersed-boundary band moments          */
 #define LBM_KERNEL_INTERP      2   /* interpolation + penalty (Eqs. 6-7)       */
 #define LBM_KERNEL_SPREAD      3   /* spreading (Eq. 8)                        */
-#define LBM_KERNEL_OTHER       4   /* init, macroscopic, reductions, copies   */
-#define LBM_NUM_KERNEL_KINDS   5
+#define LBM_KERNEL_BOUNDARY    4   /* fused stream + collide, face cells      */
+#define LBM_KERNEL_OTHER       5   /* init, macroscopic, reductions, copies   */
+#define LBM_NUM_KERNEL_KINDS   6
 int lbm_profile(lbm_ctx *h, int enable);
 /* ms[k], launches[k] for k < LBM_NUM_KERNEL_KINDS; waits for the stream. */
 int lbm_kernel_times(lbm_ctx *h, double ms[LBM_NUM_KERNEL_KINDS], long long launches[LBM_NUM_KERNEL_KINDS]);

@@ -122,8 +122,8 @@ struct Timed {
     lbm_ctx *h;
     int kind;
     cudaEvent_t a = nullptr;
-    Timed(lbm_ctx *h_, int k) : h(h_), kind(k) {
-        h->launches[kind]++;
+    Timed(lbm_ctx *h_, int k, int nlaunch = 1) : h(h_), kind(k) {
+        h->launches[kind] += nlaunch;
         if (h->prof) {
             a = pool_event(h);
             cudaEventRecord(a, h->stream);
@@ -141,6 +141,7 @@ struct Timed {
 StepParams make_params(const lbm_ctx *h, long long t) {
     StepParams P{};
     P.f = h->f;
+    for (int d = 0; d < 27; ++d) P.fp[d] = static_cast<char *>(h->f) + (size_t)d * h->plane * h->esize;
     P.outlet = h->outlet;
     Geometry &g = P.g;
     g.nx = h->nx; g.ny = h->ny; g.nz = h->nz;
@@ -215,12 +216,6 @@ template <typename T> int upload(lbm_ctx *h, T **dst, const std::vector<T> &src)
     return LBM_OK;
 }
 
-// deliver n floats from device buffer `src` to a caller pointer (host or device)
-int deliver(lbm_ctx *h, float *dst, const float *src, size_t n) {
-    CK(cudaMemcpyAsync(dst, src, n * sizeof(float), cudaMemcpyDefault, h->stream));
-    return LBM_OK;
-}
-
 int require_state(lbm_ctx *h) {
     if (!h) return fail(nullptr, LBM_EINVAL, "null context");
     if (!h->has_state) return fail(h, LBM_ESTATE, "lbm_set_state (or lbm_load) has not been called");
@@ -250,6 +245,7 @@ int lbm_create(lbm_ctx **out, int nx, int ny, int nz, double nu, const double fo
     if (nx < 1 || ny < 1 || nz < 1) return fail(nullptr, LBM_EINVAL, "dimensions must be >= 1");
     const long long N = (long long)nx * ny * nz;
     if (N > 2000000000LL) return fail(nullptr, LBM_EINVAL, "more than 2e9 cells");
+    if (ny > 65537 || nz > 65537) return fail(nullptr, LBM_EINVAL, "ny and nz must be <= 65537");
     if (!(nu > 0.0) || !std::isfinite(nu)) return fail(nullptr, LBM_EINVAL, "nu must be positive and finite");
     lbm_config c;
     if (cfg) c = *cfg;
@@ -504,7 +500,11 @@ int lbm_step(lbm_ctx *h, int n) {
             { Timed tm(h, LBM_KERNEL_INTERP); CK(launch_ib_interp(h->S, h->nband, h->X, h->area, h->ub, h->corner_band, h->band_rho, h->band_u, h->g, h->stream)); }
             { Timed tm(h, LBM_KERNEL_SPREAD); CK(launch_ib_spread(h->S, h->nband, h->X, h->g, h->base_nbr, h->cstart, h->ccount, h->bandF, h->stream)); }
         }
-        { Timed tm(h, LBM_KERNEL_STEP); CK(launch_step(h->storage, P, band, h->stream)); }
+        { Timed tm(h, LBM_KERNEL_BOUNDARY); CK(launch_step(h->storage, P, band, STEP_BOUNDARY, h->stream)); }
+        if (has_interior(P.g)) {
+            Timed tm(h, LBM_KERNEL_STEP);
+            CK(launch_step(h->storage, P, band, STEP_INTERIOR, h->stream));
+        }
         h->t = t;
     }
     return LBM_OK;

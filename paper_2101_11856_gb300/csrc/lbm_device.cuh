@@ -62,6 +62,7 @@ struct Geometry {
 
 struct StepParams {
     void *f;                     // populations, 27 planes (AA in place)
+    void *fp[27];                // start of the plane of each direction
     void *outlet;                // outlet ghost plane, [2][9][nyz] (ping-pong by step parity)
     Geometry g;
     float rho0;

@@ -16,21 +16,20 @@
 
 namespace lbm {
 
-static constexpr int STEP_THREADS = 256;
+static constexpr int STEP_BX = 64;   // threads per block of the interior step (along x)
 
 // ---- loads of the streamed populations f*(x) ------------------------------------------
 
+// interior node: every neighbour exists, constant offsets; one base pointer per plane
 template <typename St, bool NB>
 __device__ __forceinline__ void load_interior(const StepParams &P, int cell, float (&h)[27]) {
-    const St *A = static_cast<const St *>(P.f);
-    const long long pl = P.g.plane;
 #pragma unroll
     for (int d = 0; d < 27; ++d) {
         if (NB) {
-            const int off = cx(d) + cy(d) * P.g.nx + cz(d) * P.g.nxy;
-            h[d] = Store<St>::ld(A + opp(d) * pl + (cell - off));
+            const St *p = static_cast<const St *>(P.fp[opp(d)]) + (cell - (cy(d) * P.g.nx + cz(d) * P.g.nxy));
+            h[d] = Store<St>::ld(p - cx(d));
         } else {
-            h[d] = Store<St>::ld(A + d * pl + cell);
+            h[d] = Store<St>::ld(static_cast<const St *>(P.fp[d]) + cell);
         }
     }
 }
@@ -66,15 +65,13 @@ __device__ __forceinline__ void load_general(const StepParams &P, int x, int y, 
 
 template <typename St, bool NB>
 __device__ __forceinline__ void store_interior(const StepParams &P, int cell, const float (&h)[27]) {
-    St *A = static_cast<St *>(P.f);
-    const long long pl = P.g.plane;
 #pragma unroll
     for (int d = 0; d < 27; ++d) {
         if (NB) {
-            const int off = cx(d) + cy(d) * P.g.nx + cz(d) * P.g.nxy;
-            Store<St>::st(A + d * pl + (cell + off), h[d]);
+            St *p = static_cast<St *>(P.fp[d]) + (cell + (cy(d) * P.g.nx + cz(d) * P.g.nxy));
+            Store<St>::st(p + cx(d), h[d]);
         } else {
-            Store<St>::st(A + opp(d) * pl + cell, h[d]);
+            Store<St>::st(static_cast<St *>(P.fp[opp(d)]) + cell, h[d]);
         }
     }
 }
@@ -109,26 +106,10 @@ __device__ __forceinline__ void decompose(const Geometry &g, int cell, int &x, i
     x = r - y * g.nx;
 }
 
-// ---- the fused step ---------------------------------------------------------------------
-// One thread per cell: pull the 27 streamed populations (with the face rules), add the
-// band's immersed-boundary force, collide in registers, store in place.  Warps whose 32
-// cells are all interior take the constant-offset path.
-template <typename St, bool NB, bool BAND>
-__global__ void __launch_bounds__(STEP_THREADS, 2) k_step(StepParams P) {
-    const int cell = blockIdx.x * STEP_THREADS + threadIdx.x;
-    const bool active = cell < P.g.ncell;
-    int x = 0, y = 0, z = 0;
-    if (active) decompose(P.g, cell, x, y, z);
-    const bool interior = active && x >= 1 && x <= P.g.nx - 2 && y >= 1 && y <= P.g.ny - 2 &&
-                          z >= 1 && z <= P.g.nz - 2;
-    const bool fast = __all_sync(0xffffffffu, interior);
-    if (!active) return;
-
-    float h[27];
-    if (fast) load_interior<St, NB>(P, cell, h);
-    else load_general<St, NB>(P, x, y, z, cell, h);
-
-    float Fx = P.Fx, Fy = P.Fy, Fz = P.Fz;
+// immersed-boundary force of the band node at `cell` (zero off the band)
+template <bool BAND>
+__device__ __forceinline__ void band_force(const StepParams &P, int cell, float &Fx, float &Fy, float &Fz) {
+    Fx = P.Fx; Fy = P.Fy; Fz = P.Fz;
     if (BAND) {
         const uint32_t mask = P.tile_mask[cell >> 5];
         const int lane = cell & 31;
@@ -139,11 +120,70 @@ __global__ void __launch_bounds__(STEP_THREADS, 2) k_step(StepParams P) {
             Fz += P.bandF[2 * P.nband + b];
         }
     }
+}
+
+// ---- the fused step ---------------------------------------------------------------------
+// One thread per cell: pull the 27 streamed populations, add the body force and the band's
+// immersed-boundary force, collide in registers, store in place.  Interior cells (all 26
+// neighbours inside the domain) run in k_step_interior with constant offsets; the cells on
+// the six faces run the face rules in k_step_boundary.  Every cell is updated by exactly one
+// of the two, and the two touch disjoint slots.
+template <typename St, bool NB, bool BAND>
+__global__ void __launch_bounds__(STEP_BX) k_step_interior(StepParams P) {
+    const int x = blockIdx.x * STEP_BX + threadIdx.x + 1;
+    if (x > P.g.nx - 2) return;
+    const int y = blockIdx.y + 1, z = blockIdx.z + 1;
+    const int cell = x + P.g.nx * (y + P.g.ny * z);
+    float h[27];
+    load_interior<St, NB>(P, cell, h);
+    float Fx, Fy, Fz;
+    band_force<BAND>(P, cell, Fx, Fy, Fz);
     float rho, ux, uy, uz;
     collide(h, Fx, Fy, Fz, P, rho, ux, uy, uz);
+    store_interior<St, NB>(P, cell, h);
+}
 
-    if (fast) store_interior<St, NB>(P, cell, h);
-    else store_general<St, NB>(P, x, y, z, cell, h);
+// boundary cell number i -> (x, y, z): first the z faces (all x, y), then the y faces of the
+// interior z range (all x), then the x faces of the interior y, z ranges
+__device__ __forceinline__ void boundary_cell(const Geometry &g, int i, int &x, int &y, int &z) {
+    const int nzb = g.nz > 1 ? 2 : 1, nyb = g.ny > 1 ? 2 : 1, nxb = g.nx > 1 ? 2 : 1;
+    const int nzi = g.nz > 2 ? g.nz - 2 : 0, nyi = g.ny > 2 ? g.ny - 2 : 0;
+    const int gz = nzb * g.nxy;
+    const int gy = nzi * nyb * g.nx;
+    if (i < gz) {
+        const int zi = i / g.nxy, r = i - zi * g.nxy;
+        z = zi ? g.nz - 1 : 0;
+        y = r / g.nx;
+        x = r - y * g.nx;
+    } else if (i < gz + gy) {
+        const int j = i - gz, w = nyb * g.nx;
+        z = 1 + j / w;
+        const int r = j - (z - 1) * w, yi = r / g.nx;
+        y = yi ? g.ny - 1 : 0;
+        x = r - yi * g.nx;
+    } else {
+        const int j = i - gz - gy, w = nyi * nxb;
+        z = 1 + j / w;
+        const int r = j - (z - 1) * w, yi = r / nxb;
+        y = 1 + yi;
+        x = (r - yi * nxb) ? g.nx - 1 : 0;
+    }
+}
+
+template <typename St, bool NB, bool BAND>
+__global__ void __launch_bounds__(128) k_step_boundary(StepParams P, int count) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    int x, y, z;
+    boundary_cell(P.g, i, x, y, z);
+    const int cell = x + P.g.nx * (y + P.g.ny * z);
+    float h[27];
+    load_general<St, NB>(P, x, y, z, cell, h);
+    float Fx, Fy, Fz;
+    band_force<BAND>(P, cell, Fx, Fy, Fz);
+    float rho, ux, uy, uz;
+    collide(h, Fx, Fy, Fz, P, rho, ux, uy, uz);
+    store_general<St, NB>(P, x, y, z, cell, h);
 }
 
 // ---- initialisation: f = f_eq(rho, u), stored as the post-collision state of t = 0 ------
@@ -403,18 +443,30 @@ __global__ void __launch_bounds__(256) k_sum_forces(long long S, const float *__
 
 static inline unsigned blocks_for(long long n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
-template <typename St>
-static cudaError_t launch_step_t(const StepParams &P, bool band, cudaStream_t st) {
-    const bool nb = (P.t & 1) != 0;
-    const unsigned grid = blocks_for(P.g.ncell, STEP_THREADS);
-    if (nb) {
-        if (band) k_step<St, true, true><<<grid, STEP_THREADS, 0, st>>>(P);
-        else k_step<St, true, false><<<grid, STEP_THREADS, 0, st>>>(P);
-    } else {
-        if (band) k_step<St, false, true><<<grid, STEP_THREADS, 0, st>>>(P);
-        else k_step<St, false, false><<<grid, STEP_THREADS, 0, st>>>(P);
+long long boundary_count(const Geometry &g) {
+    const long long nzb = g.nz > 1 ? 2 : 1, nyb = g.ny > 1 ? 2 : 1, nxb = g.nx > 1 ? 2 : 1;
+    const long long nzi = g.nz > 2 ? g.nz - 2 : 0, nyi = g.ny > 2 ? g.ny - 2 : 0;
+    return nzb * g.nxy + nzi * nyb * g.nx + nzi * nyi * nxb;
+}
+
+template <typename St, bool NB, bool BAND>
+static cudaError_t launch_step_tt(const StepParams &P, int part, cudaStream_t st) {
+    const Geometry &g = P.g;
+    if (part == STEP_BOUNDARY) {
+        const int nb = (int)boundary_count(g);
+        k_step_boundary<St, NB, BAND><<<blocks_for(nb, 128), 128, 0, st>>>(P, nb);
+    } else if (g.nx > 2 && g.ny > 2 && g.nz > 2) {
+        const dim3 grid(blocks_for(g.nx - 2, STEP_BX), g.ny - 2, g.nz - 2);
+        k_step_interior<St, NB, BAND><<<grid, STEP_BX, 0, st>>>(P);
     }
     return cudaGetLastError();
+}
+
+template <typename St>
+static cudaError_t launch_step_t(const StepParams &P, bool band, int part, cudaStream_t st) {
+    const bool nb = (P.t & 1) != 0;
+    if (nb) return band ? launch_step_tt<St, true, true>(P, part, st) : launch_step_tt<St, true, false>(P, part, st);
+    return band ? launch_step_tt<St, false, true>(P, part, st) : launch_step_tt<St, false, false>(P, part, st);
 }
 
 template <typename F>
@@ -426,8 +478,8 @@ static cudaError_t dispatch_storage(int storage, F &&fn) {
     }
 }
 
-cudaError_t launch_step(int storage, const StepParams &P, bool band, cudaStream_t st) {
-    return dispatch_storage(storage, [&](auto tag) { return launch_step_t<decltype(tag)>(P, band, st); });
+cudaError_t launch_step(int storage, const StepParams &P, bool band, int part, cudaStream_t st) {
+    return dispatch_storage(storage, [&](auto tag) { return launch_step_t<decltype(tag)>(P, band, part, st); });
 }
 
 cudaError_t launch_init(int storage, const StepParams &P, const float *rho, const float *u, cudaStream_t st) {

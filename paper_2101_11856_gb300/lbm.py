@@ -19,7 +19,7 @@ _lib = None
 LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ETIMEOUT, LBM_ESTATE = 0, -1, -2, -3, -4, -5, -6
 STORAGE = {"f32": 0, "f16": 1, "bf16": 2}
 FACE = {"periodic": 0, "noslip": 1, "inlet": 2, "outlet": 3}
-KERNEL_KINDS = ("step", "band", "interp", "spread", "other")
+KERNEL_KINDS = ("step", "band", "interp", "spread", "boundary", "other")
 
 
 class LBMError(RuntimeError):
@@ -191,8 +191,8 @@ def lbm_profile(h, enable=True):
 
 
 def lbm_kernel_times(h):
-    ms = (C.c_double * 5)()
-    n = (C.c_longlong * 5)()
+    ms = (C.c_double * len(KERNEL_KINDS))()
+    n = (C.c_longlong * len(KERNEL_KINDS))()
     _check(library().lbm_kernel_times(h, ms, n), h)
     return {k: (ms[i], n[i]) for i, k in enumerate(KERNEL_KINDS)}
 
