@@ -29,6 +29,9 @@ import scenes  # noqa: E402
 
 BYTES_PER_CELL = {"f32": 216, "f16": 108, "bf16": 108}   # 27 loads + 27 stores per cell update
 PAPER_MLUPS = 1200 * 250 * 840 / 1.21 / 1e6                # Table 3, Fig. 1 scene: 1.21 s/step on 4x P40
+# DRAM bytes per interior cell of k_step_interior (FP32) from one ncu capture of the current kernel
+# (profiles/k_step_interior_box_city_480x100x336.md); None once the kernel changes
+TRAFFIC_PER_CELL = {"f32": 213.95}
 
 
 def parse():
@@ -291,7 +294,8 @@ def main():
                        "storage": "f32 deviations, AA in place", "l2": "state 27 GB >> L2, no flush needed",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                         "traffic": None, "kernel": "k_step_interior (fused stream+collide, interior cells)",
+                         "traffic": TRAFFIC_PER_CELL["f32"] * n_int if TRAFFIC_PER_CELL.get("f32") else None,
+                         "kernel": "k_step_interior (fused stream+collide, interior cells)",
                          "cells_per_launch": n_int, "bytes_per_cell": 216,
                          "peak_kind": peak_kind},
             "kernel_ms": breakdown,
