@@ -154,6 +154,20 @@ int lbm_kernel_times(lbm_ctx *h, double ms[LBM_NUM_KERNEL_KINDS], long long laun
 /* Number of band nodes (nodes within the 2x2x2 stencil of a sample) of the solid. */
 long long lbm_band_size(const lbm_ctx *h);
 
+/* Allocation-free FP64 sum of per-sample forces: out[a] = sum_s g[3*s + a] (the paper has
+ * no counterpart; this is a service for callers that cannot call cudaMalloc at the point
+ * where they need the sum, e.g. code running while allocation is forbidden or a memory
+ * pool is locked).  g: device pointer to count*3 floats in the layout of lbm_ib_forces;
+ * out: device pointer to 3 doubles, written on cuda_stream (NULL = legacy stream).
+ * No cudaMalloc, cudaFree or allocating library call is made: the partial sums live in a
+ * fixed 48 KiB __device__ array that every GPU loading the library holds until exit.
+ * The first call on a device looks up that array's address (cudaGetSymbolAddress); make
+ * that first call before any stream capture.  All calls on a device share the array, so
+ * calls that overlap on the GPU race; serialise them.  count may be 0 (out = 0);
+ * count > LBM_STATIC_MAX_SAMPLES, a NULL out, or a NULL g with count > 0 give LBM_EINVAL. */
+#define LBM_STATIC_MAX_SAMPLES (2048LL * 256LL * 64LL)
+int lbm_sum_forces_static(const float *g, long long count, double *out, void *cuda_stream);
+
 /* Message of the last error on h (or of the last failed lbm_create when h is NULL). */
 const char *lbm_last_error(const lbm_ctx *h);
 

@@ -55,6 +55,7 @@ _SIGS = {
     "lbm_profile": (C.c_int, [C.c_void_p, C.c_int]),
     "lbm_kernel_times": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
     "lbm_band_size": (C.c_longlong, [C.c_void_p]),
+    "lbm_sum_forces_static": (C.c_int, [C.c_void_p, C.c_longlong, C.c_void_p, C.c_void_p]),
     "lbm_last_error": (C.c_char_p, [C.c_void_p]),
 }
 
@@ -199,6 +200,18 @@ def lbm_kernel_times(h):
 
 def lbm_band_size(h):
     return library().lbm_band_size(h)
+
+
+def lbm_sum_forces_static(g, out, stream=None):
+    """Allocation-free FP64 sum of per-sample forces: g (S, 3) float32 CUDA tensor, out (3,)
+    float64 CUDA tensor; launched on ``stream`` (default: torch's current stream)."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    count = g.numel() // 3
+    rc = library().lbm_sum_forces_static(C.c_void_p(g.data_ptr()) if count else None, count,
+                                         C.c_void_p(out.data_ptr()), C.c_void_p(stream))
+    _check(rc)
 
 
 # ---- convenience wrapper -----------------------------------------------------------
