@@ -27,7 +27,7 @@ extern "C" {
 
 /* ---- status codes --------------------------------------------------------------- */
 #define LBM_OK         0
-#define LBM_EINVAL    -1   /* bad argument: dims < 2, nu <= 0, non-finite or out-of-domain samples, ... */
+#define LBM_EINVAL    -1   /* bad argument: dims < 1, nu <= 0, non-finite or out-of-domain samples, ... */
 #define LBM_ENOMEM    -2   /* a device or host allocation failed                                      */
 #define LBM_ECUDA     -3   /* a CUDA runtime call failed                                              */
 #define LBM_EUNSTABLE -4   /* non-finite density or velocity detected by lbm_check                   */
@@ -69,7 +69,8 @@ void lbm_config_default(lbm_config *cfg);
  * uniform body force forcing[3] (Guo-style force term G of Eq. 4; NULL = no force).
  * cfg = NULL takes lbm_config_default.  Allocates the population array (27 planes of
  * nx*ny*nz values of the storage type, AA in-place layout) on the current CUDA device.
- * Errors: LBM_EINVAL (dims < 2, nu <= 0, bad faces), LBM_ENOMEM, LBM_ECUDA. */
+ * Errors: LBM_EINVAL (a dim < 1, ny or nz > 65535, more than 2e9 cells, nu <= 0, bad faces),
+ * LBM_ENOMEM, LBM_ECUDA. */
 int lbm_create(lbm_ctx **out, int nx, int ny, int nz, double nu,
                const double forcing[3], const lbm_config *cfg);
 
@@ -93,8 +94,8 @@ int lbm_set_solids(lbm_ctx *h, const float *samples, long long count,
 
 /* Advance n time steps (Algorithm 2: streaming, moments, immersed boundary, collision
  * with forcing, domain faces), asynchronously on the context's stream.  Each step is one
- * fused stream+collide kernel over all cells plus three small immersed-boundary kernels
- * when a solid is installed.  Errors: LBM_ESTATE before lbm_set_state, LBM_ECUDA. */
+ * fused stream+collide kernel over the nodes with 1 <= x <= nx-2, one over the x = 0 and
+ * x = nx-1 columns, and three small immersed-boundary kernels when a solid is installed.  Errors: LBM_ESTATE before lbm_set_state, LBM_ECUDA. */
 int lbm_step(lbm_ctx *h, int n);
 
 /* Density and Guo-shifted velocity u = (sum c f + F/2)/rho used by the most recent
@@ -140,11 +141,11 @@ int lbm_load(lbm_ctx *h, const void *buf, size_t bytes);
 
 /* Per-kernel device timing (CUDA events on the context's stream around every launch).
  * lbm_profile(h, 1) enables and clears the counters; lbm_profile(h, 0) disables. */
-#define LBM_KERNEL_STEP        0   /* fused stream + collide, interior cells  */
+#define LBM_KERNEL_STEP        0   /* fused stream + collide, 1 <= x <= nx-2  */
 #define LBM_KERNEL_BAND        1   /* immersed-boundary band moments          */
 #define LBM_KERNEL_INTERP      2   /* interpolation + penalty (Eqs. 6-7)       */
 #define LBM_KERNEL_SPREAD      3   /* spreading (Eq. 8)                        */
-#define LBM_KERNEL_BOUNDARY    4   /* fused stream + collide, face cells      */
+#define LBM_KERNEL_BOUNDARY    4   /* fused stream + collide, x = 0, nx-1     */
 #define LBM_KERNEL_OTHER       5   /* init, macroscopic, reductions, copies   */
 #define LBM_NUM_KERNEL_KINDS   6
 int lbm_profile(lbm_ctx *h, int enable);

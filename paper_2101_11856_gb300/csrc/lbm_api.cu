@@ -245,7 +245,7 @@ int lbm_create(lbm_ctx **out, int nx, int ny, int nz, double nu, const double fo
     if (nx < 1 || ny < 1 || nz < 1) return fail(nullptr, LBM_EINVAL, "dimensions must be >= 1");
     const long long N = (long long)nx * ny * nz;
     if (N > 2000000000LL) return fail(nullptr, LBM_EINVAL, "more than 2e9 cells");
-    if (ny > 65537 || nz > 65537) return fail(nullptr, LBM_EINVAL, "ny and nz must be <= 65537");
+    if (ny > 65535 || nz > 65535) return fail(nullptr, LBM_EINVAL, "ny and nz must be <= 65535");
     if (!(nu > 0.0) || !std::isfinite(nu)) return fail(nullptr, LBM_EINVAL, "nu must be positive and finite");
     lbm_config c;
     if (cfg) c = *cfg;

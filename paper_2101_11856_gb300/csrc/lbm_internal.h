@@ -8,10 +8,11 @@
 namespace lbm {
 
 enum { STEP_BOUNDARY = 0, STEP_INTERIOR = 1 };
-// one part of the fused step: the face cells or the interior cells
+// one part of the fused step: the x-face columns (STEP_BOUNDARY) or every node with
+// 1 <= x <= nx-2 (STEP_INTERIOR)
 cudaError_t launch_step(int storage, const StepParams &P, bool band, int part, cudaStream_t st);
 long long boundary_count(const Geometry &g);
-inline bool has_interior(const Geometry &g) { return g.nx > 2 && g.ny > 2 && g.nz > 2; }
+inline bool has_interior(const Geometry &g) { return g.nx > 2; }
 cudaError_t launch_init(int storage, const StepParams &P, const float *rho, const float *u, cudaStream_t st);
 long long macro_blocks(const StepParams &P);
 cudaError_t launch_macro(int storage, const StepParams &P, bool band, int force_on, float *rho, float *u, float *f,

@@ -122,60 +122,99 @@ __device__ __forceinline__ void band_force(const StepParams &P, int cell, float 
     }
 }
 
+// ---- rows of a block's y/z neighbours ----------------------------------------------------
+// The y and z faces are only periodic or no-slip.  For the node rows y + S c_y, z + S c_z
+// (S = -1: pull source, S = +1: push target) give the cell offset of the row (with periodic
+// wrap) or mark it as crossing a no-slip face (bounce-back to the node's own slot).  Row j of
+// direction d is j = d / 3 = (c_y + 1) + 3 (c_z + 1).
+template <int S>
+__device__ __forceinline__ void yz_rows(const Geometry &g, int y, int z, int (&off)[9], bool (&bb)[9]) {
+    int oy[3], oz[3];
+    bool by[3], bz[3];
+#pragma unroll
+    for (int c = -1; c <= 1; ++c) {
+        int yy = y + S * c, zz = z + S * c;
+        by[c + 1] = bz[c + 1] = false;
+        if (yy < 0) { if (g.periodic[1]) yy += g.ny; else by[c + 1] = true; }
+        else if (yy >= g.ny) { if (g.periodic[1]) yy -= g.ny; else by[c + 1] = true; }
+        if (zz < 0) { if (g.periodic[2]) zz += g.nz; else bz[c + 1] = true; }
+        else if (zz >= g.nz) { if (g.periodic[2]) zz -= g.nz; else bz[c + 1] = true; }
+        oy[c + 1] = (yy - y) * g.nx;
+        oz[c + 1] = (zz - z) * g.nxy;
+    }
+#pragma unroll
+    for (int j = 0; j < 9; ++j) {
+        off[j] = oy[j % 3] + oz[j / 3];
+        bb[j] = by[j % 3] || bz[j / 3];
+    }
+}
+
+// odd-step loads/stores of a node with 1 <= x <= nx-2 on a y or z face
+template <typename St>
+__device__ __forceinline__ void load_yzface(const StepParams &P, int y, int z, int cell, float (&h)[27]) {
+    int off[9];
+    bool bb[9];
+    yz_rows<-1>(P.g, y, z, off, bb);
+#pragma unroll
+    for (int d = 0; d < 27; ++d) {
+        if (bb[d / 3]) h[d] = Store<St>::ld(static_cast<const St *>(P.fp[d]) + cell);
+        else h[d] = Store<St>::ld(static_cast<const St *>(P.fp[opp(d)]) + (cell + off[d / 3]) - cx(d));
+    }
+}
+
+template <typename St>
+__device__ __forceinline__ void store_yzface(const StepParams &P, int y, int z, int cell, const float (&h)[27]) {
+    int off[9];
+    bool bb[9];
+    yz_rows<+1>(P.g, y, z, off, bb);
+#pragma unroll
+    for (int d = 0; d < 27; ++d) {
+        if (bb[d / 3]) Store<St>::st(static_cast<St *>(P.fp[opp(d)]) + cell, h[d]);
+        else Store<St>::st(static_cast<St *>(P.fp[d]) + (cell + off[d / 3]) + cx(d), h[d]);
+    }
+}
+
 // ---- the fused step ---------------------------------------------------------------------
 // One thread per cell: pull the 27 streamed populations, add the body force and the band's
-// immersed-boundary force, collide in registers, store in place.  Interior cells (all 26
-// neighbours inside the domain) run in k_step_interior with constant offsets; the cells on
-// the six faces run the face rules in k_step_boundary.  Every cell is updated by exactly one
-// of the two, and the two touch disjoint slots.
+// immersed-boundary force, collide in registers, store in place.  k_step_main updates every
+// node with 1 <= x <= nx-2: one block row per (y, z), so a block's y/z face status is uniform
+// (interior rows use constant offsets; face rows of odd steps use wrapped or bounced rows;
+// even steps address only the node's own slots).  k_step_xfaces updates the x = 0 and
+// x = nx-1 columns with the general face rules (inlet, outlet).  Every node is updated by
+// exactly one of the two, and the two touch disjoint slots.
 template <typename St, bool NB, bool BAND>
-__global__ void __launch_bounds__(STEP_BX) k_step_interior(StepParams P) {
+__global__ void __launch_bounds__(STEP_BX) k_step_main(StepParams P) {
     const int x = blockIdx.x * STEP_BX + threadIdx.x + 1;
     if (x > P.g.nx - 2) return;
-    const int y = blockIdx.y + 1, z = blockIdx.z + 1;
+    const int y = blockIdx.y, z = blockIdx.z;
     const int cell = x + P.g.nx * (y + P.g.ny * z);
+    const bool inner = y >= 1 && y <= P.g.ny - 2 && z >= 1 && z <= P.g.nz - 2;   // uniform per block
     float h[27];
-    load_interior<St, NB>(P, cell, h);
+    if (!NB || inner) load_interior<St, NB>(P, cell, h);
+    else load_yzface<St>(P, y, z, cell, h);
     float Fx, Fy, Fz;
     band_force<BAND>(P, cell, Fx, Fy, Fz);
     float rho, ux, uy, uz;
     collide(h, Fx, Fy, Fz, P, rho, ux, uy, uz);
-    store_interior<St, NB>(P, cell, h);
+    if (!NB || inner) store_interior<St, NB>(P, cell, h);
+    else store_yzface<St>(P, y, z, cell, h);
 }
 
-// boundary cell number i -> (x, y, z): first the z faces (all x, y), then the y faces of the
-// interior z range (all x), then the x faces of the interior y, z ranges
-__device__ __forceinline__ void boundary_cell(const Geometry &g, int i, int &x, int &y, int &z) {
-    const int nzb = g.nz > 1 ? 2 : 1, nyb = g.ny > 1 ? 2 : 1, nxb = g.nx > 1 ? 2 : 1;
-    const int nzi = g.nz > 2 ? g.nz - 2 : 0, nyi = g.ny > 2 ? g.ny - 2 : 0;
-    const int gz = nzb * g.nxy;
-    const int gy = nzi * nyb * g.nx;
-    if (i < gz) {
-        const int zi = i / g.nxy, r = i - zi * g.nxy;
-        z = zi ? g.nz - 1 : 0;
-        y = r / g.nx;
-        x = r - y * g.nx;
-    } else if (i < gz + gy) {
-        const int j = i - gz, w = nyb * g.nx;
-        z = 1 + j / w;
-        const int r = j - (z - 1) * w, yi = r / g.nx;
-        y = yi ? g.ny - 1 : 0;
-        x = r - yi * g.nx;
-    } else {
-        const int j = i - gz - gy, w = nyi * nxb;
-        z = 1 + j / w;
-        const int r = j - (z - 1) * w, yi = r / nxb;
-        y = 1 + yi;
-        x = (r - yi * nxb) ? g.nx - 1 : 0;
-    }
+// x-face node number i -> (x, y, z), i = side + nxb (y + ny z)
+__device__ __forceinline__ void xface_cell(const Geometry &g, int i, int &x, int &y, int &z) {
+    const int nxb = g.nx > 1 ? 2 : 1;
+    const int r = i / nxb;
+    x = (i - r * nxb) ? g.nx - 1 : 0;
+    z = r / g.ny;
+    y = r - z * g.ny;
 }
 
 template <typename St, bool NB, bool BAND>
-__global__ void __launch_bounds__(128) k_step_boundary(StepParams P, int count) {
+__global__ void __launch_bounds__(128) k_step_xfaces(StepParams P, int count) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= count) return;
     int x, y, z;
-    boundary_cell(P.g, i, x, y, z);
+    xface_cell(P.g, i, x, y, z);
     const int cell = x + P.g.nx * (y + P.g.ny * z);
     float h[27];
     load_general<St, NB>(P, x, y, z, cell, h);
@@ -444,9 +483,7 @@ __global__ void __launch_bounds__(256) k_sum_forces(long long S, const float *__
 static inline unsigned blocks_for(long long n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
 long long boundary_count(const Geometry &g) {
-    const long long nzb = g.nz > 1 ? 2 : 1, nyb = g.ny > 1 ? 2 : 1, nxb = g.nx > 1 ? 2 : 1;
-    const long long nzi = g.nz > 2 ? g.nz - 2 : 0, nyi = g.ny > 2 ? g.ny - 2 : 0;
-    return nzb * g.nxy + nzi * nyb * g.nx + nzi * nyi * nxb;
+    return (long long)(g.nx > 1 ? 2 : 1) * g.ny * g.nz;
 }
 
 template <typename St, bool NB, bool BAND>
@@ -454,10 +491,10 @@ static cudaError_t launch_step_tt(const StepParams &P, int part, cudaStream_t st
     const Geometry &g = P.g;
     if (part == STEP_BOUNDARY) {
         const int nb = (int)boundary_count(g);
-        k_step_boundary<St, NB, BAND><<<blocks_for(nb, 128), 128, 0, st>>>(P, nb);
-    } else if (g.nx > 2 && g.ny > 2 && g.nz > 2) {
-        const dim3 grid(blocks_for(g.nx - 2, STEP_BX), g.ny - 2, g.nz - 2);
-        k_step_interior<St, NB, BAND><<<grid, STEP_BX, 0, st>>>(P);
+        k_step_xfaces<St, NB, BAND><<<blocks_for(nb, 128), 128, 0, st>>>(P, nb);
+    } else if (has_interior(g)) {
+        const dim3 grid(blocks_for(g.nx - 2, STEP_BX), g.ny, g.nz);
+        k_step_main<St, NB, BAND><<<grid, STEP_BX, 0, st>>>(P);
     }
     return cudaGetLastError();
 }
