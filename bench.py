@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp16", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     return ap.parse_args()
 
 
@@ -158,6 +159,46 @@ def run_reference(args):
             "cpu_baseline": cb,
             "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
+
+
+def adjoint_cost(torch, args):
+    """Adjoint workload: 128^3 channel, IB sphere r = 12.6 at (40, 64, 64) with 2,000 samples,
+    200 steps, loss = mean drag + kinetic energy of the slab 96 <= x < 128, checkpoints every
+    20 steps.  Reports the adjoint (forward + backward) time against 200 forward steps."""
+    from paper_2101_11856_gb300 import Solver
+    n = max(8, int(round(128 * args.scale))) if args.scale < 1.0 else 128
+    steps, K = 200, 20
+    X, A = scenes.fibonacci_sphere((40.0 * n / 128, n / 2, n / 2), 12.6 * n / 128, 2000)
+    rho, u = scenes.uniform_flow(n, n, n, (0.05, 0, 0))
+    faces = ("inlet", "outlet", "periodic", "periodic", "periodic", "periodic")
+
+    def make():
+        s = Solver(n, n, n, 0.01, faces=faces, u_in=0.05, noise=0.01, seed=2101)
+        s.set_state(rho, u)
+        s.set_solids(X, A)
+        return s
+
+    s = make()
+    s.step(5)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s.step(steps)
+    torch.cuda.synchronize()
+    fwd = time.perf_counter() - t0
+    s.close()
+    s = make()
+    s.adjoint(2, 1, 1.0, 1.0, int(96 * n / 128), n, 2000)     # warm-up (allocations, module load)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    L, dcoef, dpos = s.adjoint(steps, K, 1.0, 1.0, int(96 * n / 128), n, 2000)
+    torch.cuda.synchronize()
+    adj = time.perf_counter() - t0
+    s.close()
+    ok = bool(np.isfinite(L) and np.all(np.isfinite(dcoef)) and np.all(np.isfinite(dpos)))
+    return {"workload": f"channel_sphere_{n}^3", "samples": 2000, "steps": steps, "checkpoint_K": K,
+            "forward_ms": fwd * 1e3, "adjoint_ms": adj * 1e3, "adjoint_over_forward": adj / fwd,
+            "adjoint_mlups": n ** 3 * steps / adj / 1e6, "finite": ok,
+            "what": "lbm_adjoint (forward with checkpoints + segment recompute + backward) vs lbm_step x 200"}
 
 
 def timed_steps(solver, steps, torch):
@@ -278,6 +319,10 @@ def main():
         s16.close()
         del s16
 
+    adjoint = None
+    if not args.no_adjoint:
+        adjoint = adjoint_cost(torch, args)
+
     cpu = None
     if not args.no_cpu and rank == 0 and world == 1:
         cpu, _ = oracle_sample(d, 2)
@@ -304,6 +349,7 @@ def main():
             "clocks": clk.summary(),
             "e2e": e2e,
             "fp16": fp16,
+            "adjoint": adjoint,
             "cpu_baseline": cpu,
             "checks": {"mass": mass, "drag": list(map(float, drag))},
         }

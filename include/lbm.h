@@ -131,6 +131,29 @@ int lbm_check(lbm_ctx *h);
  * polling with cudaEventQuery: LBM_OK, LBM_ETIMEOUT or LBM_ECUDA. */
 int lbm_synchronize(lbm_ctx *h, double timeout_s);
 
+/* Loss of the adjoint problem: L = w_drag * (1/n) sum_{t=1..n} D_x(t)
+ *                                 + w_ke * 1/2 sum_{ke_x0 <= x < ke_x1} rho |u|^2 (at step n),
+ * D(t) = -sum_s g_s(t) the drag on the solid (Algorithm 2, total force) and rho, u the
+ * macroscopic fields of the last collision (Eq. 2). */
+typedef struct lbm_loss {
+    double w_drag;
+    double w_ke;
+    int ke_x0, ke_x1;            /* slab of the kinetic-energy term, 0 <= ke_x0 <= ke_x1 <= nx */
+} lbm_loss;
+
+/* Hand-written adjoint (the paper has no adjoint; the forward operator is Algorithm 2 with
+ * Eqs. 3-8).  Runs n steps forward from the current state (the state advances by n, as with
+ * lbm_step), evaluates L and back-propagates through every step: transposed streaming with
+ * the faces, the vector-Jacobian product of the central-moment collision recomputed in
+ * registers, and the transposes of IB interpolation/spreading with the derivatives of the
+ * trilinear weights.  States are recomputed from checkpoints taken every K steps
+ * (memory: about (n/K + K + 3) population arrays plus two FP32 adjoint arrays).
+ * Outputs (host pointers, any may be NULL): dL_dinflow[16] = dL/da_mn of the inflow profile
+ * (row-major in m; 0 without an inlet), dL_dpos[3*count] = dL/dX_s in the caller's sample
+ * order, *L.  Gradients are accumulated in FP64.  Errors: LBM_ESTATE, LBM_EINVAL, LBM_ENOMEM,
+ * LBM_ECUDA. */
+int lbm_adjoint(lbm_ctx *h, int n, int K, const lbm_loss *loss, double *dL_dinflow, double *dL_dpos, double *L);
+
 /* Checkpoint: serialise the state (header + populations in canonical layout in the
  * storage type + outlet ghost plane + step counter) into buf.  With buf = NULL only
  * *bytes is set to the required size.  Host pointer. */

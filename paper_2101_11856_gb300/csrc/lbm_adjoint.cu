@@ -1,0 +1,652 @@
+// Hand-written adjoint of the time step: gradients of a drag + kinetic-energy loss with
+// respect to the inflow-profile coefficients and the immersed-boundary sample positions.
+//
+// Forward step t (Algorithm 2): f*_t = S(f_{t-1}; a) (streaming with the faces; the inlet
+// adds 2 w_i rho0 c_i.u_w with u_w linear in the inflow coefficients a), IB force
+// F_t = spread(g(f*_t; X); X), f_t = C(f*_t, F_b + F_t) (central-moment collision).
+// With lambda_t = dL/df_t the backward step computes, per node, the vector-Jacobian product
+// of the collision (recomputed in registers from the stored f_{t-1}), the IB terms (the
+// transposes of spreading and interpolation, and the trilinear weights' derivatives for the
+// positions), and pushes mu = dL/df* back along the streaming (its transpose):
+// lambda_{t-1}[i](x - c_i) = mu_i(x), bounce-back slots get mu of the reflected direction,
+// the outlet ghost's duplicate goes through a small fix-up.  States f_{t-1} come from
+// segment recomputation between checkpoints taken every K steps.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "lbm_ctx.h"
+
+using namespace lbm;
+using namespace lbm_host;
+
+namespace lbm {
+
+// ---- 3-point maps of the adjoint (transposes of the forward per-axis maps) -------------
+// forward raw R: (a, b, c) -> (a + b + c, c - a, c + a); its transpose
+__device__ __forceinline__ void rawT3(float &a, float &b, float &c) {
+    const float l0 = a, l1 = b, l2 = c;
+    a = l0 - l1 + l2;
+    b = l0;
+    c = l0 + l1 + l2;
+}
+// forward inverse raw R^-1: (r0, r1, r2) -> ((r2 - r1)/2, r0 - r2, (r2 + r1)/2); its transpose
+__device__ __forceinline__ void invrawT3(float &a, float &b, float &c) {
+    const float la = a, lb = b, lc = c;
+    a = lb;
+    b = 0.5f * (lc - la);
+    c = 0.5f * (la + lc) - lb;
+}
+// central shift Sh(u) = [[1,0,0],[-u,1,0],[u^2,-2u,1]]; its transpose
+__device__ __forceinline__ void shiftT3(float &a, float &b, float &c, float u) {
+    const float l1 = b, l2 = c;
+    a = fmaf(u * u, l2, fmaf(-u, l1, a));
+    b = fmaf(-2.0f * u, l2, l1);
+}
+// inverse shift Sh(u)^-1 = [[1,0,0],[u,1,0],[u^2,2u,1]] and its transpose
+__device__ __forceinline__ void invshift3(float &m0, float &m1, float &m2, float u) {
+    const float r1 = fmaf(u, m0, m1);
+    m2 = fmaf(u, m1 + r1, m2);
+    m1 = r1;
+}
+__device__ __forceinline__ void invshiftT3(float &a, float &b, float &c, float u) {
+    a = fmaf(u * u, c, fmaf(u, b, a));
+    b = fmaf(2.0f * u, c, b);
+}
+
+template <int S, typename Op> __device__ __forceinline__ void sweep(float (&h)[27], Op op) {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) op(h[tri_base<S>(k)], h[tri_base<S>(k) + S], h[tri_base<S>(k) + 2 * S]);
+}
+
+// sum over the triplets of axis S of l[1] v[0] + 2 l[2] v[1]: the contraction with the
+// generator A of the shift (dSh/du = -A Sh, d(Sh^-1)/du = A Sh^-1)
+template <int S> __device__ __forceinline__ float gen_contract(const float (&l)[27], const float (&v)[27]) {
+    float acc = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const int b = tri_base<S>(k);
+        acc = fmaf(l[b + S], v[b], acc);
+        acc = fmaf(2.0f * l[b + 2 * S], v[b + S], acc);
+    }
+    return acc;
+}
+
+struct AdjExtra {
+    float drho, djx, djy, djz;   // direct dL/d rho*, dL/d j at this node (IB terms)
+    float wke;                   // weight of 1/2 rho |u|^2 at this node (last step, slab), else 0
+};
+
+// Vector-Jacobian product of the collision f_post = C(f*, F) (Eqs. 4-5, same operator as
+// collide() in lbm_device.cuh): in lam = dL/df_post, out lam = dL/df*, dF += dL/dF.
+__device__ __forceinline__ void collide_vjp(const float (&fs)[27], float Fx, float Fy, float Fz, const StepParams &P,
+                                            const AdjExtra &ex, float (&lam)[27], float &dFx, float &dFy, float &dFz) {
+    // forward recompute in full populations
+    float k[27];
+#pragma unroll
+    for (int d = 0; d < 27; ++d) k[d] = fs[d];
+    sweep<1>(k, [](float &a, float &b, float &c) { raw3(a, b, c); });
+    sweep<3>(k, [](float &a, float &b, float &c) { raw3(a, b, c); });
+    sweep<9>(k, [](float &a, float &b, float &c) { raw3(a, b, c); });
+    const float rho = k[K(0, 0, 0)];
+    const float inv = 1.0f / rho;
+    const float ux = (k[K(1, 0, 0)] + 0.5f * Fx) * inv;
+    const float uy = (k[K(0, 1, 0)] + 0.5f * Fy) * inv;
+    const float uz = (k[K(0, 0, 1)] + 0.5f * Fz) * inv;
+    sweep<1>(k, [ux](float &a, float &b, float &c) { shift3(a, b, c, ux); });
+    sweep<3>(k, [uy](float &a, float &b, float &c) { shift3(a, b, c, uy); });
+    sweep<9>(k, [uz](float &a, float &b, float &c) { shift3(a, b, c, uz); });
+    // k = central moments kappa; rp = post-collision central moments, then raw moments
+    const float wb = 1.0f - P.rb, w4 = 1.0f - P.r4, w6 = 1.0f - P.r6;
+    const float third = 1.0f / 3.0f, ninth = 1.0f / 9.0f;
+    float rp[27];
+#pragma unroll
+    for (int d = 0; d < 27; ++d) rp[d] = k[d];
+    rp[K(1, 0, 0)] += Fx;
+    rp[K(0, 1, 0)] += Fy;
+    rp[K(0, 0, 1)] += Fz;
+    rp[K(1, 1, 0)] *= P.rs;
+    rp[K(1, 0, 1)] *= P.rs;
+    rp[K(0, 1, 1)] *= P.rs;
+    {
+        const float a = k[K(2, 0, 0)] - rho * third, b = k[K(0, 2, 0)] - rho * third, c = k[K(0, 0, 2)] - rho * third;
+        const float s3 = (a + b + c) * third;
+        rp[K(2, 0, 0)] = rho * third + P.rb * s3 + P.rs * (a - s3);
+        rp[K(0, 2, 0)] = rho * third + P.rb * s3 + P.rs * (b - s3);
+        rp[K(0, 0, 2)] = rho * third + P.rb * s3 + P.rs * (c - s3);
+    }
+    rp[K(2, 1, 0)] = fmaf(P.r3, k[K(2, 1, 0)], P.q3 * third * Fy);
+    rp[K(2, 0, 1)] = fmaf(P.r3, k[K(2, 0, 1)], P.q3 * third * Fz);
+    rp[K(1, 2, 0)] = fmaf(P.r3, k[K(1, 2, 0)], P.q3 * third * Fx);
+    rp[K(0, 2, 1)] = fmaf(P.r3, k[K(0, 2, 1)], P.q3 * third * Fz);
+    rp[K(1, 0, 2)] = fmaf(P.r3, k[K(1, 0, 2)], P.q3 * third * Fx);
+    rp[K(0, 1, 2)] = fmaf(P.r3, k[K(0, 1, 2)], P.q3 * third * Fy);
+    rp[K(1, 1, 1)] = P.r3 * k[K(1, 1, 1)];
+    rp[K(2, 2, 0)] = fmaf(P.r4, k[K(2, 2, 0)], w4 * ninth * rho);
+    rp[K(2, 0, 2)] = fmaf(P.r4, k[K(2, 0, 2)], w4 * ninth * rho);
+    rp[K(0, 2, 2)] = fmaf(P.r4, k[K(0, 2, 2)], w4 * ninth * rho);
+    rp[K(2, 1, 1)] = P.r4 * k[K(2, 1, 1)];
+    rp[K(1, 2, 1)] = P.r4 * k[K(1, 2, 1)];
+    rp[K(1, 1, 2)] = P.r4 * k[K(1, 1, 2)];
+    rp[K(2, 2, 1)] = fmaf(P.r5, k[K(2, 2, 1)], P.q5 * ninth * Fz);
+    rp[K(2, 1, 2)] = fmaf(P.r5, k[K(2, 1, 2)], P.q5 * ninth * Fy);
+    rp[K(1, 2, 2)] = fmaf(P.r5, k[K(1, 2, 2)], P.q5 * ninth * Fx);
+    rp[K(2, 2, 2)] = fmaf(P.r6, k[K(2, 2, 2)], w6 * (1.0f / 27.0f) * rho);
+    sweep<1>(rp, [ux](float &a, float &b, float &c) { invshift3(a, b, c, ux); });
+    sweep<3>(rp, [uy](float &a, float &b, float &c) { invshift3(a, b, c, uy); });
+    sweep<9>(rp, [uz](float &a, float &b, float &c) { invshift3(a, b, c, uz); });
+
+    // backward: populations -> post-collision raw moments
+    sweep<1>(lam, [](float &a, float &b, float &c) { invrawT3(a, b, c); });
+    sweep<3>(lam, [](float &a, float &b, float &c) { invrawT3(a, b, c); });
+    sweep<9>(lam, [](float &a, float &b, float &c) { invrawT3(a, b, c); });
+    // u through the inverse shift: d/du_a (Sh^-1 kappa') = A_a r'
+    float dux = gen_contract<1>(lam, rp), duy = gen_contract<3>(lam, rp), duz = gen_contract<9>(lam, rp);
+    sweep<1>(lam, [ux](float &a, float &b, float &c) { invshiftT3(a, b, c, ux); });
+    sweep<3>(lam, [uy](float &a, float &b, float &c) { invshiftT3(a, b, c, uy); });
+    sweep<9>(lam, [uz](float &a, float &b, float &c) { invshiftT3(a, b, c, uz); });
+    // relaxation: lam = dL/d kappa'
+    float drho = 0.0f;
+    dFx += lam[K(1, 0, 0)] + P.q3 * third * (lam[K(1, 2, 0)] + lam[K(1, 0, 2)]) + P.q5 * ninth * lam[K(1, 2, 2)];
+    dFy += lam[K(0, 1, 0)] + P.q3 * third * (lam[K(2, 1, 0)] + lam[K(0, 1, 2)]) + P.q5 * ninth * lam[K(2, 1, 2)];
+    dFz += lam[K(0, 0, 1)] + P.q3 * third * (lam[K(2, 0, 1)] + lam[K(0, 2, 1)]) + P.q5 * ninth * lam[K(2, 2, 1)];
+    drho += wb * third * (lam[K(2, 0, 0)] + lam[K(0, 2, 0)] + lam[K(0, 0, 2)]);
+    drho += w4 * ninth * (lam[K(2, 2, 0)] + lam[K(2, 0, 2)] + lam[K(0, 2, 2)]);
+    drho += w6 * (1.0f / 27.0f) * lam[K(2, 2, 2)];
+    lam[K(1, 1, 0)] *= P.rs;
+    lam[K(1, 0, 1)] *= P.rs;
+    lam[K(0, 1, 1)] *= P.rs;
+    {
+        // the diagonal block (rb/3) J + (rs/3)(3 I - J) is symmetric
+        const float a = lam[K(2, 0, 0)], b = lam[K(0, 2, 0)], c = lam[K(0, 0, 2)];
+        const float s3 = (a + b + c) * third;
+        lam[K(2, 0, 0)] = P.rb * s3 + P.rs * (a - s3);
+        lam[K(0, 2, 0)] = P.rb * s3 + P.rs * (b - s3);
+        lam[K(0, 0, 2)] = P.rb * s3 + P.rs * (c - s3);
+    }
+    lam[K(2, 1, 0)] *= P.r3; lam[K(2, 0, 1)] *= P.r3; lam[K(1, 2, 0)] *= P.r3;
+    lam[K(0, 2, 1)] *= P.r3; lam[K(1, 0, 2)] *= P.r3; lam[K(0, 1, 2)] *= P.r3; lam[K(1, 1, 1)] *= P.r3;
+    lam[K(2, 2, 0)] *= P.r4; lam[K(2, 0, 2)] *= P.r4; lam[K(0, 2, 2)] *= P.r4;
+    lam[K(2, 1, 1)] *= P.r4; lam[K(1, 2, 1)] *= P.r4; lam[K(1, 1, 2)] *= P.r4;
+    lam[K(2, 2, 1)] *= P.r5; lam[K(2, 1, 2)] *= P.r5; lam[K(1, 2, 2)] *= P.r5;
+    lam[K(2, 2, 2)] *= P.r6;
+    // u through the forward shift: d/du_a (Sh r) = -A_a kappa
+    dux -= gen_contract<1>(lam, k);
+    duy -= gen_contract<3>(lam, k);
+    duz -= gen_contract<9>(lam, k);
+    sweep<1>(lam, [ux](float &a, float &b, float &c) { shiftT3(a, b, c, ux); });
+    sweep<3>(lam, [uy](float &a, float &b, float &c) { shiftT3(a, b, c, uy); });
+    sweep<9>(lam, [uz](float &a, float &b, float &c) { shiftT3(a, b, c, uz); });
+    // kinetic-energy term 1/2 rho |u|^2 of the loss
+    if (ex.wke != 0.0f) {
+        dux = fmaf(ex.wke * rho, ux, dux);
+        duy = fmaf(ex.wke * rho, uy, duy);
+        duz = fmaf(ex.wke * rho, uz, duz);
+        drho = fmaf(0.5f * ex.wke, ux * ux + uy * uy + uz * uz, drho);
+    }
+    // u = (j + F/2) / rho
+    dFx += 0.5f * dux * inv;
+    dFy += 0.5f * duy * inv;
+    dFz += 0.5f * duz * inv;
+    drho -= (dux * ux + duy * uy + duz * uz) * inv;
+    lam[K(0, 0, 0)] += drho + ex.drho;
+    lam[K(1, 0, 0)] += dux * inv + ex.djx;
+    lam[K(0, 1, 0)] += duy * inv + ex.djy;
+    lam[K(0, 0, 1)] += duz * inv + ex.djz;
+    sweep<1>(lam, [](float &a, float &b, float &c) { rawT3(a, b, c); });
+    sweep<3>(lam, [](float &a, float &b, float &c) { rawT3(a, b, c); });
+    sweep<9>(lam, [](float &a, float &b, float &c) { rawT3(a, b, c); });
+}
+
+}  // namespace lbm
+
+namespace {
+
+// full streamed populations f* of node (x, y, z) at step P.t, pulled from the stored
+// f_{t-1} with the same face rules as the forward general loader
+
+template <typename St, bool NB>
+__device__ __forceinline__ void adj_load_fstar(const StepParams &P, int x, int y, int z, int cell, float (&h)[27]) {
+    const St *B = static_cast<const St *>(P.outlet);
+    const int rpar = (int)((P.t - 1) & 1);
+    const bool inlet_node = (x == 0) && P.g.face[0] == FACE_INLET;
+    const float uw = inlet_node ? inlet_velocity(P, y, z) : 0.0f;
+#pragma unroll
+    for (int d = 0; d < 27; ++d) {
+        const Nbr n = neighbour<-1>(P.g, d, x, y, z);
+        float v;
+        if (n.kind == 0) {
+            v = NB ? Store<St>::ld(static_cast<const St *>(P.fp[opp(d)]) + n.idx)
+                   : Store<St>::ld(static_cast<const St *>(P.fp[d]) + cell);
+        } else if (n.kind & CROSS_NOSLIP) {
+            v = Store<St>::ld(static_cast<const St *>(P.fp[d]) + cell);
+        } else if (n.kind & CROSS_INLET) {
+            v = Store<St>::ld(static_cast<const St *>(P.fp[d]) + cell) + 6.0f * wgt(d) * P.rho0 * (float)cx(d) * uw;
+        } else {
+            v = Store<St>::ld(B + ((long long)(rpar * 9 + d / 3) * P.g.nyz + n.y + P.g.ny * n.z));
+        }
+        h[d] = v + wgt(d) * P.rho0;      // full population
+    }
+}
+
+__device__ __forceinline__ void adj_decompose(const Geometry &g, int cell, int &x, int &y, int &z) {
+    z = cell / g.nxy;
+    const int r = cell - z * g.nxy;
+    y = r / g.nx;
+    x = r - y * g.nx;
+}
+
+__device__ __forceinline__ bool band_index(const StepParams &P, int cell, long long &b) {
+    const uint32_t mask = P.tile_mask[cell >> 5];
+    const int lane = cell & 31;
+    if (!((mask >> lane) & 1u)) return false;
+    b = P.tile_off[cell >> 5] + __popc(mask & ((1u << lane) - 1u));
+    return true;
+}
+
+struct AdjParams {
+    const float *lam_cur;        // [27][N] dL/df_t (canonical, library direction order)
+    float *lam_prev;             // [27][N] dL/df_{t-1}
+    float *blam;                 // [9][nyz] outlet-ghost duplicates
+    double *s_inlet;             // [nyz] accumulated sum_i mu_i 6 w_i rho0 c_ix per inlet node
+    const float *adj_band;       // [4][nband] dL/d rho*, dL/d j of the band nodes
+    float *dF_band;              // [3][nband] dL/dF of the band nodes
+    float wke;                   // w_ke on the last step, else 0
+    int ke_x0, ke_x1;
+};
+
+// dL/dF at the band nodes (collision VJP with respect to the force)
+template <typename St, bool NB>
+__global__ void __launch_bounds__(128) k_adj_band_force(StepParams P, AdjParams A, const int *__restrict__ band_cell) {
+    const long long kb = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (kb >= P.nband) return;
+    const int cell = band_cell[kb];
+    int x, y, z;
+    adj_decompose(P.g, cell, x, y, z);
+    float fs[27], lam[27];
+    adj_load_fstar<St, NB>(P, x, y, z, cell, fs);
+    const long long N = P.g.ncell;
+#pragma unroll
+    for (int d = 0; d < 27; ++d) lam[d] = A.lam_cur[d * N + cell];
+    const float Fx = P.Fx + P.bandF[kb], Fy = P.Fy + P.bandF[P.nband + kb], Fz = P.Fz + P.bandF[2 * P.nband + kb];
+    AdjExtra ex{0.0f, 0.0f, 0.0f, 0.0f, (x >= A.ke_x0 && x < A.ke_x1) ? A.wke : 0.0f};
+    float dFx = 0.0f, dFy = 0.0f, dFz = 0.0f;
+    collide_vjp(fs, Fx, Fy, Fz, P, ex, lam, dFx, dFy, dFz);
+    A.dF_band[kb] = dFx;
+    A.dF_band[P.nband + kb] = dFy;
+    A.dF_band[2 * P.nband + kb] = dFz;
+}
+
+__device__ __forceinline__ float cw(int c, float wx, float wy, float wz) {
+    return ((c & 1) ? wx : 1.0f - wx) * ((c & 2) ? wy : 1.0f - wy) * ((c & 4) ? wz : 1.0f - wz);
+}
+
+// per sample: dL/dg = interpolated dL/dF + drag weight; dL/d rho_s, dL/du_s (Eq. 7 transposed);
+// position gradient from the spreading and interpolation weights (Eqs. 6 and 8)
+__global__ void __launch_bounds__(256) k_adj_samples(long long S, long long nband, const float *__restrict__ X,
+                                                     const float *__restrict__ area, const float *__restrict__ ub,
+                                                     const int *__restrict__ corner_band,
+                                                     const float *__restrict__ band_rho, const float *__restrict__ band_u,
+                                                     const float *__restrict__ g, const float *__restrict__ dF,
+                                                     float drag_w, float *__restrict__ adj_samp, double *__restrict__ dX) {
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    const float wx = X[s] - floorf(X[s]), wy = X[S + s] - floorf(X[S + s]), wz = X[2 * S + s] - floorf(X[2 * S + s]);
+    float dgx = drag_w, dgy = 0.0f, dgz = 0.0f, rs = 0.0f, us = 0.0f, vs = 0.0f, ws = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const int b = corner_band[(long long)c * S + s];
+        const float Kc = cw(c, wx, wy, wz);
+        dgx = fmaf(Kc, dF[b], dgx);
+        dgy = fmaf(Kc, dF[nband + b], dgy);
+        dgz = fmaf(Kc, dF[2 * nband + b], dgz);
+        rs = fmaf(Kc, band_rho[b], rs);
+        us = fmaf(Kc, band_u[b], us);
+        vs = fmaf(Kc, band_u[nband + b], vs);
+        ws = fmaf(Kc, band_u[2 * nband + b], ws);
+    }
+    const float a = area[s];
+    const float drs = a * ((ub[s] - us) * dgx + (ub[S + s] - vs) * dgy + (ub[2 * S + s] - ws) * dgz);
+    const float dus = -rs * a * dgx, dvs = -rs * a * dgy, dws = -rs * a * dgz;
+    adj_samp[s] = drs;
+    adj_samp[S + s] = dus;
+    adj_samp[2 * S + s] = dvs;
+    adj_samp[3 * S + s] = dws;
+    const float gx = g[s], gy = g[S + s], gz = g[2 * S + s];
+    float px = 0.0f, py = 0.0f, pz = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const int b = corner_band[(long long)c * S + s];
+        const float kx = (c & 1) ? wx : 1.0f - wx, ky = (c & 2) ? wy : 1.0f - wy, kz = (c & 4) ? wz : 1.0f - wz;
+        const float sx = (c & 1) ? 1.0f : -1.0f, sy = (c & 2) ? 1.0f : -1.0f, sz = (c & 4) ? 1.0f : -1.0f;
+        // value the corner weight multiplies: spreading (dF . g) and interpolation (rho*, u_IB)
+        const float v = dF[b] * gx + dF[nband + b] * gy + dF[2 * nband + b] * gz + drs * band_rho[b] +
+                        dus * band_u[b] + dvs * band_u[nband + b] + dws * band_u[2 * nband + b];
+        px = fmaf(sx * ky * kz, v, px);
+        py = fmaf(sy * kx * kz, v, py);
+        pz = fmaf(sz * kx * ky, v, pz);
+    }
+    dX[s] += px;
+    dX[S + s] += py;
+    dX[2 * S + s] += pz;
+}
+
+// per band node: gather dL/d rho*, dL/du_IB from the samples (transpose of Eq. 6), then
+// through u_IB = (j + F_body/2)/rho* to dL/d rho*, dL/dj
+__global__ void __launch_bounds__(256) k_adj_band_gather(long long S, long long nband, const float *__restrict__ X,
+                                                         const int *__restrict__ base_nbr, const int *__restrict__ cstart,
+                                                         const int *__restrict__ ccount, const float *__restrict__ adj_samp,
+                                                         const float *__restrict__ band_rho,
+                                                         const float *__restrict__ band_u, float *__restrict__ adj_band) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nband) return;
+    float dr = 0.0f, du = 0.0f, dv = 0.0f, dw = 0.0f;
+#pragma unroll 1
+    for (int c = 0; c < 8; ++c) {
+        const int b = base_nbr[(long long)c * nband + k];
+        if (b < 0) continue;
+        const int s0 = cstart[b], s1 = s0 + ccount[b];
+        for (int s = s0; s < s1; ++s) {
+            const float Kc = cw(c, X[s] - floorf(X[s]), X[S + s] - floorf(X[S + s]), X[2 * S + s] - floorf(X[2 * S + s]));
+            dr = fmaf(Kc, adj_samp[s], dr);
+            du = fmaf(Kc, adj_samp[S + s], du);
+            dv = fmaf(Kc, adj_samp[2 * S + s], dv);
+            dw = fmaf(Kc, adj_samp[3 * S + s], dw);
+        }
+    }
+    const float rho = band_rho[k], inv = 1.0f / rho;
+    const float u = band_u[k], v = band_u[nband + k], w = band_u[2 * nband + k];
+    adj_band[k] = dr - (du * u + dv * v + dw * w) * inv;
+    adj_band[nband + k] = du * inv;
+    adj_band[2 * nband + k] = dv * inv;
+    adj_band[3 * nband + k] = dw * inv;
+}
+
+// the backward step over all nodes: mu = dL/df* (collision VJP + IB + loss terms), pushed
+// along the transpose of the streaming into dL/df_{t-1}
+template <typename St, bool NB, bool BAND>
+__global__ void __launch_bounds__(128) k_adj_step(StepParams P, AdjParams A) {
+    const int cell = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= P.g.ncell) return;
+    int x, y, z;
+    adj_decompose(P.g, cell, x, y, z);
+    float fs[27], lam[27];
+    adj_load_fstar<St, NB>(P, x, y, z, cell, fs);
+    const long long N = P.g.ncell;
+#pragma unroll
+    for (int d = 0; d < 27; ++d) lam[d] = A.lam_cur[d * N + cell];
+    float Fx = P.Fx, Fy = P.Fy, Fz = P.Fz;
+    AdjExtra ex{0.0f, 0.0f, 0.0f, 0.0f, (x >= A.ke_x0 && x < A.ke_x1) ? A.wke : 0.0f};
+    if (BAND) {
+        long long b;
+        if (band_index(P, cell, b)) {
+            Fx += P.bandF[b];
+            Fy += P.bandF[P.nband + b];
+            Fz += P.bandF[2 * P.nband + b];
+            ex.drho = A.adj_band[b];
+            ex.djx = A.adj_band[P.nband + b];
+            ex.djy = A.adj_band[2 * P.nband + b];
+            ex.djz = A.adj_band[3 * P.nband + b];
+        }
+    }
+    float dFx = 0.0f, dFy = 0.0f, dFz = 0.0f;
+    collide_vjp(fs, Fx, Fy, Fz, P, ex, lam, dFx, dFy, dFz);
+    // push along the transposed streaming
+    double sth = 0.0;
+    const bool outlet_node = (x == P.g.nx - 1) && P.g.face[1] == FACE_OUTLET;
+#pragma unroll
+    for (int d = 0; d < 27; ++d) {
+        const Nbr n = neighbour<-1>(P.g, d, x, y, z);
+        const float mu = lam[d];
+        bool ghost = false;
+        if (n.kind == 0) {
+            A.lam_prev[d * N + n.idx] = mu;
+        } else if (n.kind & (CROSS_NOSLIP | CROSS_INLET)) {
+            A.lam_prev[opp(d) * N + cell] = mu;
+            if (!(n.kind & CROSS_NOSLIP)) sth += (double)mu * (6.0 * wgt(d) * P.rho0 * cx(d));
+        } else {
+            ghost = true;
+        }
+        if (outlet_node && cx(d) == -1) A.blam[(long long)(d / 3) * P.g.nyz + y + P.g.ny * z] = ghost ? mu : 0.0f;
+    }
+    if (x == 0 && P.g.face[0] == FACE_INLET) A.s_inlet[y + P.g.ny * z] += sth;
+}
+
+// outlet plane: zero the slots of the populations that left through the outlet (no use in
+// f*) and add the ghost duplicates dL/df_{t-1, d}(nx-1, y, z) += mu_d(nx-1, y + c_y, z + c_z)
+__global__ void __launch_bounds__(128) k_adj_outlet(StepParams P, AdjParams A) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P.g.nyz) return;
+    const int z = i / P.g.ny, y = i - z * P.g.ny, x = P.g.nx - 1;
+    const int cell = x + P.g.nx * (y + P.g.ny * z);
+    const long long N = P.g.ncell;
+#pragma unroll
+    for (int d = 0; d < 27; ++d) {
+        if (cx(d) == 1) {
+            const Nbr n = neighbour<+1>(P.g, d, x, y, z);
+            if (n.kind == CROSS_OUTLET) A.lam_prev[d * N + cell] = 0.0f;
+        } else if (cx(d) == -1) {
+            // the node (nx-1, y + c_y, z + c_z) pulled this slot through the ghost
+            int yy = y + cy(d), zz = z + cz(d);
+            bool ok = true;
+            if (yy < 0 || yy >= P.g.ny) { if (P.g.periodic[1]) yy = (yy + P.g.ny) % P.g.ny; else ok = false; }
+            if (zz < 0 || zz >= P.g.nz) { if (P.g.periodic[2]) zz = (zz + P.g.nz) % P.g.nz; else ok = false; }
+            if (ok) A.lam_prev[d * N + cell] += A.blam[(long long)(d / 3) * P.g.nyz + yy + P.g.ny * zz];
+        }
+    }
+}
+
+__global__ void k_finalize_add(const double *__restrict__ partial, long long n, int count, double *__restrict__ out) {
+    __shared__ double s[256];
+    for (int k = 0; k < count; ++k) {
+        double acc = 0.0;
+        for (long long i = threadIdx.x; i < n; i += blockDim.x) acc += partial[(long long)k * n + i];
+        s[threadIdx.x] = acc;
+        __syncthreads();
+        for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+            if (threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) out[k] += s[0];
+        __syncthreads();
+    }
+}
+
+unsigned nblocks(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+template <typename F> cudaError_t with_storage(int storage, F &&fn) {
+    switch (storage) {
+        case 0: return fn(float{});
+        case 1: return fn(__half{});
+        default: return fn(__nv_bfloat16{});
+    }
+}
+
+// pointers of one stored state: populations (27 planes) followed by the outlet plane
+void point_params(StepParams &P, const lbm_ctx *h, void *state) {
+    P.f = state;
+    for (int d = 0; d < 27; ++d) P.fp[d] = static_cast<char *>(state) + (size_t)d * h->plane * h->esize;
+    P.outlet = h->outlet ? static_cast<char *>(state) + (size_t)27 * h->plane * h->esize : nullptr;
+}
+
+struct AdjBuffers {
+    std::vector<void *> bufs;
+    ~AdjBuffers() {
+        for (void *p : bufs) cudaFree(p);
+    }
+    template <typename T> int get(lbm_ctx *h, T **p, size_t n) {
+        int rc = dev_alloc(h, p, n);
+        if (rc == LBM_OK && *p) bufs.push_back((void *)*p);
+        return rc;
+    }
+};
+
+}  // namespace
+
+extern "C" int lbm_adjoint(lbm_ctx *h, int n, int K, const lbm_loss *loss, double *dL_dinflow, double *dL_dpos,
+                           double *L) {
+    if (!h) return fail(nullptr, LBM_EINVAL, "null context");
+    if (!h->has_state) return fail(h, LBM_ESTATE, "lbm_set_state (or lbm_load) has not been called");
+    if (n < 1 || !loss) return fail(h, LBM_EINVAL, "n must be >= 1 and loss given");
+    if (loss->ke_x0 < 0 || loss->ke_x1 > h->nx || loss->ke_x0 > loss->ke_x1) return fail(h, LBM_EINVAL, "bad slab");
+    K = std::max(1, std::min(K, n));
+    const long long N = h->N, S = h->S, nb = h->nband;
+    const int nyz = h->ny * h->nz;
+    const size_t pop_bytes = (size_t)27 * h->plane * h->esize;
+    const size_t out_bytes = h->outlet ? (size_t)2 * 9 * nyz * h->esize : 0;
+    const size_t state_bytes = pop_bytes + out_bytes;
+    const int nck = (n + K - 1) / K;
+    AdjBuffers B;
+    int rc;
+    std::vector<char *> ckpt(nck), seg(K);
+    char *final_state = nullptr;
+    for (int i = 0; i < nck; ++i) if ((rc = B.get(h, &ckpt[i], state_bytes))) return rc;
+    for (int i = 0; i < K; ++i) if ((rc = B.get(h, &seg[i], state_bytes))) return rc;
+    if ((rc = B.get(h, &final_state, state_bytes))) return rc;
+    float *lamA, *lamB, *blam = nullptr, *dF_band = nullptr, *adj_band = nullptr, *adj_samp = nullptr;
+    double *s_inlet, *dX = nullptr, *acc;
+    if ((rc = B.get(h, &lamA, (size_t)27 * N)) || (rc = B.get(h, &lamB, (size_t)27 * N)) ||
+        (rc = B.get(h, &s_inlet, (size_t)nyz)) || (rc = B.get(h, &acc, 8)))
+        return rc;
+    if (h->outlet && (rc = B.get(h, &blam, (size_t)9 * nyz))) return rc;
+    if (S > 0 && ((rc = B.get(h, &dX, (size_t)3 * S)) || (rc = B.get(h, &dF_band, (size_t)3 * nb)) ||
+                  (rc = B.get(h, &adj_band, (size_t)4 * nb)) || (rc = B.get(h, &adj_samp, (size_t)4 * S))))
+        return rc;
+    const int fblk = force_sum_blocks();
+    StepParams P0 = make_params(h, h->t);
+    const long long mblk = macro_blocks(P0);
+    if ((rc = ensure_partial(h, (size_t)std::max<long long>(MACRO_SUMS * mblk, 3 * fblk)))) return rc;
+    cudaStream_t st = h->stream;
+    CK(cudaMemsetAsync(s_inlet, 0, nyz * sizeof(double), st));
+    CK(cudaMemsetAsync(acc, 0, 8 * sizeof(double), st));
+    if (dX) CK(cudaMemsetAsync(dX, 0, 3 * S * sizeof(double), st));
+    CK(cudaMemsetAsync(lamA, 0, (size_t)27 * N * sizeof(float), st));
+
+    // forward pass: checkpoints, drag accumulation, final kinetic energy
+    const long long t_start = h->t;
+    for (int i = 0; i < n; ++i) {
+        if (i % K == 0) {
+            CK(cudaMemcpyAsync(ckpt[i / K], h->f, pop_bytes, cudaMemcpyDeviceToDevice, st));
+            if (out_bytes) CK(cudaMemcpyAsync(ckpt[i / K] + pop_bytes, h->outlet, out_bytes, cudaMemcpyDeviceToDevice, st));
+        }
+        if ((rc = lbm_step(h, 1))) return rc;
+        if (S > 0) {
+            CK(launch_sum_forces(S, h->g, h->partial, st));
+            k_finalize_add<<<1, 256, 0, st>>>(h->partial, fblk, 3, acc);
+            CK(cudaGetLastError());
+        }
+    }
+    {
+        StepParams P = make_params(h, h->t);
+        CK(launch_macro(h->storage, P, S > 0, 1, nullptr, nullptr, nullptr, h->partial, nullptr, st, loss->ke_x0,
+                        loss->ke_x1));
+        k_finalize_add<<<1, 256, 0, st>>>(h->partial + 4 * mblk, mblk, 1, acc + 3);
+        CK(cudaGetLastError());
+    }
+    CK(cudaMemcpyAsync(final_state, h->f, pop_bytes, cudaMemcpyDeviceToDevice, st));
+    if (out_bytes) CK(cudaMemcpyAsync(final_state + pop_bytes, h->outlet, out_bytes, cudaMemcpyDeviceToDevice, st));
+    float *g_last = nullptr, *F_last = nullptr;     // IB diagnostics of the last step, restored at the end
+    if (S > 0) {
+        if ((rc = B.get(h, &g_last, (size_t)3 * S)) || (rc = B.get(h, &F_last, (size_t)3 * nb))) return rc;
+        CK(cudaMemcpyAsync(g_last, h->g, 3 * S * sizeof(float), cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(F_last, h->bandF, 3 * nb * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    }
+
+    // backward pass over the segments, last first
+    float *lam_cur = lamA, *lam_prev = lamB;
+    const float drag_w = (float)(-loss->w_drag / n);
+    for (int sgi = nck - 1; sgi >= 0; --sgi) {
+        const long long t0 = t_start + (long long)sgi * K;
+        const int len = (int)std::min<long long>(K, t_start + n - t0);
+        CK(cudaMemcpyAsync(h->f, ckpt[sgi], pop_bytes, cudaMemcpyDeviceToDevice, st));
+        if (out_bytes) CK(cudaMemcpyAsync(h->outlet, ckpt[sgi] + pop_bytes, out_bytes, cudaMemcpyDeviceToDevice, st));
+        h->t = t0;
+        for (int k = 0; k < len; ++k) {
+            CK(cudaMemcpyAsync(seg[k], h->f, pop_bytes, cudaMemcpyDeviceToDevice, st));
+            if (out_bytes) CK(cudaMemcpyAsync(seg[k] + pop_bytes, h->outlet, out_bytes, cudaMemcpyDeviceToDevice, st));
+            if (k < len - 1 && (rc = lbm_step(h, 1))) return rc;
+        }
+        for (long long t = t0 + len; t > t0; --t) {
+            StepParams P = make_params(h, t);
+            point_params(P, h, seg[t - 1 - t0]);
+            AdjParams A{};
+            A.lam_cur = lam_cur;
+            A.lam_prev = lam_prev;
+            A.blam = blam;
+            A.s_inlet = s_inlet;
+            A.adj_band = adj_band;
+            A.dF_band = dF_band;
+            A.wke = (t == t_start + n) ? (float)loss->w_ke : 0.0f;
+            A.ke_x0 = loss->ke_x0;
+            A.ke_x1 = loss->ke_x1;
+            const bool nbp = (t & 1) != 0;
+            if (S > 0) {
+                CK(launch_band_moments(h->storage, P, h->band_cell, h->band_rho, h->band_u, st));
+                CK(launch_ib_interp(S, nb, h->X, h->area, h->ub, h->corner_band, h->band_rho, h->band_u, h->g, st));
+                CK(launch_ib_spread(S, nb, h->X, h->g, h->base_nbr, h->cstart, h->ccount, h->bandF, st));
+                CK(with_storage(h->storage, [&](auto tag) {
+                    using St = decltype(tag);
+                    if (nbp) k_adj_band_force<St, true><<<nblocks(nb, 128), 128, 0, st>>>(P, A, h->band_cell);
+                    else k_adj_band_force<St, false><<<nblocks(nb, 128), 128, 0, st>>>(P, A, h->band_cell);
+                    return cudaGetLastError();
+                }));
+                k_adj_samples<<<nblocks(S, 256), 256, 0, st>>>(S, nb, h->X, h->area, h->ub, h->corner_band, h->band_rho,
+                                                               h->band_u, h->g, dF_band, drag_w, adj_samp, dX);
+                k_adj_band_gather<<<nblocks(nb, 256), 256, 0, st>>>(S, nb, h->X, h->base_nbr, h->cstart, h->ccount,
+                                                                    adj_samp, h->band_rho, h->band_u, adj_band);
+                CK(cudaGetLastError());
+            }
+            CK(with_storage(h->storage, [&](auto tag) {
+                using St = decltype(tag);
+                const unsigned g = nblocks(N, 128);
+                if (nbp) {
+                    if (S > 0) k_adj_step<St, true, true><<<g, 128, 0, st>>>(P, A);
+                    else k_adj_step<St, true, false><<<g, 128, 0, st>>>(P, A);
+                } else {
+                    if (S > 0) k_adj_step<St, false, true><<<g, 128, 0, st>>>(P, A);
+                    else k_adj_step<St, false, false><<<g, 128, 0, st>>>(P, A);
+                }
+                return cudaGetLastError();
+            }));
+            if (h->outlet) {
+                k_adj_outlet<<<nblocks(nyz, 128), 128, 0, st>>>(P, A);
+                CK(cudaGetLastError());
+            }
+            std::swap(lam_cur, lam_prev);
+        }
+    }
+    // restore the state reached by the forward pass
+    CK(cudaMemcpyAsync(h->f, final_state, pop_bytes, cudaMemcpyDeviceToDevice, st));
+    if (out_bytes) CK(cudaMemcpyAsync(h->outlet, final_state + pop_bytes, out_bytes, cudaMemcpyDeviceToDevice, st));
+    if (S > 0) {
+        CK(cudaMemcpyAsync(h->g, g_last, 3 * S * sizeof(float), cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(h->bandF, F_last, 3 * nb * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    }
+    h->t = t_start + n;
+
+    double hacc[8];
+    std::vector<double> sin_(nyz);
+    CK(cudaMemcpyAsync(hacc, acc, 8 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(sin_.data(), s_inlet, nyz * sizeof(double), cudaMemcpyDeviceToHost, st));
+    std::vector<double> dxs(S > 0 ? 3 * S : 0);
+    if (S > 0) CK(cudaMemcpyAsync(dxs.data(), dX, 3 * S * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (L) *L = loss->w_drag * (-hacc[0]) / n + loss->w_ke * hacc[3];
+    if (dL_dinflow) {
+        for (int m = 1; m <= 4; ++m)
+            for (int q = 1; q <= 4; ++q) {
+                double v = 0.0;
+                for (int z = 0; z < h->nz; ++z)
+                    for (int y = 0; y < h->ny; ++y)
+                        v += sin_[y + (size_t)h->ny * z] * std::sin(m * M_PI * (y + 0.5) / h->ny) *
+                             std::sin(q * M_PI * (z + 0.5) / h->nz);
+                dL_dinflow[(m - 1) * 4 + (q - 1)] = h->cfg.face_type[0] == LBM_FACE_INLET ? v : 0.0;
+            }
+    }
+    if (dL_dpos && S > 0) {
+        for (long long i = 0; i < S; ++i)
+            for (int a = 0; a < 3; ++a) dL_dpos[3 * h->order[i] + a] = dxs[a * S + i];
+    }
+    return LBM_OK;
+}

@@ -1,0 +1,187 @@
+// The solver context shared by the C-ABI translation units (lbm_api.cu, lbm_adjoint.cu)
+// and the host helpers they use.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "lbm.h"
+#include "lbm_internal.h"
+
+struct lbm_adjoint_buffers;
+
+struct EventRec {
+    int kind;
+    cudaEvent_t a, b;
+};
+
+struct lbm_ctx {
+    int nx = 0, ny = 0, nz = 0;
+    long long N = 0, plane = 0;
+    int storage = 0;
+    size_t esize = 4;
+    double nu = 0, forcing[3] = {0, 0, 0};
+    lbm_config cfg{};
+    cudaStream_t stream = nullptr;
+
+    void *f = nullptr;          // 27 * plane elements of the storage type
+    void *outlet = nullptr;     // 2 * 9 * ny * nz elements
+    float *inlet_profile = nullptr;
+    long long t = 0;
+    bool has_state = false;
+
+    // immersed solid (samples sorted by base cell)
+    long long S = 0, nband = 0, ntiles = 0;
+    float *X = nullptr, *area = nullptr, *ub = nullptr, *g = nullptr;
+    int *corner_band = nullptr, *band_cell = nullptr, *base_nbr = nullptr, *cstart = nullptr, *ccount = nullptr;
+    float *band_rho = nullptr, *band_u = nullptr, *bandF = nullptr;
+    uint32_t *tile_mask = nullptr;
+    int *tile_off = nullptr;
+    std::vector<long long> order;   // sorted position -> caller's sample index
+
+    // scratch of the reductions
+    double *partial = nullptr;
+    size_t partial_cap = 0;         // doubles
+    double *red = nullptr;          // 8 doubles
+    int *flag = nullptr;
+
+    // profiling
+    bool prof = false;
+    std::vector<EventRec> recs;
+    std::vector<cudaEvent_t> pool;
+    double ms[LBM_NUM_KERNEL_KINDS] = {};
+    long long launches[LBM_NUM_KERNEL_KINDS] = {};
+
+    std::string err;
+};
+
+namespace lbm_host {
+
+int fail(lbm_ctx *h, int code, const std::string &msg);
+
+#define CK(call)                                                                                 \
+    do {                                                                                         \
+        cudaError_t e_ = (call);                                                                 \
+        if (e_ != cudaSuccess) return fail(h, LBM_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+inline bool is_device_ptr(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <typename T>
+inline int dev_alloc(lbm_ctx *h, T **p, size_t count) {
+    *p = nullptr;
+    if (count == 0) return LBM_OK;
+    cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(h, LBM_ENOMEM, std::string("cudaMalloc of ") + std::to_string(count * sizeof(T)) + " bytes failed");
+    }
+    return LBM_OK;
+}
+
+template <typename T> inline void dev_free(T *&p) {
+    if (p) cudaFree((void *)p);
+    p = nullptr;
+}
+
+inline cudaEvent_t pool_event(lbm_ctx *h) {
+    if (!h->pool.empty()) {
+        cudaEvent_t e = h->pool.back();
+        h->pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+struct Timed {
+    lbm_ctx *h;
+    int kind;
+    cudaEvent_t a = nullptr;
+    Timed(lbm_ctx *h_, int k, int nlaunch = 1) : h(h_), kind(k) {
+        h->launches[kind] += nlaunch;
+        if (h->prof) {
+            a = pool_event(h);
+            cudaEventRecord(a, h->stream);
+        }
+    }
+    ~Timed() {
+        if (h->prof) {
+            cudaEvent_t b = pool_event(h);
+            cudaEventRecord(b, h->stream);
+            h->recs.push_back({kind, a, b});
+        }
+    }
+};
+
+inline lbm::StepParams make_params(const lbm_ctx *h, long long t) {
+    lbm::StepParams P{};
+    P.f = h->f;
+    for (int d = 0; d < 27; ++d) P.fp[d] = static_cast<char *>(h->f) + (size_t)d * h->plane * h->esize;
+    P.outlet = h->outlet;
+    lbm::Geometry &g = P.g;
+    g.nx = h->nx; g.ny = h->ny; g.nz = h->nz;
+    g.nxy = h->nx * h->ny;
+    g.ncell = (int)h->N;
+    g.nyz = h->ny * h->nz;
+    g.plane = h->plane;
+    for (int a = 0; a < 3; ++a) g.periodic[a] = h->cfg.face_type[2 * a] == LBM_FACE_PERIODIC;
+    for (int k = 0; k < 6; ++k) g.face[k] = h->cfg.face_type[k];
+    P.rho0 = (float)h->cfg.rho0;
+    P.Fx = (float)h->forcing[0];
+    P.Fy = (float)h->forcing[1];
+    P.Fz = (float)h->forcing[2];
+    const double ws = 1.0 / (3.0 * h->nu + 0.5);
+    P.rs = (float)(1.0 - ws);
+    P.rb = (float)(1.0 - h->cfg.omega_bulk);
+    P.r3 = (float)(1.0 - h->cfg.omega_hi[0]);
+    P.r4 = (float)(1.0 - h->cfg.omega_hi[1]);
+    P.r5 = (float)(1.0 - h->cfg.omega_hi[2]);
+    P.r6 = (float)(1.0 - h->cfg.omega_hi[3]);
+    P.q3 = (float)(1.0 - 0.5 * h->cfg.omega_hi[0]);
+    P.q5 = (float)(1.0 - 0.5 * h->cfg.omega_hi[2]);
+    P.u_in = (float)h->cfg.u_in;
+    P.noise = (float)h->cfg.inlet_noise;
+    P.seed = h->cfg.seed;
+    P.t = t;
+    P.inlet_profile = h->inlet_profile;
+    P.tile_mask = h->tile_mask;
+    P.tile_off = h->tile_off;
+    P.bandF = h->bandF;
+    P.nband = h->nband;
+    return P;
+}
+
+inline int ensure_partial(lbm_ctx *h, size_t doubles) {
+    if (doubles <= h->partial_cap) return LBM_OK;
+    dev_free(h->partial);
+    h->partial_cap = 0;
+    int rc = dev_alloc(h, &h->partial, doubles);
+    if (rc) return rc;
+    h->partial_cap = doubles;
+    return LBM_OK;
+}
+
+inline void free_solid(lbm_ctx *h) {
+    dev_free(h->X); dev_free(h->area); dev_free(h->ub); dev_free(h->g);
+    dev_free(h->corner_band); dev_free(h->band_cell); dev_free(h->base_nbr);
+    dev_free(h->cstart); dev_free(h->ccount);
+    dev_free(h->band_rho); dev_free(h->band_u); dev_free(h->bandF);
+    dev_free(h->tile_mask); dev_free(h->tile_off);
+    h->S = h->nband = h->ntiles = 0;
+    h->order.clear();
+}
+
+
+}  // namespace lbm_host

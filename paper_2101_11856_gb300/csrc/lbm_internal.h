@@ -15,8 +15,10 @@ long long boundary_count(const Geometry &g);
 inline bool has_interior(const Geometry &g) { return g.nx > 2; }
 cudaError_t launch_init(int storage, const StepParams &P, const float *rho, const float *u, cudaStream_t st);
 long long macro_blocks(const StepParams &P);
+// rows of the k_macro partial sums: mass, momentum x/y/z, slab kinetic energy
+constexpr int MACRO_SUMS = 5;
 cudaError_t launch_macro(int storage, const StepParams &P, bool band, int force_on, float *rho, float *u, float *f,
-                         double *partial, int *nonfinite, cudaStream_t st);
+                         double *partial, int *nonfinite, cudaStream_t st, int ke_x0 = 0, int ke_x1 = 0);
 cudaError_t launch_finalize(const double *partial, long long n, int count, double *out, cudaStream_t st);
 cudaError_t launch_band_moments(int storage, const StepParams &P, const int *band_cell, float *band_rho, float *band_u,
                                 cudaStream_t st);

@@ -11,6 +11,8 @@
 // the node's own slot A[d][x] (the previous step wrote the reflected value there), which
 // gives half-way bounce-back (the paper's Algorithm 1) and the moving-wall inlet; the
 // outlet reads a ping-pong copy of the outlet plane's previous post-collision values.
+#include <algorithm>
+
 #include "lbm_device.cuh"
 #include "lbm_internal.h"
 
@@ -280,14 +282,15 @@ __device__ __forceinline__ void load_post(const StepParams &P, int x, int y, int
 }
 
 // per-cell rho and Guo-shifted u of the last collision, optional field output and FP64
-// block partial sums (mass, momentum) for the deterministic global reduction
+// block partial sums for the deterministic global reductions: mass, momentum (3) and the
+// kinetic energy 1/2 rho |u|^2 of the slab ke_x0 <= x < ke_x1 (grid-stride over the cells)
 template <typename St, bool AFTER_NB, bool BAND>
 __global__ void __launch_bounds__(256) k_macro(StepParams P, int force_on, float *__restrict__ rho_out,
                                                float *__restrict__ u_out, float *__restrict__ f_out,
-                                               double *__restrict__ partial, int *__restrict__ nonfinite) {
-    const int cell = blockIdx.x * blockDim.x + threadIdx.x;
-    double m = 0.0, jx = 0.0, jy = 0.0, jz = 0.0;
-    if (cell < P.g.ncell) {
+                                               double *__restrict__ partial, int *__restrict__ nonfinite,
+                                               int ke_x0, int ke_x1) {
+    double acc[MACRO_SUMS] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int cell = blockIdx.x * blockDim.x + threadIdx.x; cell < P.g.ncell; cell += gridDim.x * blockDim.x) {
         int x, y, z;
         decompose(P.g, cell, x, y, z);
         float h[27];
@@ -306,19 +309,7 @@ __global__ void __launch_bounds__(256) k_macro(StepParams P, int force_on, float
             if (cz(d)) pz += cz(d) * h[d];
         }
         float Fx = 0.0f, Fy = 0.0f, Fz = 0.0f;
-        if (force_on) {
-            Fx = P.Fx; Fy = P.Fy; Fz = P.Fz;
-            if (BAND) {
-                const uint32_t mask = P.tile_mask[cell >> 5];
-                const int lane = cell & 31;
-                if ((mask >> lane) & 1u) {
-                    const long long b = P.tile_off[cell >> 5] + __popc(mask & ((1u << lane) - 1u));
-                    Fx += P.bandF[b];
-                    Fy += P.bandF[P.nband + b];
-                    Fz += P.bandF[2 * P.nband + b];
-                }
-            }
-        }
+        if (force_on) band_force<BAND>(P, cell, Fx, Fy, Fz);
         // post-collision momentum is j + F, so rho u = sum c f_post - F/2
         const float rho = P.rho0 + rp;
         const float jxs = px - 0.5f * Fx, jys = py - 0.5f * Fy, jzs = pz - 0.5f * Fz;
@@ -331,26 +322,29 @@ __global__ void __launch_bounds__(256) k_macro(StepParams P, int force_on, float
         }
         if (nonfinite && !(isfinite(rho) && isfinite(jxs * inv) && isfinite(jys * inv) && isfinite(jzs * inv)))
             atomicOr(nonfinite, 1);
-        m = (double)rho;
-        jx = (double)jxs;
-        jy = (double)jys;
-        jz = (double)jzs;
+        acc[0] += (double)rho;
+        acc[1] += (double)jxs;
+        acc[2] += (double)jys;
+        acc[3] += (double)jzs;
+        if (x >= ke_x0 && x < ke_x1)
+            acc[4] += 0.5 * ((double)jxs * jxs + (double)jys * jys + (double)jzs * jzs) / (double)rho;
     }
     if (partial) {
         // fixed-order block tree reduction in FP64
-        __shared__ double s[4][256];
-        s[0][threadIdx.x] = m; s[1][threadIdx.x] = jx; s[2][threadIdx.x] = jy; s[3][threadIdx.x] = jz;
+        __shared__ double s[MACRO_SUMS][256];
+#pragma unroll
+        for (int k = 0; k < MACRO_SUMS; ++k) s[k][threadIdx.x] = acc[k];
         __syncthreads();
         for (int w = blockDim.x / 2; w > 0; w >>= 1) {
             if (threadIdx.x < w) {
 #pragma unroll
-                for (int k = 0; k < 4; ++k) s[k][threadIdx.x] += s[k][threadIdx.x + w];
+                for (int k = 0; k < MACRO_SUMS; ++k) s[k][threadIdx.x] += s[k][threadIdx.x + w];
             }
             __syncthreads();
         }
         if (threadIdx.x == 0) {
 #pragma unroll
-            for (int k = 0; k < 4; ++k) partial[(long long)k * gridDim.x + blockIdx.x] = s[k][0];
+            for (int k = 0; k < MACRO_SUMS; ++k) partial[(long long)k * gridDim.x + blockIdx.x] = s[k][0];
         }
     }
 }
@@ -526,21 +520,21 @@ cudaError_t launch_init(int storage, const StepParams &P, const float *rho, cons
     });
 }
 
-long long macro_blocks(const StepParams &P) { return blocks_for(P.g.ncell, 256); }
+long long macro_blocks(const StepParams &P) { return std::min<long long>(blocks_for(P.g.ncell, 256), 2432); }
 
 cudaError_t launch_macro(int storage, const StepParams &P, bool band, int force_on, float *rho, float *u, float *f,
-                         double *partial, int *nonfinite, cudaStream_t st) {
+                         double *partial, int *nonfinite, cudaStream_t st, int ke_x0, int ke_x1) {
     // the state after step t was written by a neighbour step when t is odd
     const bool after_nb = (P.t & 1) != 0;
     return dispatch_storage(storage, [&](auto tag) {
         using St = decltype(tag);
-        const unsigned grid = blocks_for(P.g.ncell, 256);
+        const unsigned grid = (unsigned)macro_blocks(P);
         if (after_nb) {
-            if (band) k_macro<St, true, true><<<grid, 256, 0, st>>>(P, force_on, rho, u, f, partial, nonfinite);
-            else k_macro<St, true, false><<<grid, 256, 0, st>>>(P, force_on, rho, u, f, partial, nonfinite);
+            if (band) k_macro<St, true, true><<<grid, 256, 0, st>>>(P, force_on, rho, u, f, partial, nonfinite, ke_x0, ke_x1);
+            else k_macro<St, true, false><<<grid, 256, 0, st>>>(P, force_on, rho, u, f, partial, nonfinite, ke_x0, ke_x1);
         } else {
-            if (band) k_macro<St, false, true><<<grid, 256, 0, st>>>(P, force_on, rho, u, f, partial, nonfinite);
-            else k_macro<St, false, false><<<grid, 256, 0, st>>>(P, force_on, rho, u, f, partial, nonfinite);
+            if (band) k_macro<St, false, true><<<grid, 256, 0, st>>>(P, force_on, rho, u, f, partial, nonfinite, ke_x0, ke_x1);
+            else k_macro<St, false, false><<<grid, 256, 0, st>>>(P, force_on, rho, u, f, partial, nonfinite, ke_x0, ke_x1);
         }
         return cudaGetLastError();
     });

@@ -34,6 +34,10 @@ class lbm_config(C.Structure):
                 ("omega_bulk", C.c_double), ("omega_hi", C.c_double * 4), ("cuda_stream", C.c_void_p)]
 
 
+class lbm_loss(C.Structure):
+    _fields_ = [("w_drag", C.c_double), ("w_ke", C.c_double), ("ke_x0", C.c_int), ("ke_x1", C.c_int)]
+
+
 _SIGS = {
     "lbm_config_default": (None, [C.POINTER(lbm_config)]),
     "lbm_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_int, C.c_double,
@@ -55,6 +59,8 @@ _SIGS = {
     "lbm_profile": (C.c_int, [C.c_void_p, C.c_int]),
     "lbm_kernel_times": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
     "lbm_band_size": (C.c_longlong, [C.c_void_p]),
+    "lbm_adjoint": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.POINTER(lbm_loss), C.POINTER(C.c_double),
+                              C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "lbm_sum_forces_static": (C.c_int, [C.c_void_p, C.c_longlong, C.c_void_p, C.c_void_p]),
     "lbm_last_error": (C.c_char_p, [C.c_void_p]),
 }
@@ -202,6 +208,16 @@ def lbm_band_size(h):
     return library().lbm_band_size(h)
 
 
+def lbm_adjoint(h, n, K, w_drag=1.0, w_ke=0.0, ke_x0=0, ke_x1=0, count=0):
+    """Run n steps with the adjoint; returns (L, dL/d inflow coefficients (16,), dL/dX (count, 3))."""
+    loss = lbm_loss(w_drag, w_ke, ke_x0, ke_x1)
+    dinf = (C.c_double * 16)()
+    dpos = (C.c_double * max(3 * count, 1))()
+    L = C.c_double()
+    _check(library().lbm_adjoint(h, int(n), int(K), C.byref(loss), dinf, dpos, C.byref(L)), h)
+    return L.value, np.array(dinf[:]), np.array(dpos[: 3 * count]).reshape(count, 3)
+
+
 def lbm_sum_forces_static(g, out, stream=None):
     """Allocation-free FP64 sum of per-sample forces: g (S, 3) float32 CUDA tensor, out (3,)
     float64 CUDA tensor; launched on ``stream`` (default: torch's current stream)."""
@@ -284,6 +300,9 @@ class Solver:
         f = np.empty((27,) + self.shape, np.float32)
         lbm_populations(self.h, f)
         return f
+
+    def adjoint(self, n, K=20, w_drag=1.0, w_ke=0.0, ke_x0=0, ke_x1=0, count=0):
+        return lbm_adjoint(self.h, n, K, w_drag, w_ke, ke_x0, ke_x1, count)
 
     @property
     def time(self):

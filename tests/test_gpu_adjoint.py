@@ -1,0 +1,103 @@
+"""GPU adjoint (through the C ABI) against the FP64 oracle's reverse-mode gradients.
+
+The oracle's gradients are pinned to central finite differences (test_oracle_adjoint.py);
+here the FP32 hand-written adjoint must match them: loss to 1e-5 relative, gradient vectors
+to 1e-3 relative L2 (FP32 arithmetic in forward and backward over a few steps)."""
+import numpy as np
+import pytest
+import torch
+
+import scenes
+from gpu_helpers import need_gpu, rel_l2
+from oracle.adjoint import Loss, loss_and_gradients
+from oracle.solver import Problem
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(autouse=True)
+def _gpu():
+    need_gpu()
+
+
+def run_both(nx, ny, nz, nu, n, K, loss, faces, rho, u, X=None, A=None, ub=None, coef=None, u_in=0.0, noise=0.0,
+             forcing=(0.0, 0.0, 0.0), rates=None):
+    from paper_2101_11856_gb300 import Solver
+    rates = rates or dict(omega_bulk=1.0, omega_hi=(1.0, 1.0, 1.0, 1.0))
+    s = Solver(nx, ny, nz, nu, forcing=forcing, faces=faces, u_in=u_in, noise=noise, seed=11, inflow_coef=coef, **rates)
+    s.set_state(rho, u)
+    count = 0
+    if X is not None:
+        s.set_solids(X, A, ub)
+        count = len(X)
+    Lg, dcg, dxg = s.adjoint(n, K, loss.w_drag, loss.w_ke, loss.ke_x0, loss.ke_x1, count)
+    p = Problem(nx, ny, nz, nu=nu, forcing=forcing, faces=faces, u_in=u_in, noise=noise, seed=11,
+                omega_bulk=rates["omega_bulk"], omega_hi=tuple(rates["omega_hi"]))
+    c = np.zeros(16) if coef is None else coef
+    Xo = np.zeros((0, 3)) if X is None else X.astype(np.float32).astype(np.float64)
+    Lo, dco, dxo = loss_and_gradients(p, rho, u, Xo, A, ub, c, n, loss) if X is not None else (None, None, None)
+    return s, (Lg, dcg, dxg), (Lo, dco, dxo)
+
+
+def test_channel_sphere_drag_and_ke_with_segments():
+    nx, ny, nz = 14, 8, 8
+    faces = ("inlet", "outlet", "periodic", "periodic", "periodic", "periodic")
+    X, A = scenes.fibonacci_sphere((5.3, 3.6, 3.4), 1.7, 24)
+    rho, u = scenes.uniform_flow(nx, ny, nz, (0.04, 0, 0))
+    coef = np.random.default_rng(1).uniform(-0.005, 0.005, 16)
+    loss = Loss(1.0, 2.0, 10, 13)
+    for K in (6, 4, 1):
+        s, (Lg, dcg, dxg), (Lo, dco, dxo) = run_both(nx, ny, nz, 0.05, 6, K, loss, faces, rho, u, X, A, coef=coef,
+                                                     u_in=0.04, noise=0.01)
+        print(f"K={K}: L {Lg:.6e} vs {Lo:.6e}; rel dtheta {rel_l2(dcg, dco.numpy()):.2e}; rel dX {rel_l2(dxg, dxo.numpy()):.2e}")
+        assert abs(Lg - Lo) <= 1e-5 * abs(Lo)
+        assert rel_l2(dcg, dco.numpy()) <= 1e-3
+        assert rel_l2(dxg, dxo.numpy()) <= 1e-3
+        assert s.time == 6
+
+
+def test_periodic_box_forced_distinct_rates():
+    n = 10
+    rho, u = scenes.taylor_green(n, n, n, 0.04)
+    X, A = scenes.fibonacci_sphere((4.6, 5.2, 4.9), 2.4, 40)
+    ub = np.tile([0.01, -0.005, 0.002], (40, 1))
+    rates = dict(omega_bulk=1.3, omega_hi=(1.2, 0.9, 1.45, 1.1))
+    loss = Loss(1.0, 0.5, 2, 7)
+    s, (Lg, dcg, dxg), (Lo, dco, dxo) = run_both(n, n, n, 0.03, 5, 2, loss, ("periodic",) * 6, rho, u, X, A, ub,
+                                                 forcing=(1e-5, -2e-5, 0), rates=rates)
+    print(f"L {Lg:.6e} vs {Lo:.6e}; rel dX {rel_l2(dxg, dxo.numpy()):.2e}")
+    assert abs(Lg - Lo) <= 1e-5 * abs(Lo)
+    assert rel_l2(dxg, dxo.numpy()) <= 1e-3
+    assert np.all(dcg == 0.0)
+
+
+def test_noslip_walls_outlet_ke_only():
+    nx, ny, nz = 12, 7, 6
+    faces = ("inlet", "outlet", "noslip", "noslip", "noslip", "noslip")
+    rho, u = scenes.uniform_flow(nx, ny, nz, (0.03, 0, 0))
+    X, A = scenes.fibonacci_sphere((4.5, 3.1, 2.6), 1.2, 12)
+    coef = np.random.default_rng(2).uniform(-0.004, 0.004, 16)
+    loss = Loss(0.0, 1.0, 6, 12)
+    s, (Lg, dcg, dxg), (Lo, dco, dxo) = run_both(nx, ny, nz, 0.04, 7, 3, loss, faces, rho, u, X, A, coef=coef,
+                                                 u_in=0.03)
+    print(f"L {Lg:.6e} vs {Lo:.6e}; rel dtheta {rel_l2(dcg, dco.numpy()):.2e}; rel dX {rel_l2(dxg, dxo.numpy()):.2e}")
+    assert abs(Lg - Lo) <= 1e-5 * abs(Lo)
+    assert rel_l2(dcg, dco.numpy()) <= 1e-3
+    assert rel_l2(dxg, dxo.numpy()) <= 1e-3
+
+
+def test_adjoint_advances_state_like_forward_steps():
+    from paper_2101_11856_gb300 import Solver
+    nx, ny, nz = 16, 9, 8
+    faces = ("inlet", "outlet", "periodic", "periodic", "noslip", "noslip")
+    rho, u = scenes.uniform_flow(nx, ny, nz, (0.04, 0, 0))
+    X, A = scenes.fibonacci_sphere((6.0, 4.2, 3.7), 2.0, 30)
+    a = Solver(nx, ny, nz, 0.04, faces=faces, u_in=0.04, noise=0.01)
+    b = Solver(nx, ny, nz, 0.04, faces=faces, u_in=0.04, noise=0.01)
+    for s in (a, b):
+        s.set_state(rho, u)
+        s.set_solids(X, A)
+    a.adjoint(7, 3, 1.0, 1.0, 8, 16, 30)
+    b.step(7)
+    assert np.array_equal(a.populations(), b.populations())
+    assert np.allclose(a.reductions()[2], b.reductions()[2], rtol=0, atol=0)
