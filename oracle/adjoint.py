@@ -61,7 +61,10 @@ def loss_and_gradients(p: Problem, rho, u, X, area, u_b, coef, n: int, loss: Los
     u_b = torch.zeros(3, S, dtype=DTYPE) if u_b is None else torch.as_tensor(np.asarray(u_b), dtype=DTYPE).T
     ct = torch.as_tensor(np.asarray(coef), dtype=DTYPE).clone().requires_grad_(True)
     L = run_loss(p, rho, u, Xt, area, u_b, ct, n, loss)
-    gc, gX = torch.autograd.grad(L, [ct, Xt])
+    gc, gX = torch.autograd.grad(L, [ct, Xt], allow_unused=True)
+    # a parameter the loss does not depend on (no inlet, no solid) has zero gradient
+    gc = torch.zeros_like(ct) if gc is None else gc
+    gX = torch.zeros_like(Xt) if gX is None else gX
     return float(L.detach()), gc.detach(), gX.detach()
 
 
