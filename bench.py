@@ -31,7 +31,7 @@ BYTES_PER_CELL = {"f32": 216, "f16": 108, "bf16": 108}   # 27 loads + 27 stores 
 PAPER_MLUPS = 1200 * 250 * 840 / 1.21 / 1e6                # Table 3, Fig. 1 scene: 1.21 s/step on 4x P40
 # DRAM bytes per cell of k_step_main (FP32) from one ncu capture of the current kernel
 # (profiles/k_step_main_box_city_480x100x336.md); None once the kernel changes
-TRAFFIC_PER_CELL = {"f32": 214.0}
+TRAFFIC_PER_CELL = {"f32": None}
 
 
 def parse():
@@ -266,7 +266,8 @@ def main():
         ms_max = float(t.item())
     ms_step = ms_max / args.steps
     mlups = world * N / (ms_step * 1e-3) / 1e6
-    n_int = max(nx - 2, 0) * ny * nz     # cells of the main step kernel (1 <= x <= nx-2)
+    xedge = 32                            # edge strip of the face kernel (XEDGE in lbm_internal.h)
+    n_int = max(nx - 2 * xedge, 0) * ny * nz if nx >= 2 * xedge + 1 else 0   # cells of k_step_main
     step_ms, step_n = kt["step"]
     k_ms = step_ms / max(step_n, 1)
     achieved = BYTES_PER_CELL["f32"] * n_int / (k_ms * 1e-3) / 1e9
@@ -340,7 +341,7 @@ def main():
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": TRAFFIC_PER_CELL["f32"] * n_int if TRAFFIC_PER_CELL.get("f32") else None,
-                         "kernel": "k_step_main (fused stream+collide, 1 <= x <= nx-2)",
+                         "kernel": "k_step_main (fused stream+collide, 32 <= x < nx-32)",
                          "cells_per_launch": n_int, "bytes_per_cell": 216,
                          "peak_kind": peak_kind},
             "kernel_ms": breakdown,

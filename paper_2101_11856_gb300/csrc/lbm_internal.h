@@ -8,11 +8,15 @@
 namespace lbm {
 
 enum { STEP_BOUNDARY = 0, STEP_INTERIOR = 1 };
-// one part of the fused step: the x-face columns (STEP_BOUNDARY) or every node with
-// 1 <= x <= nx-2 (STEP_INTERIOR)
+// The x range is split into two edge strips of XEDGE nodes per row, run by the general face
+// kernel in whole coalesced warps (STEP_BOUNDARY), and the nodes XEDGE <= x < nx - XEDGE,
+// run by the main kernel (STEP_INTERIOR).  Rows shorter than 2 XEDGE + 1 run entirely in the
+// face kernel.
+constexpr int XEDGE = 32;
 cudaError_t launch_step(int storage, const StepParams &P, bool band, int part, cudaStream_t st);
 long long boundary_count(const Geometry &g);
-inline bool has_interior(const Geometry &g) { return g.nx > 2; }
+__host__ __device__ inline bool has_interior(const Geometry &g) { return g.nx >= 2 * XEDGE + 1; }
+__host__ __device__ inline int edge_per_row(const Geometry &g) { return has_interior(g) ? 2 * XEDGE : g.nx; }
 cudaError_t launch_init(int storage, const StepParams &P, const float *rho, const float *u, cudaStream_t st);
 long long macro_blocks(const StepParams &P);
 // rows of the k_macro partial sums: mass, momentum x/y/z, slab kinetic energy

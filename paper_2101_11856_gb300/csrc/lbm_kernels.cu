@@ -178,16 +178,16 @@ __device__ __forceinline__ void store_yzface(const StepParams &P, int y, int z, 
 
 // ---- the fused step ---------------------------------------------------------------------
 // One thread per cell: pull the 27 streamed populations, add the body force and the band's
-// immersed-boundary force, collide in registers, store in place.  k_step_main updates every
-// node with 1 <= x <= nx-2: one block row per (y, z), so a block's y/z face status is uniform
-// (interior rows use constant offsets; face rows of odd steps use wrapped or bounced rows;
-// even steps address only the node's own slots).  k_step_xfaces updates the x = 0 and
-// x = nx-1 columns with the general face rules (inlet, outlet).  Every node is updated by
-// exactly one of the two, and the two touch disjoint slots.
+// immersed-boundary force, collide in registers, store in place.  k_step_main updates the
+// nodes XEDGE <= x < nx - XEDGE: one block row per (y, z), so a block's y/z face status is
+// uniform (interior rows use constant offsets; face rows of odd steps use wrapped or bounced
+// rows; even steps address only the node's own slots).  k_step_edges updates the two edge
+// strips of each row with the general face rules (inlet, outlet, x wrap) in whole warps.
+// Every node is updated by exactly one of the two, and the two touch disjoint slots.
 template <typename St, bool NB, bool BAND>
 __global__ void __launch_bounds__(STEP_BX) k_step_main(StepParams P) {
-    const int x = blockIdx.x * STEP_BX + threadIdx.x + 1;
-    if (x > P.g.nx - 2) return;
+    const int x = blockIdx.x * STEP_BX + threadIdx.x + XEDGE;
+    if (x >= P.g.nx - XEDGE) return;
     const int y = blockIdx.y, z = blockIdx.z;
     const int cell = x + P.g.nx * (y + P.g.ny * z);
     const bool inner = y >= 1 && y <= P.g.ny - 2 && z >= 1 && z <= P.g.nz - 2;   // uniform per block
@@ -202,29 +202,97 @@ __global__ void __launch_bounds__(STEP_BX) k_step_main(StepParams P) {
     else store_yzface<St>(P, y, z, cell, h);
 }
 
-// x-face node number i -> (x, y, z), i = side + nxb (y + ny z)
-__device__ __forceinline__ void xface_cell(const Geometry &g, int i, int &x, int &y, int &z) {
-    const int nxb = g.nx > 1 ? 2 : 1;
-    const int r = i / nxb;
-    x = (i - r * nxb) ? g.nx - 1 : 0;
-    z = r / g.ny;
-    y = r - z * g.ny;
+// ---- the edge strips: y/z faces per block, x faces per lane --------------------------------
+// Same pull/push rules as load_general/store_general, arranged for a block that covers one
+// strip of one (y, z) row: the y/z rows come from yz_rows (uniform), and only the lanes at
+// x = 0 or x = nx-1 take the x-face rule for the directions whose source (pull) or target
+// (push) lies across that face.  Priority at edges: no-slip > inlet > outlet.
+template <typename St, bool NB>
+__device__ __forceinline__ void load_edge(const StepParams &P, int x, int y, int z, int cell, float (&h)[27]) {
+    int off[9];
+    bool bb[9];
+    yz_rows<-1>(P.g, y, z, off, bb);
+    const bool xlo = x == 0, xhi = x == P.g.nx - 1;
+    const float uw = (xlo && P.g.face[0] == FACE_INLET) ? inlet_velocity(P, y, z) : 0.0f;
+#pragma unroll
+    for (int d = 0; d < 27; ++d) {
+        const int j = d / 3;
+        const bool xcross = (cx(d) == 1 && xlo) || (cx(d) == -1 && xhi);
+        const St *own = static_cast<const St *>(P.fp[d]) + cell;
+        if (!xcross) {
+            h[d] = (NB && !bb[j]) ? Store<St>::ld(static_cast<const St *>(P.fp[opp(d)]) + (cell + off[j]) - cx(d))
+                                  : Store<St>::ld(own);
+            continue;
+        }
+        const int ft = P.g.face[cx(d) == 1 ? 0 : 1];
+        if (bb[j] || ft == FACE_NOSLIP) {
+            h[d] = Store<St>::ld(own);
+        } else if (ft == FACE_PERIODIC) {
+            h[d] = NB ? Store<St>::ld(static_cast<const St *>(P.fp[opp(d)]) + (cell + off[j] + cx(d) * (P.g.nx - 1)))
+                      : Store<St>::ld(own);
+        } else if (ft == FACE_INLET) {
+            h[d] = Store<St>::ld(own) + 6.0f * wgt(d) * P.rho0 * (float)cx(d) * uw;
+        } else {
+            // outlet ghost: post-collision f_d of (nx-1, y - c_dy, z - c_dz) of the previous step
+            int ys = y - cy(d), zs = z - cz(d);
+            ys += ys < 0 ? P.g.ny : (ys >= P.g.ny ? -P.g.ny : 0);
+            zs += zs < 0 ? P.g.nz : (zs >= P.g.nz ? -P.g.nz : 0);
+            const St *B = static_cast<const St *>(P.outlet);
+            h[d] = Store<St>::ld(B + ((long long)(((P.t - 1) & 1) * 9 + d / 3) * P.g.nyz + ys + P.g.ny * zs));
+        }
+    }
 }
 
+template <typename St, bool NB>
+__device__ __forceinline__ void store_edge(const StepParams &P, int x, int y, int z, int cell, const float (&h)[27]) {
+    const bool xlo = x == 0, xhi = x == P.g.nx - 1;
+    if (NB) {
+        int off[9];
+        bool bb[9];
+        yz_rows<+1>(P.g, y, z, off, bb);
+#pragma unroll
+        for (int d = 0; d < 27; ++d) {
+            const int j = d / 3;
+            const bool xcross = (cx(d) == 1 && xhi) || (cx(d) == -1 && xlo);
+            St *own = static_cast<St *>(P.fp[opp(d)]) + cell;
+            if (bb[j]) {
+                Store<St>::st(own, h[d]);
+            } else if (!xcross) {
+                Store<St>::st(static_cast<St *>(P.fp[d]) + (cell + off[j]) + cx(d), h[d]);
+            } else if (P.g.periodic[0]) {
+                Store<St>::st(static_cast<St *>(P.fp[d]) + (cell + off[j] - cx(d) * (P.g.nx - 1)), h[d]);
+            } else {
+                Store<St>::st(own, h[d]);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int d = 0; d < 27; ++d) Store<St>::st(static_cast<St *>(P.fp[opp(d)]) + cell, h[d]);
+    }
+    if (xhi && P.g.face[1] == FACE_OUTLET) {
+        St *B = static_cast<St *>(P.outlet);
+        const int wpar = (int)(P.t & 1);
+#pragma unroll
+        for (int d = 0; d < 27; d += 3)   // the nine directions with c_x = -1
+            Store<St>::st(B + ((long long)(wpar * 9 + d / 3) * P.g.nyz + y + P.g.ny * z), h[d]);
+    }
+}
+
+// one warp per edge strip of one (y, z) row: blockIdx.x = strip (rows too short for the main
+// kernel are covered by consecutive warps), blockIdx.y = y, blockIdx.z = z
 template <typename St, bool NB, bool BAND>
-__global__ void __launch_bounds__(128) k_step_xfaces(StepParams P, int count) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= count) return;
-    int x, y, z;
-    xface_cell(P.g, i, x, y, z);
+__global__ void __launch_bounds__(XEDGE) k_step_edges(StepParams P) {
+    const int x = (has_interior(P.g) && blockIdx.x == 1) ? P.g.nx - XEDGE + threadIdx.x : blockIdx.x * XEDGE + threadIdx.x;
+    if (x >= P.g.nx) return;
+    const int y = blockIdx.y, z = blockIdx.z;
     const int cell = x + P.g.nx * (y + P.g.ny * z);
     float h[27];
-    load_general<St, NB>(P, x, y, z, cell, h);
+    load_edge<St, NB>(P, x, y, z, cell, h);
     float Fx, Fy, Fz;
     band_force<BAND>(P, cell, Fx, Fy, Fz);
     float rho, ux, uy, uz;
     collide(h, Fx, Fy, Fz, P, rho, ux, uy, uz);
-    store_general<St, NB>(P, x, y, z, cell, h);
+    store_edge<St, NB>(P, x, y, z, cell, h);
 }
 
 // ---- initialisation: f = f_eq(rho, u), stored as the post-collision state of t = 0 ------
@@ -476,18 +544,16 @@ __global__ void __launch_bounds__(256) k_sum_forces(long long S, const float *__
 
 static inline unsigned blocks_for(long long n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
-long long boundary_count(const Geometry &g) {
-    return (long long)(g.nx > 1 ? 2 : 1) * g.ny * g.nz;
-}
+long long boundary_count(const Geometry &g) { return (long long)edge_per_row(g) * g.ny * g.nz; }
 
 template <typename St, bool NB, bool BAND>
 static cudaError_t launch_step_tt(const StepParams &P, int part, cudaStream_t st) {
     const Geometry &g = P.g;
     if (part == STEP_BOUNDARY) {
-        const int nb = (int)boundary_count(g);
-        k_step_xfaces<St, NB, BAND><<<blocks_for(nb, 128), 128, 0, st>>>(P, nb);
+        const dim3 grid(has_interior(g) ? 2 : blocks_for(g.nx, XEDGE), g.ny, g.nz);
+        k_step_edges<St, NB, BAND><<<grid, XEDGE, 0, st>>>(P);
     } else if (has_interior(g)) {
-        const dim3 grid(blocks_for(g.nx - 2, STEP_BX), g.ny, g.nz);
+        const dim3 grid(blocks_for(g.nx - 2 * XEDGE, STEP_BX), g.ny, g.nz);
         k_step_main<St, NB, BAND><<<grid, STEP_BX, 0, st>>>(P);
     }
     return cudaGetLastError();

@@ -24,19 +24,22 @@ def _gpu():
     need_gpu()
 
 
-def test_tgv32_100_steps_fp32():
-    s = scenes.scene_tgv32()
-    g, o = run_pair(32, 32, 32, s["nu"], 100, s["rho"], s["u"])
+@pytest.mark.parametrize("dims", [(32, 32, 32), (96, 10, 12)])
+def test_tgv_100_steps_fp32(dims):
+    """The 32^3 box runs in the edge-strip kernel only; nx = 96 also exercises the main kernel."""
+    rho, u = scenes.taylor_green(*dims, 0.05)
+    g, o = run_pair(*dims, 0.01, 100, rho, u)
     e_rho, e_drho, e_u = compare_fields(g, o)
-    print(f"TGV32 100 steps: rel L2 rho {e_rho:.2e}, rho-1 {e_drho:.2e}, u {e_u:.2e}")
+    print(f"TGV {dims} 100 steps: rel L2 rho {e_rho:.2e}, rho-1 {e_drho:.2e}, u {e_u:.2e}")
     assert e_rho <= 1e-5 and e_u <= 1e-5
     assert e_drho <= 1e-4
 
 
+@pytest.mark.parametrize("n", [(11, 9, 7), (70, 5, 4)])
 @pytest.mark.parametrize("steps", [1, 2, 3])
-def test_populations_both_aa_parities(steps):
-    """Odd steps use the neighbour-addressed AA kernel, even steps the local one."""
-    n = (11, 9, 7)
+def test_populations_both_aa_parities(steps, n):
+    """Odd steps use the neighbour-addressed AA kernels, even steps the local ones; nx = 70
+    runs both the edge-strip kernel and the main kernel."""
     rho, u = scenes.taylor_green(*n, 0.05)
     g, o = run_pair(*n, 0.03, steps, rho, u, forcing=(1e-5, -2e-5, 3e-5), **RATES)
     err = compare_populations(g, o)
@@ -51,7 +54,7 @@ def test_matrix_form_oracle_agrees():
     assert compare_populations(g, o) <= 2e-7
 
 
-@pytest.mark.parametrize("dims", [(13, 7, 9), (33, 6, 5), (4, 4, 4)])
+@pytest.mark.parametrize("dims", [(13, 7, 9), (33, 6, 5), (4, 4, 4), (77, 6, 5), (65, 3, 4)])
 def test_channel_faces_ragged(dims):
     """Inlet (moving wall + seeded noise + Fourier profile), outlet, no-slip walls, periodic z."""
     nx, ny, nz = dims
@@ -65,8 +68,8 @@ def test_channel_faces_ragged(dims):
         assert err <= 3e-7, (steps, err)
 
 
-def test_closed_box_all_noslip():
-    n = (9, 8, 10)
+@pytest.mark.parametrize("n", [(9, 8, 10), (70, 6, 5)])
+def test_closed_box_all_noslip(n):
     rho, u = scenes.taylor_green(*n, 0.05)
     g, o = run_pair(*n, 0.02, 12, rho, u, faces=("noslip",) * 6)
     assert compare_populations(g, o) <= 2e-7
@@ -75,12 +78,13 @@ def test_closed_box_all_noslip():
     assert abs(m_g - m_o) <= 1e-6 * abs(m_o)
 
 
-def test_immersed_sphere_periodic_box():
+@pytest.mark.parametrize("nx,center", [(16, (7.3, 8.1, 6.6)), (72, (33.3, 8.1, 6.6))])
+def test_immersed_sphere_periodic_box(nx, center):
     n = 16
-    rho, u = scenes.taylor_green(n, n, n, 0.04)
-    X, A = scenes.fibonacci_sphere((7.3, 8.1, 6.6), 3.7, 300)
+    rho, u = scenes.taylor_green(nx, n, n, 0.04)
+    X, A = scenes.fibonacci_sphere(center, 3.7, 300)
     ub = np.tile([0.01, -0.005, 0.0], (300, 1))
-    g, o = run_pair(n, n, n, 0.02, 6, rho, u, forcing=(1e-6, 0, 0), samples=X, area=A, u_b=ub, **RATES)
+    g, o = run_pair(nx, n, n, 0.02, 6, rho, u, forcing=(1e-6, 0, 0), samples=X, area=A, u_b=ub, **RATES)
     assert compare_populations(g, o) <= 3e-7
     e_rho, _, e_u = compare_fields(g, o)
     assert e_rho <= 1e-6 and e_u <= 1e-5
@@ -96,7 +100,7 @@ def test_immersed_sphere_periodic_box():
 
 def test_sphere_channel_small():
     """Small version of the sphere channel: inlet noise, outlet, periodic y/z, IB sphere."""
-    nx, ny, nz = 40, 20, 18
+    nx, ny, nz = 72, 20, 18
     s = scenes.scene_sphere_channel(nx, ny, nz, radius=4.0, count=400, u_in=0.05, nu=0.02)
     g, o = run_pair(nx, ny, nz, s["nu"], 30, s["rho"], s["u"], faces=s["faces"], samples=s["samples"],
                     area=s["area"], u_in=0.05, noise=0.01, seed=2101)
