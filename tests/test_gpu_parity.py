@@ -32,7 +32,8 @@ def test_tgv_100_steps_fp32(dims):
     e_rho, e_drho, e_u = compare_fields(g, o)
     print(f"TGV {dims} 100 steps: rel L2 rho {e_rho:.2e}, rho-1 {e_drho:.2e}, u {e_u:.2e}")
     assert e_rho <= 1e-5 and e_u <= 1e-5
-    assert e_drho <= 1e-4
+    # rho is returned in FP32 near 1, so its absolute resolution is 2^-24 = 6e-8; allow 4 ulps
+    assert np.abs(g.macroscopic()[0] - o.macroscopic()[0].numpy()).max() <= 2.4e-7
 
 
 @pytest.mark.parametrize("n", [(11, 9, 7), (70, 5, 4)])
@@ -90,7 +91,9 @@ def test_immersed_sphere_periodic_box(nx, center):
     assert e_rho <= 1e-6 and e_u <= 1e-5
     gg = g.ib_forces(300)
     go = o.diag["g"].numpy().T
-    assert np.abs(gg - go).max() <= 1e-6 * np.abs(go).max() + 1e-9
+    # g = rho dA (u_b - u_s): the FP32 error of u_s (~1e-6 of |u| <= 0.05) is not reduced by the
+    # difference, so the bound is absolute: rho dA * 1e-6 * 0.05 with rho dA <= 0.6
+    assert np.abs(gg - go).max() <= 3e-8 + 1e-6 * np.abs(go).max()
     m_g, mom_g, drag_g = g.reductions()
     m_o, mom_o, drag_o = o.reductions()
     assert abs(m_g - m_o) <= 1e-6 * m_o
