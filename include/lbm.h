@@ -146,8 +146,9 @@ typedef struct lbm_loss {
  * lbm_step), evaluates L and back-propagates through every step: transposed streaming with
  * the faces, the vector-Jacobian product of the central-moment collision recomputed in
  * registers, and the transposes of IB interpolation/spreading with the derivatives of the
- * trilinear weights.  States are recomputed from checkpoints taken every K steps
- * (memory: about (n/K + K + 3) population arrays plus two FP32 adjoint arrays).
+ * trilinear weights.  States are recomputed out of place from checkpoints taken every K
+ * steps (memory: about n/K + K population arrays plus two FP32 adjoint arrays; K = n stores
+ * every state and recomputes nothing).
  * Outputs (host pointers, any may be NULL): dL_dinflow[16] = dL/da_mn of the inflow profile
  * (row-major in m; 0 without an inlet), dL_dpos[3*count] = dL/dX_s in the caller's sample
  * order, *L.  Gradients are accumulated in FP64.  Errors: LBM_ESTATE, LBM_EINVAL, LBM_ENOMEM,

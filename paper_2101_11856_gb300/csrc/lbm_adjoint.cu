@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "lbm_ctx.h"
+#include "lbm_step.cuh"
 
 using namespace lbm;
 using namespace lbm_host;
@@ -203,38 +204,13 @@ __device__ __forceinline__ void collide_vjp(const float (&fs)[27], float Fx, flo
 
 namespace {
 
-// full streamed populations f* of node (x, y, z) at step P.t, pulled from the stored
-// f_{t-1} with the same face rules as the forward general loader
-
+// full streamed populations f* of node (x, y, z) at step P.t from the stored f_{t-1}, with
+// the general per-direction face classification (band nodes: few, anywhere in the domain)
 template <typename St, bool NB>
 __device__ __forceinline__ void adj_load_fstar(const StepParams &P, int x, int y, int z, int cell, float (&h)[27]) {
-    const St *B = static_cast<const St *>(P.outlet);
-    const int rpar = (int)((P.t - 1) & 1);
-    const bool inlet_node = (x == 0) && P.g.face[0] == FACE_INLET;
-    const float uw = inlet_node ? inlet_velocity(P, y, z) : 0.0f;
+    load_general<St, NB>(P, x, y, z, cell, h);
 #pragma unroll
-    for (int d = 0; d < 27; ++d) {
-        const Nbr n = neighbour<-1>(P.g, d, x, y, z);
-        float v;
-        if (n.kind == 0) {
-            v = NB ? Store<St>::ld(static_cast<const St *>(P.fp[opp(d)]) + n.idx)
-                   : Store<St>::ld(static_cast<const St *>(P.fp[d]) + cell);
-        } else if (n.kind & CROSS_NOSLIP) {
-            v = Store<St>::ld(static_cast<const St *>(P.fp[d]) + cell);
-        } else if (n.kind & CROSS_INLET) {
-            v = Store<St>::ld(static_cast<const St *>(P.fp[d]) + cell) + 6.0f * wgt(d) * P.rho0 * (float)cx(d) * uw;
-        } else {
-            v = Store<St>::ld(B + ((long long)(rpar * 9 + d / 3) * P.g.nyz + n.y + P.g.ny * n.z));
-        }
-        h[d] = v + wgt(d) * P.rho0;      // full population
-    }
-}
-
-__device__ __forceinline__ void adj_decompose(const Geometry &g, int cell, int &x, int &y, int &z) {
-    z = cell / g.nxy;
-    const int r = cell - z * g.nxy;
-    y = r / g.nx;
-    x = r - y * g.nx;
+    for (int d = 0; d < 27; ++d) h[d] += wgt(d) * P.rho0;
 }
 
 __device__ __forceinline__ bool band_index(const StepParams &P, int cell, long long &b) {
@@ -263,7 +239,7 @@ __global__ void __launch_bounds__(128) k_adj_band_force(StepParams P, AdjParams 
     if (kb >= P.nband) return;
     const int cell = band_cell[kb];
     int x, y, z;
-    adj_decompose(P.g, cell, x, y, z);
+    decompose(P.g, cell, x, y, z);
     float fs[27], lam[27];
     adj_load_fstar<St, NB>(P, x, y, z, cell, fs);
     const long long N = P.g.ncell;
@@ -363,19 +339,16 @@ __global__ void __launch_bounds__(256) k_adj_band_gather(long long S, long long 
     adj_band[3 * nband + k] = dw * inv;
 }
 
-// the backward step over all nodes: mu = dL/df* (collision VJP + IB + loss terms), pushed
-// along the transpose of the streaming into dL/df_{t-1}
-template <typename St, bool NB, bool BAND>
-__global__ void __launch_bounds__(128) k_adj_step(StepParams P, AdjParams A) {
-    const int cell = blockIdx.x * blockDim.x + threadIdx.x;
-    if (cell >= P.g.ncell) return;
-    int x, y, z;
-    adj_decompose(P.g, cell, x, y, z);
-    float fs[27], lam[27];
-    adj_load_fstar<St, NB>(P, x, y, z, cell, fs);
+// dL/df* of a node: collision VJP with the band's IB terms and the loss's kinetic-energy term
+template <bool BAND>
+__device__ __forceinline__ void node_vjp(const StepParams &P, const AdjParams &A, int x, int cell, float (&fs)[27],
+                                         float (&lam)[27]) {
     const long long N = P.g.ncell;
 #pragma unroll
-    for (int d = 0; d < 27; ++d) lam[d] = A.lam_cur[d * N + cell];
+    for (int d = 0; d < 27; ++d) {
+        fs[d] += wgt(d) * P.rho0;
+        lam[d] = A.lam_cur[d * N + cell];
+    }
     float Fx = P.Fx, Fy = P.Fy, Fz = P.Fz;
     AdjExtra ex{0.0f, 0.0f, 0.0f, 0.0f, (x >= A.ke_x0 && x < A.ke_x1) ? A.wke : 0.0f};
     if (BAND) {
@@ -392,25 +365,81 @@ __global__ void __launch_bounds__(128) k_adj_step(StepParams P, AdjParams A) {
     }
     float dFx = 0.0f, dFy = 0.0f, dFz = 0.0f;
     collide_vjp(fs, Fx, Fy, Fz, P, ex, lam, dFx, dFy, dFz);
-    // push along the transposed streaming
+}
+
+// Backward step of the nodes XEDGE <= x < nx - XEDGE (one block row per (y, z)): mu = dL/df*
+// pushed along the transposed streaming, lambda_{t-1}[d](x - c_d) = mu_d(x), or to the
+// bounce-back slot lambda_{t-1}[opp(d)](x) where the source lies across a no-slip y/z face.
+template <typename St, bool NB, bool BAND>
+__global__ void __launch_bounds__(STEP_BX) k_adj_main(StepParams P, AdjParams A) {
+    const int x = blockIdx.x * STEP_BX + threadIdx.x + XEDGE;
+    if (x >= P.g.nx - XEDGE) return;
+    const int y = blockIdx.y, z = blockIdx.z;
+    const int cell = x + P.g.nx * (y + P.g.ny * z);
+    const bool inner = y >= 1 && y <= P.g.ny - 2 && z >= 1 && z <= P.g.nz - 2;   // uniform per block
+    float fs[27], lam[27];
+    if (!NB || inner) load_interior<St, NB>(P, cell, fs);
+    else load_yzface<St>(P, y, z, cell, fs);
+    node_vjp<BAND>(P, A, x, cell, fs, lam);
+    const long long N = P.g.ncell;
+    if (inner) {
+#pragma unroll
+        for (int d = 0; d < 27; ++d)
+            A.lam_prev[d * N + cell - (cx(d) + cy(d) * P.g.nx + cz(d) * P.g.nxy)] = lam[d];
+    } else {
+        int off[9];
+        bool bb[9];
+        yz_rows<-1>(P.g, y, z, off, bb);
+#pragma unroll
+        for (int d = 0; d < 27; ++d) {
+            if (bb[d / 3]) A.lam_prev[opp(d) * N + cell] = lam[d];
+            else A.lam_prev[d * N + cell + off[d / 3] - cx(d)] = lam[d];
+        }
+    }
+}
+
+// Backward step of the edge strips (whole warps; the x-face rules per lane): periodic x wraps,
+// no-slip and inlet faces bounce back (the inlet also feeds the inflow-coefficient gradient),
+// the outlet ghost's use goes to the duplicate buffer for k_adj_outlet.
+template <typename St, bool NB, bool BAND>
+__global__ void __launch_bounds__(XEDGE) k_adj_edges(StepParams P, AdjParams A) {
+    const int x = (has_interior(P.g) && blockIdx.x == 1) ? P.g.nx - XEDGE + threadIdx.x : blockIdx.x * XEDGE + threadIdx.x;
+    if (x >= P.g.nx) return;
+    const int y = blockIdx.y, z = blockIdx.z;
+    const int cell = x + P.g.nx * (y + P.g.ny * z);
+    float fs[27], lam[27];
+    load_edge<St, NB>(P, x, y, z, cell, fs);
+    node_vjp<BAND>(P, A, x, cell, fs, lam);
+    const long long N = P.g.ncell;
+    int off[9];
+    bool bb[9];
+    yz_rows<-1>(P.g, y, z, off, bb);
+    const bool xlo = x == 0, xhi = x == P.g.nx - 1;
+    const bool outlet_node = xhi && P.g.face[1] == FACE_OUTLET;
     double sth = 0.0;
-    const bool outlet_node = (x == P.g.nx - 1) && P.g.face[1] == FACE_OUTLET;
 #pragma unroll
     for (int d = 0; d < 27; ++d) {
-        const Nbr n = neighbour<-1>(P.g, d, x, y, z);
+        const int j = d / 3;
         const float mu = lam[d];
         bool ghost = false;
-        if (n.kind == 0) {
-            A.lam_prev[d * N + n.idx] = mu;
-        } else if (n.kind & (CROSS_NOSLIP | CROSS_INLET)) {
+        if (bb[j]) {
             A.lam_prev[opp(d) * N + cell] = mu;
-            if (!(n.kind & CROSS_NOSLIP)) sth += (double)mu * (6.0 * wgt(d) * P.rho0 * cx(d));
+        } else if (cx(d) == 0 || !(cx(d) == 1 ? xlo : xhi)) {
+            A.lam_prev[d * N + cell + off[j] - cx(d)] = mu;
         } else {
-            ghost = true;
+            const int ft = P.g.face[cx(d) == 1 ? 0 : 1];
+            if (ft == FACE_PERIODIC) {
+                A.lam_prev[d * N + cell + off[j] + cx(d) * (P.g.nx - 1)] = mu;
+            } else if (ft == FACE_OUTLET) {
+                ghost = true;
+            } else {
+                A.lam_prev[opp(d) * N + cell] = mu;
+                if (ft == FACE_INLET) sth += (double)mu * (6.0 * wgt(d) * P.rho0 * cx(d));
+            }
         }
-        if (outlet_node && cx(d) == -1) A.blam[(long long)(d / 3) * P.g.nyz + y + P.g.ny * z] = ghost ? mu : 0.0f;
+        if (outlet_node && cx(d) == -1) A.blam[(long long)j * P.g.nyz + y + P.g.ny * z] = ghost ? mu : 0.0f;
     }
-    if (x == 0 && P.g.face[0] == FACE_INLET) A.s_inlet[y + P.g.ny * z] += sth;
+    if (xlo && P.g.face[0] == FACE_INLET) A.s_inlet[y + P.g.ny * z] += sth;
 }
 
 // outlet plane: zero the slots of the populations that left through the outlet (no use in
@@ -463,13 +492,6 @@ template <typename F> cudaError_t with_storage(int storage, F &&fn) {
     }
 }
 
-// pointers of one stored state: populations (27 planes) followed by the outlet plane
-void point_params(StepParams &P, const lbm_ctx *h, void *state) {
-    P.f = state;
-    for (int d = 0; d < 27; ++d) P.fp[d] = static_cast<char *>(state) + (size_t)d * h->plane * h->esize;
-    P.outlet = h->outlet ? static_cast<char *>(state) + (size_t)27 * h->plane * h->esize : nullptr;
-}
-
 struct AdjBuffers {
     std::vector<void *> bufs;
     ~AdjBuffers() {
@@ -500,10 +522,8 @@ extern "C" int lbm_adjoint(lbm_ctx *h, int n, int K, const lbm_loss *loss, doubl
     AdjBuffers B;
     int rc;
     std::vector<char *> ckpt(nck), seg(K);
-    char *final_state = nullptr;
     for (int i = 0; i < nck; ++i) if ((rc = B.get(h, &ckpt[i], state_bytes))) return rc;
     for (int i = 0; i < K; ++i) if ((rc = B.get(h, &seg[i], state_bytes))) return rc;
-    if ((rc = B.get(h, &final_state, state_bytes))) return rc;
     float *lamA, *lamB, *blam = nullptr, *dF_band = nullptr, *adj_band = nullptr, *adj_samp = nullptr;
     double *s_inlet, *dX = nullptr, *acc;
     if ((rc = B.get(h, &lamA, (size_t)27 * N)) || (rc = B.get(h, &lamB, (size_t)27 * N)) ||
@@ -544,8 +564,6 @@ extern "C" int lbm_adjoint(lbm_ctx *h, int n, int K, const lbm_loss *loss, doubl
         k_finalize_add<<<1, 256, 0, st>>>(h->partial + 4 * mblk, mblk, 1, acc + 3);
         CK(cudaGetLastError());
     }
-    CK(cudaMemcpyAsync(final_state, h->f, pop_bytes, cudaMemcpyDeviceToDevice, st));
-    if (out_bytes) CK(cudaMemcpyAsync(final_state + pop_bytes, h->outlet, out_bytes, cudaMemcpyDeviceToDevice, st));
     float *g_last = nullptr, *F_last = nullptr;     // IB diagnostics of the last step, restored at the end
     if (S > 0) {
         if ((rc = B.get(h, &g_last, (size_t)3 * S)) || (rc = B.get(h, &F_last, (size_t)3 * nb))) return rc;
@@ -559,17 +577,16 @@ extern "C" int lbm_adjoint(lbm_ctx *h, int n, int K, const lbm_loss *loss, doubl
     for (int sgi = nck - 1; sgi >= 0; --sgi) {
         const long long t0 = t_start + (long long)sgi * K;
         const int len = (int)std::min<long long>(K, t_start + n - t0);
-        CK(cudaMemcpyAsync(h->f, ckpt[sgi], pop_bytes, cudaMemcpyDeviceToDevice, st));
-        if (out_bytes) CK(cudaMemcpyAsync(h->outlet, ckpt[sgi] + pop_bytes, out_bytes, cudaMemcpyDeviceToDevice, st));
-        h->t = t0;
-        for (int k = 0; k < len; ++k) {
-            CK(cudaMemcpyAsync(seg[k], h->f, pop_bytes, cudaMemcpyDeviceToDevice, st));
-            if (out_bytes) CK(cudaMemcpyAsync(seg[k] + pop_bytes, h->outlet, out_bytes, cudaMemcpyDeviceToDevice, st));
-            if (k < len - 1 && (rc = lbm_step(h, 1))) return rc;
+        // recompute the segment's states out of place: seg[k] = f_{t0 + k}
+        CK(cudaMemcpyAsync(seg[0], ckpt[sgi], state_bytes, cudaMemcpyDeviceToDevice, st));
+        for (int k = 0; k + 1 < len; ++k) {
+            StepParams Pf = make_params(h, t0 + k + 1);
+            point_states(Pf, h, seg[k], seg[k + 1]);
+            if ((rc = step_with(h, Pf))) return rc;
         }
         for (long long t = t0 + len; t > t0; --t) {
             StepParams P = make_params(h, t);
-            point_params(P, h, seg[t - 1 - t0]);
+            point_states(P, h, seg[t - 1 - t0], seg[t - 1 - t0]);
             AdjParams A{};
             A.lam_cur = lam_cur;
             A.lam_prev = lam_prev;
@@ -599,13 +616,25 @@ extern "C" int lbm_adjoint(lbm_ctx *h, int n, int K, const lbm_loss *loss, doubl
             }
             CK(with_storage(h->storage, [&](auto tag) {
                 using St = decltype(tag);
-                const unsigned g = nblocks(N, 128);
+                const dim3 ge(has_interior(P.g) ? 2 : nblocks(h->nx, XEDGE), h->ny, h->nz);
+                const dim3 gm(has_interior(P.g) ? nblocks(h->nx - 2 * XEDGE, STEP_BX) : 1, h->ny, h->nz);
+                const bool mn = has_interior(P.g);
                 if (nbp) {
-                    if (S > 0) k_adj_step<St, true, true><<<g, 128, 0, st>>>(P, A);
-                    else k_adj_step<St, true, false><<<g, 128, 0, st>>>(P, A);
+                    if (S > 0) {
+                        k_adj_edges<St, true, true><<<ge, XEDGE, 0, st>>>(P, A);
+                        if (mn) k_adj_main<St, true, true><<<gm, STEP_BX, 0, st>>>(P, A);
+                    } else {
+                        k_adj_edges<St, true, false><<<ge, XEDGE, 0, st>>>(P, A);
+                        if (mn) k_adj_main<St, true, false><<<gm, STEP_BX, 0, st>>>(P, A);
+                    }
                 } else {
-                    if (S > 0) k_adj_step<St, false, true><<<g, 128, 0, st>>>(P, A);
-                    else k_adj_step<St, false, false><<<g, 128, 0, st>>>(P, A);
+                    if (S > 0) {
+                        k_adj_edges<St, false, true><<<ge, XEDGE, 0, st>>>(P, A);
+                        if (mn) k_adj_main<St, false, true><<<gm, STEP_BX, 0, st>>>(P, A);
+                    } else {
+                        k_adj_edges<St, false, false><<<ge, XEDGE, 0, st>>>(P, A);
+                        if (mn) k_adj_main<St, false, false><<<gm, STEP_BX, 0, st>>>(P, A);
+                    }
                 }
                 return cudaGetLastError();
             }));
@@ -616,9 +645,7 @@ extern "C" int lbm_adjoint(lbm_ctx *h, int n, int K, const lbm_loss *loss, doubl
             std::swap(lam_cur, lam_prev);
         }
     }
-    // restore the state reached by the forward pass
-    CK(cudaMemcpyAsync(h->f, final_state, pop_bytes, cudaMemcpyDeviceToDevice, st));
-    if (out_bytes) CK(cudaMemcpyAsync(h->outlet, final_state + pop_bytes, out_bytes, cudaMemcpyDeviceToDevice, st));
+    // the forward pass left the state at t_start + n; restore its IB diagnostics
     if (S > 0) {
         CK(cudaMemcpyAsync(h->g, g_last, 3 * S * sizeof(float), cudaMemcpyDeviceToDevice, st));
         CK(cudaMemcpyAsync(h->bandF, F_last, 3 * nb * sizeof(float), cudaMemcpyDeviceToDevice, st));

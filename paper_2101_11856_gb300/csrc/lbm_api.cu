@@ -24,6 +24,21 @@ int fail(lbm_ctx *h, int code, const std::string &msg) {
     else g_create_error = msg;
     return code;
 }
+
+int step_with(lbm_ctx *h, const StepParams &P) {
+    const bool band = h->S > 0;
+    if (band) {
+        { Timed tm(h, LBM_KERNEL_BAND); CK(launch_band_moments(h->storage, P, h->band_cell, h->band_rho, h->band_u, h->stream)); }
+        { Timed tm(h, LBM_KERNEL_INTERP); CK(launch_ib_interp(h->S, h->nband, h->X, h->area, h->ub, h->corner_band, h->band_rho, h->band_u, h->g, h->stream)); }
+        { Timed tm(h, LBM_KERNEL_SPREAD); CK(launch_ib_spread(h->S, h->nband, h->X, h->g, h->base_nbr, h->cstart, h->ccount, h->bandF, h->stream)); }
+    }
+    { Timed tm(h, LBM_KERNEL_BOUNDARY); CK(launch_step(h->storage, P, band, STEP_BOUNDARY, h->stream)); }
+    if (has_interior(P.g)) {
+        Timed tm(h, LBM_KERNEL_STEP);
+        CK(launch_step(h->storage, P, band, STEP_INTERIOR, h->stream));
+    }
+    return LBM_OK;
+}
 }  // namespace lbm_host
 
 using namespace lbm_host;
@@ -327,18 +342,7 @@ int lbm_step(lbm_ctx *h, int n) {
     if (n < 0) return fail(h, LBM_EINVAL, "negative step count");
     for (int k = 0; k < n; ++k) {
         const long long t = h->t + 1;
-        StepParams P = make_params(h, t);
-        const bool band = h->S > 0;
-        if (band) {
-            { Timed tm(h, LBM_KERNEL_BAND); CK(launch_band_moments(h->storage, P, h->band_cell, h->band_rho, h->band_u, h->stream)); }
-            { Timed tm(h, LBM_KERNEL_INTERP); CK(launch_ib_interp(h->S, h->nband, h->X, h->area, h->ub, h->corner_band, h->band_rho, h->band_u, h->g, h->stream)); }
-            { Timed tm(h, LBM_KERNEL_SPREAD); CK(launch_ib_spread(h->S, h->nband, h->X, h->g, h->base_nbr, h->cstart, h->ccount, h->bandF, h->stream)); }
-        }
-        { Timed tm(h, LBM_KERNEL_BOUNDARY); CK(launch_step(h->storage, P, band, STEP_BOUNDARY, h->stream)); }
-        if (has_interior(P.g)) {
-            Timed tm(h, LBM_KERNEL_STEP);
-            CK(launch_step(h->storage, P, band, STEP_INTERIOR, h->stream));
-        }
+        if ((rc = step_with(h, make_params(h, t)))) return rc;
         h->t = t;
     }
     return LBM_OK;

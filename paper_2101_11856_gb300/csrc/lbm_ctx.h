@@ -128,8 +128,8 @@ struct Timed {
 inline lbm::StepParams make_params(const lbm_ctx *h, long long t) {
     lbm::StepParams P{};
     P.f = h->f;
-    for (int d = 0; d < 27; ++d) P.fp[d] = static_cast<char *>(h->f) + (size_t)d * h->plane * h->esize;
-    P.outlet = h->outlet;
+    for (int d = 0; d < 27; ++d) P.fp[d] = P.fpo[d] = static_cast<char *>(h->f) + (size_t)d * h->plane * h->esize;
+    P.outlet = P.outlet_o = h->outlet;
     lbm::Geometry &g = P.g;
     g.nx = h->nx; g.ny = h->ny; g.nz = h->nz;
     g.nxy = h->nx * h->ny;
@@ -162,6 +162,23 @@ inline lbm::StepParams make_params(const lbm_ctx *h, long long t) {
     P.nband = h->nband;
     return P;
 }
+
+// point the reads (src) and writes (dst) of a step at two stored states; a stored state is
+// the 27 population planes followed by the outlet ghost plane (when the grid has an outlet)
+inline void point_states(lbm::StepParams &P, const lbm_ctx *h, void *src, void *dst) {
+    P.f = src;
+    const size_t pb = (size_t)h->plane * h->esize;
+    for (int d = 0; d < 27; ++d) {
+        P.fp[d] = static_cast<char *>(src) + d * pb;
+        P.fpo[d] = static_cast<char *>(dst) + d * pb;
+    }
+    P.outlet = h->outlet ? static_cast<char *>(src) + 27 * pb : nullptr;
+    P.outlet_o = h->outlet ? static_cast<char *>(dst) + 27 * pb : nullptr;
+}
+
+// one full time step t (IB stage + fused step kernels) reading P's source and writing its
+// destination; defined in lbm_api.cu
+int step_with(lbm_ctx *h, const lbm::StepParams &P);
 
 inline int ensure_partial(lbm_ctx *h, size_t doubles) {
     if (doubles <= h->partial_cap) return LBM_OK;

@@ -62,8 +62,10 @@ struct Geometry {
 
 struct StepParams {
     void *f;                     // populations, 27 planes (AA in place)
-    void *fp[27];                // start of the plane of each direction
-    void *outlet;                // outlet ghost plane, [2][9][nyz] (ping-pong by step parity)
+    void *fp[27];                // start of the plane of each direction (read)
+    void *fpo[27];               // planes written by the step (= fp in place; another state out of place)
+    void *outlet;                // outlet ghost plane, [2][9][nyz] (ping-pong by step parity), read
+    void *outlet_o;              // outlet ghost plane written by the step
     Geometry g;
     float rho0;
     float Fx, Fy, Fz;            // body force

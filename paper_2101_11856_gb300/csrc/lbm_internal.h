@@ -13,6 +13,7 @@ enum { STEP_BOUNDARY = 0, STEP_INTERIOR = 1 };
 // run by the main kernel (STEP_INTERIOR).  Rows shorter than 2 XEDGE + 1 run entirely in the
 // face kernel.
 constexpr int XEDGE = 32;
+constexpr int STEP_BX = 64;   // threads per block of the main step kernels (along x)
 cudaError_t launch_step(int storage, const StepParams &P, bool band, int part, cudaStream_t st);
 long long boundary_count(const Geometry &g);
 __host__ __device__ inline bool has_interior(const Geometry &g) { return g.nx >= 2 * XEDGE + 1; }

@@ -1,180 +1,12 @@
-// CUDA kernels of the GB300 path: the fused AA-pattern D3Q27 step, its initialisation,
-// the immersed-boundary band / interpolation / spreading kernels, and the diagnostics.
-//
-// AA pattern (in-place streaming, one population array): with A[d][cell] the storage,
-//  * after an even step (and at t = 0) A[opp(d)][x] holds the post-collision f_d(x);
-//  * an odd step t ("neighbour" step) pulls f*_d(x) = A[opp(d)][x - c_d] and writes the
-//    new f_d(x) to A[d][x + c_d];
-//  * an even step ("local" step) reads f*_d(x) = A[d][x] and writes f_d(x) to A[opp(d)][x].
-// Each node reads and writes the same 27 slots, so one array suffices and no two threads
-// touch a slot.  A population whose source lies behind a non-periodic face is found in
-// the node's own slot A[d][x] (the previous step wrote the reflected value there), which
-// gives half-way bounce-back (the paper's Algorithm 1) and the moving-wall inlet; the
-// outlet reads a ping-pong copy of the outlet plane's previous post-collision values.
+// CUDA kernels of the GB300 path: the fused D3Q27 step (main and edge-strip kernels), its
+// initialisation, the immersed-boundary band / interpolation / spreading kernels, and the
+// diagnostics.  The AA-pattern addressing lives in lbm_step.cuh.
 #include <algorithm>
 
-#include "lbm_device.cuh"
-#include "lbm_internal.h"
+#include "lbm_step.cuh"
 
 namespace lbm {
 
-static constexpr int STEP_BX = 64;   // threads per block of the interior step (along x)
-
-// ---- loads of the streamed populations f*(x) ------------------------------------------
-
-// interior node: every neighbour exists, constant offsets; one base pointer per plane
-template <typename St, bool NB>
-__device__ __forceinline__ void load_interior(const StepParams &P, int cell, float (&h)[27]) {
-#pragma unroll
-    for (int d = 0; d < 27; ++d) {
-        if (NB) {
-            const St *p = static_cast<const St *>(P.fp[opp(d)]) + (cell - (cy(d) * P.g.nx + cz(d) * P.g.nxy));
-            h[d] = Store<St>::ld(p - cx(d));
-        } else {
-            h[d] = Store<St>::ld(static_cast<const St *>(P.fp[d]) + cell);
-        }
-    }
-}
-
-template <typename St, bool NB>
-__device__ __forceinline__ void load_general(const StepParams &P, int x, int y, int z, int cell, float (&h)[27]) {
-    const St *A = static_cast<const St *>(P.f);
-    const St *B = static_cast<const St *>(P.outlet);
-    const long long pl = P.g.plane;
-    const int rpar = (int)((P.t - 1) & 1);
-    const bool inlet_node = (x == 0) && P.g.face[0] == FACE_INLET;
-    const float uw = inlet_node ? inlet_velocity(P, y, z) : 0.0f;
-#pragma unroll
-    for (int d = 0; d < 27; ++d) {
-        const Nbr n = neighbour<-1>(P.g, d, x, y, z);
-        float v;
-        if (n.kind == 0) {
-            v = NB ? Store<St>::ld(A + opp(d) * pl + n.idx) : Store<St>::ld(A + d * pl + cell);
-        } else if (n.kind & CROSS_NOSLIP) {
-            v = Store<St>::ld(A + d * pl + cell);
-        } else if (n.kind & CROSS_INLET) {
-            // moving wall: f*_d = f_opp(d) + 2 w_d rho0 (c_d . u_w) / c_s^2
-            v = Store<St>::ld(A + d * pl + cell) + 6.0f * wgt(d) * P.rho0 * (float)cx(d) * uw;
-        } else {
-            // outlet ghost: post-collision f_d of (nx-1, y - c_dy, z - c_dz) of the previous step
-            v = Store<St>::ld(B + ((long long)(rpar * 9 + d / 3) * P.g.nyz + n.y + P.g.ny * n.z));
-        }
-        h[d] = v;
-    }
-}
-
-// ---- stores of the post-collision populations ------------------------------------------
-
-template <typename St, bool NB>
-__device__ __forceinline__ void store_interior(const StepParams &P, int cell, const float (&h)[27]) {
-#pragma unroll
-    for (int d = 0; d < 27; ++d) {
-        if (NB) {
-            St *p = static_cast<St *>(P.fp[d]) + (cell + (cy(d) * P.g.nx + cz(d) * P.g.nxy));
-            Store<St>::st(p + cx(d), h[d]);
-        } else {
-            Store<St>::st(static_cast<St *>(P.fp[opp(d)]) + cell, h[d]);
-        }
-    }
-}
-
-template <typename St, bool NB>
-__device__ __forceinline__ void store_general(const StepParams &P, int x, int y, int z, int cell, const float (&h)[27]) {
-    St *A = static_cast<St *>(P.f);
-    const long long pl = P.g.plane;
-#pragma unroll
-    for (int d = 0; d < 27; ++d) {
-        if (NB) {
-            const Nbr n = neighbour<+1>(P.g, d, x, y, z);
-            if (n.kind == 0) Store<St>::st(A + d * pl + n.idx, h[d]);
-            else Store<St>::st(A + opp(d) * pl + cell, h[d]);
-        } else {
-            Store<St>::st(A + opp(d) * pl + cell, h[d]);
-        }
-    }
-    if (x == P.g.nx - 1 && P.g.face[1] == FACE_OUTLET) {
-        St *B = static_cast<St *>(P.outlet);
-        const int wpar = (int)(P.t & 1);
-#pragma unroll
-        for (int d = 0; d < 27; d += 3)   // the nine directions with c_x = -1
-            Store<St>::st(B + ((long long)(wpar * 9 + d / 3) * P.g.nyz + y + P.g.ny * z), h[d]);
-    }
-}
-
-__device__ __forceinline__ void decompose(const Geometry &g, int cell, int &x, int &y, int &z) {
-    z = cell / g.nxy;
-    const int r = cell - z * g.nxy;
-    y = r / g.nx;
-    x = r - y * g.nx;
-}
-
-// immersed-boundary force of the band node at `cell` (zero off the band)
-template <bool BAND>
-__device__ __forceinline__ void band_force(const StepParams &P, int cell, float &Fx, float &Fy, float &Fz) {
-    Fx = P.Fx; Fy = P.Fy; Fz = P.Fz;
-    if (BAND) {
-        const uint32_t mask = P.tile_mask[cell >> 5];
-        const int lane = cell & 31;
-        if ((mask >> lane) & 1u) {
-            const long long b = P.tile_off[cell >> 5] + __popc(mask & ((1u << lane) - 1u));
-            Fx += P.bandF[b];
-            Fy += P.bandF[P.nband + b];
-            Fz += P.bandF[2 * P.nband + b];
-        }
-    }
-}
-
-// ---- rows of a block's y/z neighbours ----------------------------------------------------
-// The y and z faces are only periodic or no-slip.  For the node rows y + S c_y, z + S c_z
-// (S = -1: pull source, S = +1: push target) give the cell offset of the row (with periodic
-// wrap) or mark it as crossing a no-slip face (bounce-back to the node's own slot).  Row j of
-// direction d is j = d / 3 = (c_y + 1) + 3 (c_z + 1).
-template <int S>
-__device__ __forceinline__ void yz_rows(const Geometry &g, int y, int z, int (&off)[9], bool (&bb)[9]) {
-    int oy[3], oz[3];
-    bool by[3], bz[3];
-#pragma unroll
-    for (int c = -1; c <= 1; ++c) {
-        int yy = y + S * c, zz = z + S * c;
-        by[c + 1] = bz[c + 1] = false;
-        if (yy < 0) { if (g.periodic[1]) yy += g.ny; else by[c + 1] = true; }
-        else if (yy >= g.ny) { if (g.periodic[1]) yy -= g.ny; else by[c + 1] = true; }
-        if (zz < 0) { if (g.periodic[2]) zz += g.nz; else bz[c + 1] = true; }
-        else if (zz >= g.nz) { if (g.periodic[2]) zz -= g.nz; else bz[c + 1] = true; }
-        oy[c + 1] = (yy - y) * g.nx;
-        oz[c + 1] = (zz - z) * g.nxy;
-    }
-#pragma unroll
-    for (int j = 0; j < 9; ++j) {
-        off[j] = oy[j % 3] + oz[j / 3];
-        bb[j] = by[j % 3] || bz[j / 3];
-    }
-}
-
-// odd-step loads/stores of a node with 1 <= x <= nx-2 on a y or z face
-template <typename St>
-__device__ __forceinline__ void load_yzface(const StepParams &P, int y, int z, int cell, float (&h)[27]) {
-    int off[9];
-    bool bb[9];
-    yz_rows<-1>(P.g, y, z, off, bb);
-#pragma unroll
-    for (int d = 0; d < 27; ++d) {
-        if (bb[d / 3]) h[d] = Store<St>::ld(static_cast<const St *>(P.fp[d]) + cell);
-        else h[d] = Store<St>::ld(static_cast<const St *>(P.fp[opp(d)]) + (cell + off[d / 3]) - cx(d));
-    }
-}
-
-template <typename St>
-__device__ __forceinline__ void store_yzface(const StepParams &P, int y, int z, int cell, const float (&h)[27]) {
-    int off[9];
-    bool bb[9];
-    yz_rows<+1>(P.g, y, z, off, bb);
-#pragma unroll
-    for (int d = 0; d < 27; ++d) {
-        if (bb[d / 3]) Store<St>::st(static_cast<St *>(P.fp[opp(d)]) + cell, h[d]);
-        else Store<St>::st(static_cast<St *>(P.fp[d]) + (cell + off[d / 3]) + cx(d), h[d]);
-    }
-}
 
 // ---- the fused step ---------------------------------------------------------------------
 // One thread per cell: pull the 27 streamed populations, add the body force and the band's
@@ -200,82 +32,6 @@ __global__ void __launch_bounds__(STEP_BX) k_step_main(StepParams P) {
     collide(h, Fx, Fy, Fz, P, rho, ux, uy, uz);
     if (!NB || inner) store_interior<St, NB>(P, cell, h);
     else store_yzface<St>(P, y, z, cell, h);
-}
-
-// ---- the edge strips: y/z faces per block, x faces per lane --------------------------------
-// Same pull/push rules as load_general/store_general, arranged for a block that covers one
-// strip of one (y, z) row: the y/z rows come from yz_rows (uniform), and only the lanes at
-// x = 0 or x = nx-1 take the x-face rule for the directions whose source (pull) or target
-// (push) lies across that face.  Priority at edges: no-slip > inlet > outlet.
-template <typename St, bool NB>
-__device__ __forceinline__ void load_edge(const StepParams &P, int x, int y, int z, int cell, float (&h)[27]) {
-    int off[9];
-    bool bb[9];
-    yz_rows<-1>(P.g, y, z, off, bb);
-    const bool xlo = x == 0, xhi = x == P.g.nx - 1;
-    const float uw = (xlo && P.g.face[0] == FACE_INLET) ? inlet_velocity(P, y, z) : 0.0f;
-#pragma unroll
-    for (int d = 0; d < 27; ++d) {
-        const int j = d / 3;
-        const bool xcross = (cx(d) == 1 && xlo) || (cx(d) == -1 && xhi);
-        const St *own = static_cast<const St *>(P.fp[d]) + cell;
-        if (!xcross) {
-            h[d] = (NB && !bb[j]) ? Store<St>::ld(static_cast<const St *>(P.fp[opp(d)]) + (cell + off[j]) - cx(d))
-                                  : Store<St>::ld(own);
-            continue;
-        }
-        const int ft = P.g.face[cx(d) == 1 ? 0 : 1];
-        if (bb[j] || ft == FACE_NOSLIP) {
-            h[d] = Store<St>::ld(own);
-        } else if (ft == FACE_PERIODIC) {
-            h[d] = NB ? Store<St>::ld(static_cast<const St *>(P.fp[opp(d)]) + (cell + off[j] + cx(d) * (P.g.nx - 1)))
-                      : Store<St>::ld(own);
-        } else if (ft == FACE_INLET) {
-            h[d] = Store<St>::ld(own) + 6.0f * wgt(d) * P.rho0 * (float)cx(d) * uw;
-        } else {
-            // outlet ghost: post-collision f_d of (nx-1, y - c_dy, z - c_dz) of the previous step
-            int ys = y - cy(d), zs = z - cz(d);
-            ys += ys < 0 ? P.g.ny : (ys >= P.g.ny ? -P.g.ny : 0);
-            zs += zs < 0 ? P.g.nz : (zs >= P.g.nz ? -P.g.nz : 0);
-            const St *B = static_cast<const St *>(P.outlet);
-            h[d] = Store<St>::ld(B + ((long long)(((P.t - 1) & 1) * 9 + d / 3) * P.g.nyz + ys + P.g.ny * zs));
-        }
-    }
-}
-
-template <typename St, bool NB>
-__device__ __forceinline__ void store_edge(const StepParams &P, int x, int y, int z, int cell, const float (&h)[27]) {
-    const bool xlo = x == 0, xhi = x == P.g.nx - 1;
-    if (NB) {
-        int off[9];
-        bool bb[9];
-        yz_rows<+1>(P.g, y, z, off, bb);
-#pragma unroll
-        for (int d = 0; d < 27; ++d) {
-            const int j = d / 3;
-            const bool xcross = (cx(d) == 1 && xhi) || (cx(d) == -1 && xlo);
-            St *own = static_cast<St *>(P.fp[opp(d)]) + cell;
-            if (bb[j]) {
-                Store<St>::st(own, h[d]);
-            } else if (!xcross) {
-                Store<St>::st(static_cast<St *>(P.fp[d]) + (cell + off[j]) + cx(d), h[d]);
-            } else if (P.g.periodic[0]) {
-                Store<St>::st(static_cast<St *>(P.fp[d]) + (cell + off[j] - cx(d) * (P.g.nx - 1)), h[d]);
-            } else {
-                Store<St>::st(own, h[d]);
-            }
-        }
-    } else {
-#pragma unroll
-        for (int d = 0; d < 27; ++d) Store<St>::st(static_cast<St *>(P.fp[opp(d)]) + cell, h[d]);
-    }
-    if (xhi && P.g.face[1] == FACE_OUTLET) {
-        St *B = static_cast<St *>(P.outlet);
-        const int wpar = (int)(P.t & 1);
-#pragma unroll
-        for (int d = 0; d < 27; d += 3)   // the nine directions with c_x = -1
-            Store<St>::st(B + ((long long)(wpar * 9 + d / 3) * P.g.nyz + y + P.g.ny * z), h[d]);
-    }
 }
 
 // one warp per edge strip of one (y, z) row: blockIdx.x = strip (rows too short for the main
