@@ -94,8 +94,10 @@ int lbm_set_solids(lbm_ctx *h, const float *samples, long long count,
 
 /* Advance n time steps (Algorithm 2: streaming, moments, immersed boundary, collision
  * with forcing, domain faces), asynchronously on the context's stream.  Each step is one
- * fused stream+collide kernel over the nodes with 1 <= x <= nx-2, one over the x = 0 and
- * x = nx-1 columns, and three small immersed-boundary kernels when a solid is installed.  Errors: LBM_ESTATE before lbm_set_state, LBM_ECUDA. */
+ * fused stream+collide kernel over the nodes 32 <= x < nx-32, one over the two 32-node
+ * edge strips of every row (the inlet/outlet/x-periodic rules), and three small
+ * immersed-boundary kernels when a solid is installed.
+ * Errors: LBM_ESTATE before lbm_set_state, LBM_ECUDA. */
 int lbm_step(lbm_ctx *h, int n);
 
 /* Density and Guo-shifted velocity u = (sum c f + F/2)/rho used by the most recent
