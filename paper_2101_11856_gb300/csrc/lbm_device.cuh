@@ -58,6 +58,7 @@ struct Geometry {
     long long plane;     // elements between consecutive direction planes (>= ncell)
     int periodic[3];
     int face[6];         // FaceType of -x, +x, -y, +y, -z, +z
+    int paired;          // run the main range two nodes per thread where nx allows it
 };
 
 struct StepParams {
@@ -136,31 +137,55 @@ __device__ __forceinline__ Nbr neighbour(const Geometry &g, int D, int x, int y,
     return n;
 }
 
+// ---- arithmetic on one node (float) or on two adjacent nodes at once (F2) --------------
+// F2 carries the same FP32 arithmetic for two nodes in the packed FP32 instructions of
+// sm_100+ (one FMA / add / multiply instruction for both), so a thread that updates two
+// nodes issues about half the floating-point instructions.  Every operation is IEEE FP32
+// with round-to-nearest, component by component.
+struct F2 {
+    float2 v;
+};
+__device__ __forceinline__ F2 mk2(float s) { return {make_float2(s, s)}; }
+__device__ __forceinline__ F2 operator+(F2 a, F2 b) { return {__fadd2_rn(a.v, b.v)}; }
+__device__ __forceinline__ F2 operator-(F2 a, F2 b) { return {__ffma2_rn(b.v, make_float2(-1.0f, -1.0f), a.v)}; }
+__device__ __forceinline__ F2 operator-(F2 a) { return {make_float2(-a.v.x, -a.v.y)}; }
+__device__ __forceinline__ F2 operator*(F2 a, F2 b) { return {__fmul2_rn(a.v, b.v)}; }
+__device__ __forceinline__ F2 operator*(float s, F2 b) { return {__fmul2_rn(make_float2(s, s), b.v)}; }
+__device__ __forceinline__ F2 operator+(float s, F2 b) { return {__fadd2_rn(make_float2(s, s), b.v)}; }
+__device__ __forceinline__ F2 vfma(F2 a, F2 b, F2 c) { return {__ffma2_rn(a.v, b.v, c.v)}; }
+__device__ __forceinline__ F2 vfma(float a, F2 b, F2 c) { return {__ffma2_rn(make_float2(a, a), b.v, c.v)}; }
+__device__ __forceinline__ F2 vrcp(F2 a) { return {make_float2(__frcp_rn(a.v.x), __frcp_rn(a.v.y))}; }
+__device__ __forceinline__ float vfma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ float vrcp(float a) { return __frcp_rn(a); }
+template <typename V> __device__ __forceinline__ V vconst(float s);
+template <> __device__ __forceinline__ float vconst<float>(float s) { return s; }
+template <> __device__ __forceinline__ F2 vconst<F2>(float s) { return mk2(s); }
+
 // ---- the 3-point transforms of the factorised central-moment basis -------------------
 // A triplet holds (v(c=-1), v(c=0), v(c=+1)) of one axis; after a forward transform the
 // same slots hold the moments of order 0, 1, 2 along that axis.
 
 // populations -> raw moments (sum v, sum c v, sum c^2 v)
-__device__ __forceinline__ void raw3(float &a, float &b, float &c) {
-    const float s = a + c, d = c - a;
+template <typename V> __device__ __forceinline__ void raw3(V &a, V &b, V &c) {
+    const V s = a + c, d = c - a;
     a = s + b;
     b = d;
     c = s;
 }
 // raw -> central moments about u
-__device__ __forceinline__ void shift3(float &m0, float &m1, float &m2, float u) {
-    const float t = fmaf(u, m0, -2.0f * m1);
-    m1 = fmaf(-u, m0, m1);
-    m2 = fmaf(u, t, m2);
+template <typename V> __device__ __forceinline__ void shift3(V &m0, V &m1, V &m2, V u) {
+    const V t = vfma(u, m0, -2.0f * m1);
+    m1 = vfma(-u, m0, m1);
+    m2 = vfma(u, t, m2);
 }
 // central moments about u -> populations
-__device__ __forceinline__ void inv3(float &m0, float &m1, float &m2, float u) {
-    const float r1 = fmaf(u, m0, m1);
-    const float r2 = fmaf(u, m1 + r1, m2);
-    const float hr = 0.5f * r1;
-    const float b = m0 - r2;
-    m0 = fmaf(0.5f, r2, -hr);
-    m2 = fmaf(0.5f, r2, hr);
+template <typename V> __device__ __forceinline__ void inv3(V &m0, V &m1, V &m2, V u) {
+    const V r1 = vfma(u, m0, m1);
+    const V r2 = vfma(u, m1 + r1, m2);
+    const V hr = 0.5f * r1;
+    const V b = m0 - r2;
+    m0 = vfma(0.5f, r2, -hr);
+    m2 = vfma(0.5f, r2, hr);
     m1 = b;
 }
 
@@ -169,15 +194,15 @@ template <int S> __host__ __device__ constexpr int tri_base(int k) {
     return S == 1 ? 3 * k : S == 3 ? (k % 3) + 9 * (k / 3) : k;
 }
 
-template <int S> __device__ __forceinline__ void sweep_raw(float (&h)[27]) {
+template <int S, typename V> __device__ __forceinline__ void sweep_raw(V (&h)[27]) {
 #pragma unroll
     for (int k = 0; k < 9; ++k) raw3(h[tri_base<S>(k)], h[tri_base<S>(k) + S], h[tri_base<S>(k) + 2 * S]);
 }
-template <int S> __device__ __forceinline__ void sweep_shift(float (&h)[27], float u) {
+template <int S, typename V> __device__ __forceinline__ void sweep_shift(V (&h)[27], V u) {
 #pragma unroll
     for (int k = 0; k < 9; ++k) shift3(h[tri_base<S>(k)], h[tri_base<S>(k) + S], h[tri_base<S>(k) + 2 * S], u);
 }
-template <int S> __device__ __forceinline__ void sweep_inv(float (&h)[27], float u) {
+template <int S, typename V> __device__ __forceinline__ void sweep_inv(V (&h)[27], V u) {
 #pragma unroll
     for (int k = 0; k < 9; ++k) inv3(h[tri_base<S>(k)], h[tri_base<S>(k) + S], h[tri_base<S>(k) + 2 * S], u);
 }
@@ -194,81 +219,88 @@ template <int S> __device__ __forceinline__ void sweep_inv(float (&h)[27], float
 // central moments rho0 t_p(u_x) t_q(u_y) t_r(u_z), t = (1, -u, 1/3 + u^2), so with
 // e = kappa_eq - rho0 t t t the update reads h' = e + (1 - omega)(h - e) + (1 - omega/2) R^F
 // in moment space, every term small; the e are expanded to avoid cancellation.
-__device__ __forceinline__ void collide(float (&h)[27], float Fx, float Fy, float Fz, const StepParams &P,
-                                        float &rho, float &ux, float &uy, float &uz) {
+template <typename V>
+__device__ __forceinline__ void collide_v(V (&h)[27], V Fx, V Fy, V Fz, const StepParams &P, V &rho, V &ux, V &uy,
+                                          V &uz) {
     sweep_raw<1>(h);
     sweep_raw<3>(h);
     sweep_raw<9>(h);
-    const float rhop = h[K(0, 0, 0)];            // rho - rho0
+    const V rhop = h[K(0, 0, 0)];            // rho - rho0
     rho = P.rho0 + rhop;
-    const float inv = __frcp_rn(rho);
-    ux = (h[K(1, 0, 0)] + 0.5f * Fx) * inv;
-    uy = (h[K(0, 1, 0)] + 0.5f * Fy) * inv;
-    uz = (h[K(0, 0, 1)] + 0.5f * Fz) * inv;
+    const V inv = vrcp(rho);
+    ux = vfma(0.5f, Fx, h[K(1, 0, 0)]) * inv;
+    uy = vfma(0.5f, Fy, h[K(0, 1, 0)]) * inv;
+    uz = vfma(0.5f, Fz, h[K(0, 0, 1)]) * inv;
     sweep_shift<1>(h, ux);
     sweep_shift<3>(h, uy);
     sweep_shift<9>(h, uz);
 
     const float r0 = P.rho0;
-    const float ux2 = ux * ux, uy2 = uy * uy, uz2 = uz * uz;
-    const float tx = (1.0f / 3.0f) + ux2, ty = (1.0f / 3.0f) + uy2, tz = (1.0f / 3.0f) + uz2;
+    const V ux2 = ux * ux, uy2 = uy * uy, uz2 = uz * uz;
     const float third = 1.0f / 3.0f, ninth = 1.0f / 9.0f;
+    const V tx = third + ux2, ty = third + uy2, tz = third + uz2;
 
     // order 1: conserved, kappa'_100 = F_x / 2  (stored as deviation moment rho0 u_x + F_x/2)
-    h[K(1, 0, 0)] = fmaf(r0, ux, 0.5f * Fx);
-    h[K(0, 1, 0)] = fmaf(r0, uy, 0.5f * Fy);
-    h[K(0, 0, 1)] = fmaf(r0, uz, 0.5f * Fz);
+    h[K(1, 0, 0)] = vfma(r0, ux, 0.5f * Fx);
+    h[K(0, 1, 0)] = vfma(r0, uy, 0.5f * Fy);
+    h[K(0, 0, 1)] = vfma(r0, uz, 0.5f * Fz);
 
+#define RELAX(idx, e, r) { const V e_ = (e); h[idx] = vfma(vconst<V>(r), h[idx] - e_, e_); }
+#define RELAXF(idx, e, r, fr) { const V e_ = (e); h[idx] = vfma(vconst<V>(r), h[idx] - e_, e_ + (fr)); }
     // order 2, off-diagonal (shear)
-#define RELAX(idx, e, r) { const float e_ = (e); h[idx] = fmaf((r), h[idx] - e_, e_); }
-#define RELAXF(idx, e, r, fr) { const float e_ = (e); h[idx] = fmaf((r), h[idx] - e_, e_ + (fr)); }
-    RELAX(K(1, 1, 0), -r0 * ux * uy, P.rs);
-    RELAX(K(1, 0, 1), -r0 * ux * uz, P.rs);
-    RELAX(K(0, 1, 1), -r0 * uy * uz, P.rs);
+    RELAX(K(1, 1, 0), -r0 * (ux * uy), P.rs);
+    RELAX(K(1, 0, 1), -r0 * (ux * uz), P.rs);
+    RELAX(K(0, 1, 1), -r0 * (uy * uz), P.rs);
     // order 2, diagonal: trace (bulk) and two deviators (shear)
     {
-        const float e200 = fmaf(third, rhop, -r0 * ux2);
-        const float e020 = fmaf(third, rhop, -r0 * uy2);
-        const float e002 = fmaf(third, rhop, -r0 * uz2);
-        const float a = h[K(2, 0, 0)] - e200, b = h[K(0, 2, 0)] - e020, c = h[K(0, 0, 2)] - e002;
-        const float tr = P.rb * (a + b + c);
-        const float d1 = P.rs * (a - b);
-        const float d2 = P.rs * (a - c);
-        h[K(2, 0, 0)] = e200 + third * (tr + d1 + d2);
-        h[K(0, 2, 0)] = e020 + third * (tr - 2.0f * d1 + d2);
-        h[K(0, 0, 2)] = e002 + third * (tr + d1 - 2.0f * d2);
+        const V e200 = vfma(third, rhop, -r0 * ux2);
+        const V e020 = vfma(third, rhop, -r0 * uy2);
+        const V e002 = vfma(third, rhop, -r0 * uz2);
+        const V a = h[K(2, 0, 0)] - e200, b = h[K(0, 2, 0)] - e020, c = h[K(0, 0, 2)] - e002;
+        const V tr = P.rb * (a + b + c);
+        const V d1 = P.rs * (a - b);
+        const V d2 = P.rs * (a - c);
+        h[K(2, 0, 0)] = vfma(third, tr + d1 + d2, e200);
+        h[K(0, 2, 0)] = vfma(third, vfma(-2.0f, d1, tr + d2), e020);
+        h[K(0, 0, 2)] = vfma(third, vfma(-2.0f, d2, tr + d1), e002);
     }
     // order 3 (force moments F/3 on 210, 201, 120, 021, 102, 012)
-    RELAXF(K(2, 1, 0), r0 * uy * tx, P.r3, P.q3 * third * Fy);
-    RELAXF(K(2, 0, 1), r0 * uz * tx, P.r3, P.q3 * third * Fz);
-    RELAXF(K(1, 2, 0), r0 * ux * ty, P.r3, P.q3 * third * Fx);
-    RELAXF(K(0, 2, 1), r0 * uz * ty, P.r3, P.q3 * third * Fz);
-    RELAXF(K(1, 0, 2), r0 * ux * tz, P.r3, P.q3 * third * Fx);
-    RELAXF(K(0, 1, 2), r0 * uy * tz, P.r3, P.q3 * third * Fy);
-    RELAX(K(1, 1, 1), r0 * ux * uy * uz, P.r3);
+    const float q3t = P.q3 * third, q5n = P.q5 * ninth;
+    RELAXF(K(2, 1, 0), r0 * (uy * tx), P.r3, q3t * Fy);
+    RELAXF(K(2, 0, 1), r0 * (uz * tx), P.r3, q3t * Fz);
+    RELAXF(K(1, 2, 0), r0 * (ux * ty), P.r3, q3t * Fx);
+    RELAXF(K(0, 2, 1), r0 * (uz * ty), P.r3, q3t * Fz);
+    RELAXF(K(1, 0, 2), r0 * (ux * tz), P.r3, q3t * Fx);
+    RELAXF(K(0, 1, 2), r0 * (uy * tz), P.r3, q3t * Fy);
+    RELAX(K(1, 1, 1), r0 * (ux * uy * uz), P.r3);
     // order 4
-    RELAX(K(2, 2, 0), fmaf(ninth, rhop, -r0 * fmaf(ux2, uy2, third * (ux2 + uy2))), P.r4);
-    RELAX(K(2, 0, 2), fmaf(ninth, rhop, -r0 * fmaf(ux2, uz2, third * (ux2 + uz2))), P.r4);
-    RELAX(K(0, 2, 2), fmaf(ninth, rhop, -r0 * fmaf(uy2, uz2, third * (uy2 + uz2))), P.r4);
-    RELAX(K(2, 1, 1), -r0 * tx * uy * uz, P.r4);
-    RELAX(K(1, 2, 1), -r0 * ty * ux * uz, P.r4);
-    RELAX(K(1, 1, 2), -r0 * tz * ux * uy, P.r4);
+    RELAX(K(2, 2, 0), vfma(ninth, rhop, -r0 * vfma(ux2, uy2, third * (ux2 + uy2))), P.r4);
+    RELAX(K(2, 0, 2), vfma(ninth, rhop, -r0 * vfma(ux2, uz2, third * (ux2 + uz2))), P.r4);
+    RELAX(K(0, 2, 2), vfma(ninth, rhop, -r0 * vfma(uy2, uz2, third * (uy2 + uz2))), P.r4);
+    RELAX(K(2, 1, 1), -r0 * (tx * (uy * uz)), P.r4);
+    RELAX(K(1, 2, 1), -r0 * (ty * (ux * uz)), P.r4);
+    RELAX(K(1, 1, 2), -r0 * (tz * (ux * uy)), P.r4);
     // order 5 (force moments F/9 on 221, 212, 122)
-    RELAXF(K(2, 2, 1), r0 * uz * tx * ty, P.r5, P.q5 * ninth * Fz);
-    RELAXF(K(2, 1, 2), r0 * uy * tx * tz, P.r5, P.q5 * ninth * Fy);
-    RELAXF(K(1, 2, 2), r0 * ux * ty * tz, P.r5, P.q5 * ninth * Fx);
+    RELAXF(K(2, 2, 1), r0 * (uz * (tx * ty)), P.r5, q5n * Fz);
+    RELAXF(K(2, 1, 2), r0 * (uy * (tx * tz)), P.r5, q5n * Fy);
+    RELAXF(K(1, 2, 2), r0 * (ux * (ty * tz)), P.r5, q5n * Fx);
     // order 6
     {
-        const float s1 = ux2 + uy2 + uz2;
-        const float s2 = ux2 * uy2 + ux2 * uz2 + uy2 * uz2;
-        const float s3 = ux2 * uy2 * uz2;
-        RELAX(K(2, 2, 2), (1.0f / 27.0f) * rhop - r0 * (ninth * s1 + third * s2 + s3), P.r6);
+        const V s1 = ux2 + uy2 + uz2;
+        const V s2 = ux2 * uy2 + ux2 * uz2 + uy2 * uz2;
+        const V s3 = ux2 * uy2 * uz2;
+        RELAX(K(2, 2, 2), vfma(1.0f / 27.0f, rhop, -r0 * vfma(ninth, s1, vfma(third, s2, s3))), P.r6);
     }
 #undef RELAX
 #undef RELAXF
     sweep_inv<9>(h, uz);
     sweep_inv<3>(h, uy);
     sweep_inv<1>(h, ux);
+}
+
+__device__ __forceinline__ void collide(float (&h)[27], float Fx, float Fy, float Fz, const StepParams &P,
+                                        float &rho, float &ux, float &uy, float &uz) {
+    collide_v<float>(h, Fx, Fy, Fz, P, rho, ux, uy, uz);
 }
 
 }  // namespace lbm
