@@ -123,8 +123,6 @@ int lbm_create(lbm_ctx **out, int nx, int ny, int nz, double nu, const double fo
     if (forcing) for (int a = 0; a < 3; ++a) h->forcing[a] = forcing[a];
     h->cfg = c;
     h->stream = (cudaStream_t)c.cuda_stream;
-    // LBM_PAIRED=0 selects the one-node-per-thread main kernel (same arithmetic, for comparison)
-    if (const char *e = std::getenv("LBM_PAIRED")) h->paired = std::atoi(e) != 0;
 
     auto bail = [&](int rc) {
         std::string msg = h->err;

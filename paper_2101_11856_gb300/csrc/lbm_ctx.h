@@ -31,7 +31,6 @@ struct lbm_ctx {
     float *inlet_profile = nullptr;
     long long t = 0;
     bool has_state = false;
-    int paired = 1;             // main step kernel on node pairs (packed FP32) where nx is even
 
     // immersed solid (samples sorted by base cell)
     long long S = 0, nband = 0, ntiles = 0;
@@ -137,7 +136,6 @@ inline lbm::StepParams make_params(const lbm_ctx *h, long long t) {
     g.ncell = (int)h->N;
     g.nyz = h->ny * h->nz;
     g.plane = h->plane;
-    g.paired = h->paired;
     for (int a = 0; a < 3; ++a) g.periodic[a] = h->cfg.face_type[2 * a] == LBM_FACE_PERIODIC;
     for (int k = 0; k < 6; ++k) g.face[k] = h->cfg.face_type[k];
     P.rho0 = (float)h->cfg.rho0;

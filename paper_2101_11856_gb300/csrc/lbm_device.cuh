@@ -58,7 +58,6 @@ struct Geometry {
     long long plane;     // elements between consecutive direction planes (>= ncell)
     int periodic[3];
     int face[6];         // FaceType of -x, +x, -y, +y, -z, +z
-    int paired;          // run the main range two nodes per thread where nx allows it
 };
 
 struct StepParams {
@@ -137,29 +136,10 @@ __device__ __forceinline__ Nbr neighbour(const Geometry &g, int D, int x, int y,
     return n;
 }
 
-// ---- arithmetic on one node (float) or on two adjacent nodes at once (F2) --------------
-// F2 carries the same FP32 arithmetic for two nodes in the packed FP32 instructions of
-// sm_100+ (one FMA / add / multiply instruction for both), so a thread that updates two
-// nodes issues about half the floating-point instructions.  Every operation is IEEE FP32
-// with round-to-nearest, component by component.
-struct F2 {
-    float2 v;
-};
-__device__ __forceinline__ F2 mk2(float s) { return {make_float2(s, s)}; }
-__device__ __forceinline__ F2 operator+(F2 a, F2 b) { return {__fadd2_rn(a.v, b.v)}; }
-__device__ __forceinline__ F2 operator-(F2 a, F2 b) { return {__ffma2_rn(b.v, make_float2(-1.0f, -1.0f), a.v)}; }
-__device__ __forceinline__ F2 operator-(F2 a) { return {make_float2(-a.v.x, -a.v.y)}; }
-__device__ __forceinline__ F2 operator*(F2 a, F2 b) { return {__fmul2_rn(a.v, b.v)}; }
-__device__ __forceinline__ F2 operator*(float s, F2 b) { return {__fmul2_rn(make_float2(s, s), b.v)}; }
-__device__ __forceinline__ F2 operator+(float s, F2 b) { return {__fadd2_rn(make_float2(s, s), b.v)}; }
-__device__ __forceinline__ F2 vfma(F2 a, F2 b, F2 c) { return {__ffma2_rn(a.v, b.v, c.v)}; }
-__device__ __forceinline__ F2 vfma(float a, F2 b, F2 c) { return {__ffma2_rn(make_float2(a, a), b.v, c.v)}; }
-__device__ __forceinline__ F2 vrcp(F2 a) { return {make_float2(__frcp_rn(a.v.x), __frcp_rn(a.v.y))}; }
+// ---- scalar helpers of the templated arithmetic ---------------------------------------
 __device__ __forceinline__ float vfma(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ float vrcp(float a) { return __frcp_rn(a); }
-template <typename V> __device__ __forceinline__ V vconst(float s);
-template <> __device__ __forceinline__ float vconst<float>(float s) { return s; }
-template <> __device__ __forceinline__ F2 vconst<F2>(float s) { return mk2(s); }
+template <typename V> __device__ __forceinline__ V vconst(float s) { return V(s); }
 
 // ---- the 3-point transforms of the factorised central-moment basis -------------------
 // A triplet holds (v(c=-1), v(c=0), v(c=+1)) of one axis; after a forward transform the

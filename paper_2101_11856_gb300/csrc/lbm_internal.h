@@ -18,9 +18,6 @@ cudaError_t launch_step(int storage, const StepParams &P, bool band, int part, c
 long long boundary_count(const Geometry &g);
 __host__ __device__ inline bool has_interior(const Geometry &g) { return g.nx >= 2 * XEDGE + 1; }
 __host__ __device__ inline int edge_per_row(const Geometry &g) { return has_interior(g) ? 2 * XEDGE : g.nx; }
-// the main range runs two nodes per thread (k_step_main2) when every node pair starts on an
-// even cell index, i.e. nx even; otherwise one node per thread (k_step_main)
-__host__ __device__ inline bool paired_main(const Geometry &g) { return (g.nx % 2) == 0 && g.paired; }
 cudaError_t launch_init(int storage, const StepParams &P, const float *rho, const float *u, cudaStream_t st);
 long long macro_blocks(const StepParams &P);
 // rows of the k_macro partial sums: mass, momentum x/y/z, slab kinetic energy

@@ -34,90 +34,6 @@ __global__ void __launch_bounds__(STEP_BX) k_step_main(StepParams P) {
     else store_yzface<St>(P, y, z, cell, h);
 }
 
-// ---- two adjacent nodes per thread ---------------------------------------------------------
-// k_step_main2 updates the node pair (x, x+1), x even, with the packed FP32 arithmetic of
-// collide_v<F2>.  With nx even every pair starts on an even cell index, so the directions
-// with c_x = 0 move the pair with one aligned two-element access; the c_x = +-1 directions of
-// odd steps are shifted by one element and use two element accesses.
-template <typename T> struct PairIO;
-template <> struct PairIO<float> {
-    static __device__ __forceinline__ F2 ld(const float *p) { return {*reinterpret_cast<const float2 *>(p)}; }
-    static __device__ __forceinline__ void st(float *p, F2 v) { *reinterpret_cast<float2 *>(p) = v.v; }
-};
-template <> struct PairIO<__half> {
-    static __device__ __forceinline__ F2 ld(const __half *p) { return {__half22float2(*reinterpret_cast<const __half2 *>(p))}; }
-    static __device__ __forceinline__ void st(__half *p, F2 v) { *reinterpret_cast<__half2 *>(p) = __float22half2_rn(v.v); }
-};
-template <> struct PairIO<__nv_bfloat16> {
-    static __device__ __forceinline__ F2 ld(const __nv_bfloat16 *p) {
-        return {__bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(p))};
-    }
-    static __device__ __forceinline__ void st(__nv_bfloat16 *p, F2 v) {
-        *reinterpret_cast<__nv_bfloat162 *>(p) = __float22bfloat162_rn(v.v);
-    }
-};
-// pair access at p, aligned when the x offset is even (A = true)
-template <typename St, bool A> __device__ __forceinline__ F2 ld_pair(const St *p) {
-    if (A) return PairIO<St>::ld(p);
-    return {make_float2(Store<St>::ld(p), Store<St>::ld(p + 1))};
-}
-template <typename St, bool A> __device__ __forceinline__ void st_pair(St *p, F2 v) {
-    if (A) PairIO<St>::st(p, v);
-    else {
-        Store<St>::st(p, v.v.x);
-        Store<St>::st(p + 1, v.v.y);
-    }
-}
-
-template <typename St, bool NB, bool BAND>
-__global__ void __launch_bounds__(STEP_BX) k_step_main2(StepParams P) {
-    const int x = 2 * (blockIdx.x * STEP_BX + threadIdx.x) + XEDGE;
-    if (x >= P.g.nx - XEDGE) return;
-    const int y = blockIdx.y, z = blockIdx.z;
-    const int cell = x + P.g.nx * (y + P.g.ny * z);
-    const bool inner = y >= 1 && y <= P.g.ny - 2 && z >= 1 && z <= P.g.nz - 2;   // uniform per block
-    F2 h[27];
-    int off[9];
-    bool bb[9];
-    if (NB && !inner) yz_rows<-1>(P.g, y, z, off, bb);
-#pragma unroll
-    for (int d = 0; d < 27; ++d) {
-        if (!NB) {
-            h[d] = ld_pair<St, true>(static_cast<const St *>(P.fp[d]) + cell);
-        } else if (inner) {
-            const St *p = static_cast<const St *>(P.fp[opp(d)]) + (cell - (cy(d) * P.g.nx + cz(d) * P.g.nxy)) - cx(d);
-            h[d] = cx(d) == 0 ? ld_pair<St, true>(p) : ld_pair<St, false>(p);
-        } else if (bb[d / 3]) {
-            h[d] = ld_pair<St, true>(static_cast<const St *>(P.fp[d]) + cell);
-        } else {
-            const St *p = static_cast<const St *>(P.fp[opp(d)]) + (cell + off[d / 3]) - cx(d);
-            h[d] = cx(d) == 0 ? ld_pair<St, true>(p) : ld_pair<St, false>(p);
-        }
-    }
-    float Fx0, Fy0, Fz0, Fx1, Fy1, Fz1;
-    band_force<BAND>(P, cell, Fx0, Fy0, Fz0);
-    band_force<BAND>(P, cell + 1, Fx1, Fy1, Fz1);
-    F2 rho, ux, uy, uz;
-    collide_v<F2>(h, {make_float2(Fx0, Fx1)}, {make_float2(Fy0, Fy1)}, {make_float2(Fz0, Fz1)}, P, rho, ux, uy, uz);
-    if (NB && !inner) yz_rows<+1>(P.g, y, z, off, bb);
-#pragma unroll
-    for (int d = 0; d < 27; ++d) {
-        if (!NB) {
-            st_pair<St, true>(static_cast<St *>(P.fpo[opp(d)]) + cell, h[d]);
-        } else if (inner) {
-            St *p = static_cast<St *>(P.fpo[d]) + (cell + (cy(d) * P.g.nx + cz(d) * P.g.nxy)) + cx(d);
-            if (cx(d) == 0) st_pair<St, true>(p, h[d]);
-            else st_pair<St, false>(p, h[d]);
-        } else if (bb[d / 3]) {
-            st_pair<St, true>(static_cast<St *>(P.fpo[opp(d)]) + cell, h[d]);
-        } else {
-            St *p = static_cast<St *>(P.fpo[d]) + (cell + off[d / 3]) + cx(d);
-            if (cx(d) == 0) st_pair<St, true>(p, h[d]);
-            else st_pair<St, false>(p, h[d]);
-        }
-    }
-}
-
 // one warp per edge strip of one (y, z) row: blockIdx.x = strip (rows too short for the main
 // kernel are covered by consecutive warps), blockIdx.y = y, blockIdx.z = z
 template <typename St, bool NB, bool BAND>
@@ -392,9 +308,6 @@ static cudaError_t launch_step_tt(const StepParams &P, int part, cudaStream_t st
     if (part == STEP_BOUNDARY) {
         const dim3 grid(has_interior(g) ? 2 : blocks_for(g.nx, XEDGE), g.ny, g.nz);
         k_step_edges<St, NB, BAND><<<grid, XEDGE, 0, st>>>(P);
-    } else if (has_interior(g) && paired_main(g)) {
-        const dim3 grid(blocks_for((g.nx - 2 * XEDGE) / 2, STEP_BX), g.ny, g.nz);
-        k_step_main2<St, NB, BAND><<<grid, STEP_BX, 0, st>>>(P);
     } else if (has_interior(g)) {
         const dim3 grid(blocks_for(g.nx - 2 * XEDGE, STEP_BX), g.ny, g.nz);
         k_step_main<St, NB, BAND><<<grid, STEP_BX, 0, st>>>(P);
