@@ -202,7 +202,11 @@ __global__ void __launch_bounds__(256) k_band_moments(StepParams P, const int *_
     int x, y, z;
     decompose(P.g, cell, x, y, z);
     float h[27];
-    load_general<St, NB>(P, x, y, z, cell, h);
+    // nodes away from every face pull with constant offsets; the rest apply the face rules
+    if (x >= 1 && x <= P.g.nx - 2 && y >= 1 && y <= P.g.ny - 2 && z >= 1 && z <= P.g.nz - 2)
+        load_interior<St, NB>(P, cell, h);
+    else
+        load_general<St, NB>(P, x, y, z, cell, h);
     float rp = 0.0f, px = 0.0f, py = 0.0f, pz = 0.0f;
 #pragma unroll
     for (int d = 0; d < 27; ++d) {
