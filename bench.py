@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--no-fp16", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--adjoint-only", action="store_true", help="time only the adjoint workload")
     return ap.parse_args()
 
 
@@ -222,6 +223,9 @@ def main():
     import torch
     from paper_2101_11856_gb300 import Solver, lbm
     lbm.library()
+    if args.adjoint_only:
+        print(json.dumps({"adjoint": adjoint_cost(torch, args)}))
+        return
     rank, world = int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
