@@ -156,71 +156,92 @@ __device__ __forceinline__ void store_yzface(const StepParams &P, int y, int z, 
 // strip of one (y, z) row: the y/z rows come from yz_rows (uniform), and only the lanes at
 // x = 0 or x = nx-1 take the x-face rule for the directions whose source (pull) or target
 // (push) lies across that face.  Priority at edges: no-slip > inlet > outlet.
-template <typename St, bool NB>
-__device__ __forceinline__ void load_edge(const StepParams &P, int x, int y, int z, int cell, float (&h)[27]) {
+// Row offsets of the 9 (c_y, c_z) neighbour rows, pull (S = -1) or push (S = +1): constant
+// offsets for a row away from the y/z faces (INNER), else yz_rows (wrap / no-slip flags).
+template <int S, bool INNER>
+__device__ __forceinline__ void row_offsets(const Geometry &g, int y, int z, int (&off)[9], bool (&bb)[9]) {
+    if (INNER) {
+#pragma unroll
+        for (int j = 0; j < 9; ++j) {
+            off[j] = S * ((j % 3 - 1) * g.nx + (j / 3 - 1) * g.nxy);
+            bb[j] = false;
+        }
+    } else {
+        yz_rows<S>(g, y, z, off, bb);
+    }
+}
+
+template <typename St, bool NB, bool INNER>
+__device__ __forceinline__ void load_edge_t(const StepParams &P, int x, int y, int z, int cell, float (&h)[27]) {
     int off[9];
     bool bb[9];
-    yz_rows<-1>(P.g, y, z, off, bb);
-    const bool xlo = x == 0, xhi = x == P.g.nx - 1, per = P.g.periodic[0];
-    // every lane loads: the x-face lanes read their own slot (bounce-back / inlet / outlet
-    // placeholder) or the wrapped source, chosen by address, without divergence
+    row_offsets<-1, INNER>(P.g, y, z, off, bb);
+    const bool xlo = x == 0, xhi = x == P.g.nx - 1;
+    // every lane pulls as an interior node; the lanes at x = 0 / nx-1 read their own slot for
+    // the directions whose source lies across the x face, and are fixed up below
 #pragma unroll
     for (int d = 0; d < 27; ++d) {
         const int j = d / 3;
-        const St *own = static_cast<const St *>(P.fp[d]) + cell;
-        const St *p = own;
-        if (NB && !bb[j]) {
-            const St *src = static_cast<const St *>(P.fp[opp(d)]) + (cell + off[j]);
-            if (cx(d) == 0) p = src;
-            else {
-                const bool xc = cx(d) == 1 ? xlo : xhi;
-                p = xc ? (per ? src + cx(d) * (P.g.nx - 1) : own) : src - cx(d);
-            }
+        if (!NB) {
+            h[d] = Store<St>::ld(static_cast<const St *>(P.fp[d]) + cell);
+            continue;
         }
-        h[d] = Store<St>::ld(p);
+        bool own = bb[j];
+        if (cx(d) == 1) own = own || xlo;
+        if (cx(d) == -1) own = own || xhi;
+        const St *base = static_cast<const St *>(own ? P.fp[d] : P.fp[opp(d)]);
+        h[d] = Store<St>::ld(base + (own ? cell : cell + off[j] - cx(d)));
     }
-    // the x-face rules of the face lanes, once per side
-    if (xlo && P.g.face[0] == FACE_INLET) {
-        const float uw = inlet_velocity(P, y, z);
+    // x-face rules of the face lanes (one per warp), once per side
+    if (xlo) {
+        const int ft = P.g.face[0];
+        const float uw = ft == FACE_INLET ? inlet_velocity(P, y, z) : 0.0f;
 #pragma unroll
-        for (int d = 2; d < 27; d += 3)   // c_x = +1: sources across the -x face
-            if (!bb[d / 3]) h[d] += 6.0f * wgt(d) * P.rho0 * uw;
+        for (int d = 2; d < 27; d += 3) {   // c_x = +1: sources across the -x face
+            if (bb[d / 3]) continue;         // no-slip wins at edges
+            if (ft == FACE_PERIODIC && NB)
+                h[d] = Store<St>::ld(static_cast<const St *>(P.fp[opp(d)]) + (cell + off[d / 3] + (P.g.nx - 1)));
+            else if (ft == FACE_INLET)
+                h[d] += 6.0f * wgt(d) * P.rho0 * uw;
+        }
     }
-    if (xhi && P.g.face[1] == FACE_OUTLET) {
-        // outlet ghost: post-collision f_d of (nx-1, y - c_dy, z - c_dz) of the previous step
+    if (xhi) {
+        const int ft = P.g.face[1];
         const St *B = static_cast<const St *>(P.outlet) + (long long)(((P.t - 1) & 1) * 9) * P.g.nyz;
 #pragma unroll
-        for (int d = 0; d < 27; d += 3) {  // c_x = -1: sources across the +x face
+        for (int d = 0; d < 27; d += 3) {   // c_x = -1: sources across the +x face
             if (bb[d / 3]) continue;
-            int ys = y - cy(d), zs = z - cz(d);
-            ys += ys < 0 ? P.g.ny : (ys >= P.g.ny ? -P.g.ny : 0);
-            zs += zs < 0 ? P.g.nz : (zs >= P.g.nz ? -P.g.nz : 0);
-            h[d] = Store<St>::ld(B + (long long)(d / 3) * P.g.nyz + ys + P.g.ny * zs);
+            if (ft == FACE_PERIODIC && NB) {
+                h[d] = Store<St>::ld(static_cast<const St *>(P.fp[opp(d)]) + (cell + off[d / 3] - (P.g.nx - 1)));
+            } else if (ft == FACE_OUTLET) {
+                // outlet ghost: post-collision f_d of (nx-1, y - c_dy, z - c_dz) of the previous step
+                int ys = y - cy(d), zs = z - cz(d);
+                ys += ys < 0 ? P.g.ny : (ys >= P.g.ny ? -P.g.ny : 0);
+                zs += zs < 0 ? P.g.nz : (zs >= P.g.nz ? -P.g.nz : 0);
+                h[d] = Store<St>::ld(B + (long long)(d / 3) * P.g.nyz + ys + P.g.ny * zs);
+            }
         }
     }
 }
 
-template <typename St, bool NB>
-__device__ __forceinline__ void store_edge(const StepParams &P, int x, int y, int z, int cell, const float (&h)[27]) {
+template <typename St, bool NB, bool INNER>
+__device__ __forceinline__ void store_edge_t(const StepParams &P, int x, int y, int z, int cell, const float (&h)[27]) {
     const bool xlo = x == 0, xhi = x == P.g.nx - 1, per = P.g.periodic[0];
     if (NB) {
         int off[9];
         bool bb[9];
-        yz_rows<+1>(P.g, y, z, off, bb);
+        row_offsets<+1, INNER>(P.g, y, z, off, bb);
 #pragma unroll
         for (int d = 0; d < 27; ++d) {
             const int j = d / 3;
-            St *own = static_cast<St *>(P.fpo[opp(d)]) + cell;
-            St *p = own;
-            if (!bb[j]) {
-                St *tgt = static_cast<St *>(P.fpo[d]) + (cell + off[j]);
-                if (cx(d) == 0) p = tgt;
-                else {
-                    const bool xc = cx(d) == 1 ? xhi : xlo;
-                    p = xc ? (per ? tgt - cx(d) * (P.g.nx - 1) : own) : tgt + cx(d);
-                }
-            }
-            Store<St>::st(p, h[d]);
+            bool xc = false;
+            if (cx(d) == 1) xc = xhi;
+            if (cx(d) == -1) xc = xlo;
+            // target across a no-slip face (or a non-periodic x face): the node's own slot
+            const bool own = bb[j] || (xc && !per);
+            const int idx = own ? cell : cell + off[j] + (xc ? -cx(d) * (P.g.nx - 1) : cx(d));
+            St *base = static_cast<St *>(own ? P.fpo[opp(d)] : P.fpo[d]);
+            Store<St>::st(base + idx, h[d]);
         }
     } else {
 #pragma unroll
@@ -232,6 +253,19 @@ __device__ __forceinline__ void store_edge(const StepParams &P, int x, int y, in
         for (int d = 0; d < 27; d += 3)   // the nine directions with c_x = -1
             Store<St>::st(B + (long long)(d / 3) * P.g.nyz, h[d]);
     }
+}
+
+// edge-strip node of a block row: INNER when the row is away from the y/z faces
+template <typename St, bool NB>
+__device__ __forceinline__ void load_edge(const StepParams &P, int x, int y, int z, int cell, float (&h)[27]) {
+    if (y >= 1 && y <= P.g.ny - 2 && z >= 1 && z <= P.g.nz - 2) load_edge_t<St, NB, true>(P, x, y, z, cell, h);
+    else load_edge_t<St, NB, false>(P, x, y, z, cell, h);
+}
+
+template <typename St, bool NB>
+__device__ __forceinline__ void store_edge(const StepParams &P, int x, int y, int z, int cell, const float (&h)[27]) {
+    if (y >= 1 && y <= P.g.ny - 2 && z >= 1 && z <= P.g.nz - 2) store_edge_t<St, NB, true>(P, x, y, z, cell, h);
+    else store_edge_t<St, NB, false>(P, x, y, z, cell, h);
 }
 
 }  // namespace lbm
