@@ -153,8 +153,9 @@ typedef struct lbm_loss {
  * every state and recomputes nothing).
  * Outputs (host pointers, any may be NULL): dL_dinflow[16] = dL/da_mn of the inflow profile
  * (row-major in m; 0 without an inlet), dL_dpos[3*count] = dL/dX_s in the caller's sample
- * order, *L.  Gradients are accumulated in FP64.  Errors: LBM_ESTATE, LBM_EINVAL, LBM_ENOMEM,
- * LBM_ECUDA. */
+ * order, *L.  Gradients are accumulated in FP64.  The device workspace (checkpoints, states,
+ * adjoint arrays) stays with the context for later calls and is freed by lbm_destroy.
+ * Errors: LBM_ESTATE, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA. */
 int lbm_adjoint(lbm_ctx *h, int n, int K, const lbm_loss *loss, double *dL_dinflow, double *dL_dpos, double *L);
 
 /* Checkpoint: serialise the state (header + populations in canonical layout in the

@@ -398,23 +398,16 @@ __global__ void __launch_bounds__(STEP_BX) k_adj_main(StepParams P, AdjParams A)
     }
 }
 
-// Backward step of the edge strips (whole warps; the x-face rules per lane): periodic x wraps,
-// no-slip and inlet faces bounce back (the inlet also feeds the inflow-coefficient gradient),
-// the outlet ghost's use goes to the duplicate buffer for k_adj_outlet.
-template <typename St, bool NB, bool BAND>
-__global__ void __launch_bounds__(XEDGE) k_adj_edges(StepParams P, AdjParams A) {
-    const int x = (has_interior(P.g) && blockIdx.x == 1) ? P.g.nx - XEDGE + threadIdx.x : blockIdx.x * XEDGE + threadIdx.x;
-    if (x >= P.g.nx) return;
-    const int y = blockIdx.y, z = blockIdx.z;
-    const int cell = x + P.g.nx * (y + P.g.ny * z);
-    float fs[27], lam[27];
-    load_edge<St, NB>(P, x, y, z, cell, fs);
-    node_vjp<BAND>(P, A, x, cell, fs, lam);
+// push of mu from an edge-strip node: interior rows use constant row offsets, face rows the
+// wrapped / bounced rows; the x-face lane applies the x rule of its face
+template <bool INNER, int SIDE>
+__device__ __forceinline__ void adj_push_edge(const StepParams &P, const AdjParams &A, int x, int y, int z, int cell,
+                                              const float (&lam)[27]) {
     const long long N = P.g.ncell;
     int off[9];
     bool bb[9];
-    yz_rows<-1>(P.g, y, z, off, bb);
-    const bool xlo = x == 0, xhi = x == P.g.nx - 1;
+    row_offsets<-1, INNER>(P.g, y, z, off, bb);
+    const bool xlo = SIDE != 1 && x == 0, xhi = SIDE != 0 && x == P.g.nx - 1;
     const bool outlet_node = xhi && P.g.face[1] == FACE_OUTLET;
     double sth = 0.0;
 #pragma unroll
@@ -440,6 +433,23 @@ __global__ void __launch_bounds__(XEDGE) k_adj_edges(StepParams P, AdjParams A) 
         if (outlet_node && cx(d) == -1) A.blam[(long long)j * P.g.nyz + y + P.g.ny * z] = ghost ? mu : 0.0f;
     }
     if (xlo && P.g.face[0] == FACE_INLET) A.s_inlet[y + P.g.ny * z] += sth;
+}
+
+// Backward step of the edge strips (one warp per strip and row, EDGE_ROWS rows per block; the
+// x-face rules per lane): periodic x wraps, no-slip and inlet faces bounce back (the inlet also
+// feeds the inflow-coefficient gradient), the outlet ghost's use goes to the duplicate buffer
+// for k_adj_outlet.
+template <typename St, bool NB, bool BAND, int SIDE>
+__global__ void __launch_bounds__(XEDGE * EDGE_ROWS) k_adj_edges(StepParams P, AdjParams A) {
+    const int x = edge_x<SIDE>(P.g);
+    const int y = blockIdx.y * EDGE_ROWS + threadIdx.y, z = blockIdx.z;
+    if (x >= P.g.nx || y >= P.g.ny) return;
+    const int cell = x + P.g.nx * (y + P.g.ny * z);
+    float fs[27], lam[27];
+    load_edge<St, NB, SIDE>(P, x, y, z, cell, fs);
+    node_vjp<BAND>(P, A, x, cell, fs, lam);
+    if (y >= 1 && y <= P.g.ny - 2 && z >= 1 && z <= P.g.nz - 2) adj_push_edge<true, SIDE>(P, A, x, y, z, cell, lam);
+    else adj_push_edge<false, SIDE>(P, A, x, y, z, cell, lam);
 }
 
 // outlet plane: zero the slots of the populations that left through the outlet (no use in
@@ -492,17 +502,54 @@ template <typename F> cudaError_t with_storage(int storage, F &&fn) {
     }
 }
 
+// the adjoint's device workspace, kept by the context between calls: the k-th request of a
+// call reuses the k-th buffer when it is large enough (calls with the same sizes allocate
+// nothing after the first)
 struct AdjBuffers {
-    std::vector<void *> bufs;
-    ~AdjBuffers() {
-        for (void *p : bufs) cudaFree(p);
-    }
-    template <typename T> int get(lbm_ctx *h, T **p, size_t n) {
-        int rc = dev_alloc(h, p, n);
-        if (rc == LBM_OK && *p) bufs.push_back((void *)*p);
-        return rc;
+    lbm_ctx *h;
+    size_t next = 0;
+    explicit AdjBuffers(lbm_ctx *h_) : h(h_) {}
+    template <typename T> int get(lbm_ctx *, T **p, size_t n) {
+        const size_t bytes = n * sizeof(T);
+        if (next == h->adj_ws.size()) h->adj_ws.push_back({nullptr, 0});
+        auto &slot = h->adj_ws[next++];
+        if (slot.second < bytes) {
+            if (slot.first) cudaFree(slot.first);
+            slot = {nullptr, 0};
+            void *q = nullptr;
+            if (cudaMalloc(&q, bytes) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(h, LBM_ENOMEM, "cannot allocate the adjoint workspace (" + std::to_string(bytes) + " bytes)");
+            }
+            slot = {q, bytes};
+        }
+        *p = static_cast<T *>(slot.first);
+        return LBM_OK;
     }
 };
+
+template <typename St, bool NB, bool BAND>
+cudaError_t launch_adj_step_tt(const StepParams &P, const AdjParams &A, cudaStream_t st) {
+    const Geometry &g = P.g;
+    const dim3 eb(XEDGE, EDGE_ROWS);
+    if (has_interior(g)) {
+        const dim3 ge(1, nblocks(g.ny, EDGE_ROWS), g.nz);
+        k_adj_edges<St, NB, BAND, 0><<<ge, eb, 0, st>>>(P, A);
+        k_adj_edges<St, NB, BAND, 1><<<ge, eb, 0, st>>>(P, A);
+        const dim3 gm(nblocks(g.nx - 2 * XEDGE, STEP_BX), g.ny, g.nz);
+        k_adj_main<St, NB, BAND><<<gm, STEP_BX, 0, st>>>(P, A);
+    } else {
+        const dim3 ge(nblocks(g.nx, XEDGE), nblocks(g.ny, EDGE_ROWS), g.nz);
+        k_adj_edges<St, NB, BAND, 2><<<ge, eb, 0, st>>>(P, A);
+    }
+    return cudaGetLastError();
+}
+
+template <typename St>
+cudaError_t launch_adj_step(const StepParams &P, const AdjParams &A, bool nb, bool band, cudaStream_t st) {
+    if (nb) return band ? launch_adj_step_tt<St, true, true>(P, A, st) : launch_adj_step_tt<St, true, false>(P, A, st);
+    return band ? launch_adj_step_tt<St, false, true>(P, A, st) : launch_adj_step_tt<St, false, false>(P, A, st);
+}
 
 }  // namespace
 
@@ -519,7 +566,7 @@ extern "C" int lbm_adjoint(lbm_ctx *h, int n, int K, const lbm_loss *loss, doubl
     const size_t out_bytes = h->outlet ? (size_t)2 * 9 * nyz * h->esize : 0;
     const size_t state_bytes = pop_bytes + out_bytes;
     const int nck = (n + K - 1) / K;
-    AdjBuffers B;
+    AdjBuffers B(h);
     int rc;
     std::vector<char *> ckpt(nck), seg(K);
     for (int i = 0; i < nck; ++i) if ((rc = B.get(h, &ckpt[i], state_bytes))) return rc;
@@ -616,27 +663,7 @@ extern "C" int lbm_adjoint(lbm_ctx *h, int n, int K, const lbm_loss *loss, doubl
             }
             CK(with_storage(h->storage, [&](auto tag) {
                 using St = decltype(tag);
-                const dim3 ge(has_interior(P.g) ? 2 : nblocks(h->nx, XEDGE), h->ny, h->nz);
-                const dim3 gm(has_interior(P.g) ? nblocks(h->nx - 2 * XEDGE, STEP_BX) : 1, h->ny, h->nz);
-                const bool mn = has_interior(P.g);
-                if (nbp) {
-                    if (S > 0) {
-                        k_adj_edges<St, true, true><<<ge, XEDGE, 0, st>>>(P, A);
-                        if (mn) k_adj_main<St, true, true><<<gm, STEP_BX, 0, st>>>(P, A);
-                    } else {
-                        k_adj_edges<St, true, false><<<ge, XEDGE, 0, st>>>(P, A);
-                        if (mn) k_adj_main<St, true, false><<<gm, STEP_BX, 0, st>>>(P, A);
-                    }
-                } else {
-                    if (S > 0) {
-                        k_adj_edges<St, false, true><<<ge, XEDGE, 0, st>>>(P, A);
-                        if (mn) k_adj_main<St, false, true><<<gm, STEP_BX, 0, st>>>(P, A);
-                    } else {
-                        k_adj_edges<St, false, false><<<ge, XEDGE, 0, st>>>(P, A);
-                        if (mn) k_adj_main<St, false, false><<<gm, STEP_BX, 0, st>>>(P, A);
-                    }
-                }
-                return cudaGetLastError();
+                return launch_adj_step<St>(P, A, nbp, S > 0, st);
             }));
             if (h->outlet) {
                 k_adj_outlet<<<nblocks(nyz, 128), 128, 0, st>>>(P, A);

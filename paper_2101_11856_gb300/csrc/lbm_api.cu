@@ -184,6 +184,8 @@ int lbm_destroy(lbm_ctx *h) {
         cudaEventDestroy(r.b);
     }
     for (auto e : h->pool) cudaEventDestroy(e);
+    for (auto &w : h->adj_ws)
+        if (w.first) cudaFree(w.first);
     delete h;
     return LBM_OK;
 }

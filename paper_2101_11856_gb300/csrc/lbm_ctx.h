@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "lbm.h"
@@ -53,6 +54,9 @@ struct lbm_ctx {
     std::vector<cudaEvent_t> pool;
     double ms[LBM_NUM_KERNEL_KINDS] = {};
     long long launches[LBM_NUM_KERNEL_KINDS] = {};
+
+    // device workspace of lbm_adjoint (pointer, bytes), reused by later calls
+    std::vector<std::pair<void *, size_t>> adj_ws;
 
     std::string err;
 };

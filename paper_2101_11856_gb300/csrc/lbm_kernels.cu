@@ -34,21 +34,21 @@ __global__ void __launch_bounds__(STEP_BX) k_step_main(StepParams P) {
     else store_yzface<St>(P, y, z, cell, h);
 }
 
-// one warp per edge strip of one (y, z) row: blockIdx.x = strip (rows too short for the main
-// kernel are covered by consecutive warps), blockIdx.y = y, blockIdx.z = z
-template <typename St, bool NB, bool BAND>
-__global__ void __launch_bounds__(XEDGE) k_step_edges(StepParams P) {
-    const int x = (has_interior(P.g) && blockIdx.x == 1) ? P.g.nx - XEDGE + threadIdx.x : blockIdx.x * XEDGE + threadIdx.x;
-    if (x >= P.g.nx) return;
-    const int y = blockIdx.y, z = blockIdx.z;
+// one warp per edge strip of one row, EDGE_ROWS rows (y) per block: blockIdx.y * EDGE_ROWS +
+// threadIdx.y = y, blockIdx.z = z; SIDE picks the strip (see edge_x)
+template <typename St, bool NB, bool BAND, int SIDE>
+__global__ void __launch_bounds__(XEDGE * EDGE_ROWS) k_step_edges(StepParams P) {
+    const int x = edge_x<SIDE>(P.g);
+    const int y = blockIdx.y * EDGE_ROWS + threadIdx.y, z = blockIdx.z;
+    if (x >= P.g.nx || y >= P.g.ny) return;
     const int cell = x + P.g.nx * (y + P.g.ny * z);
     float h[27];
-    load_edge<St, NB>(P, x, y, z, cell, h);
+    load_edge<St, NB, SIDE>(P, x, y, z, cell, h);
     float Fx, Fy, Fz;
     band_force<BAND>(P, cell, Fx, Fy, Fz);
     float rho, ux, uy, uz;
     collide(h, Fx, Fy, Fz, P, rho, ux, uy, uz);
-    store_edge<St, NB>(P, x, y, z, cell, h);
+    store_edge<St, NB, SIDE>(P, x, y, z, cell, h);
 }
 
 // ---- initialisation: f = f_eq(rho, u), stored as the post-collision state of t = 0 ------
@@ -310,8 +310,15 @@ template <typename St, bool NB, bool BAND>
 static cudaError_t launch_step_tt(const StepParams &P, int part, cudaStream_t st) {
     const Geometry &g = P.g;
     if (part == STEP_BOUNDARY) {
-        const dim3 grid(has_interior(g) ? 2 : blocks_for(g.nx, XEDGE), g.ny, g.nz);
-        k_step_edges<St, NB, BAND><<<grid, XEDGE, 0, st>>>(P);
+        const dim3 block(XEDGE, EDGE_ROWS);
+        if (has_interior(g)) {
+            const dim3 grid(1, blocks_for(g.ny, EDGE_ROWS), g.nz);
+            k_step_edges<St, NB, BAND, 0><<<grid, block, 0, st>>>(P);
+            k_step_edges<St, NB, BAND, 1><<<grid, block, 0, st>>>(P);
+        } else {
+            const dim3 grid(blocks_for(g.nx, XEDGE), blocks_for(g.ny, EDGE_ROWS), g.nz);
+            k_step_edges<St, NB, BAND, 2><<<grid, block, 0, st>>>(P);
+        }
     } else if (has_interior(g)) {
         const dim3 grid(blocks_for(g.nx - 2 * XEDGE, STEP_BX), g.ny, g.nz);
         k_step_main<St, NB, BAND><<<grid, STEP_BX, 0, st>>>(P);

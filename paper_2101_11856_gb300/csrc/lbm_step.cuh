@@ -171,12 +171,14 @@ __device__ __forceinline__ void row_offsets(const Geometry &g, int y, int z, int
     }
 }
 
-template <typename St, bool NB, bool INNER>
+// SIDE: 0 = left strip (only x = 0 can be a face lane), 1 = right strip (only x = nx-1),
+// 2 = a whole short row (both)
+template <typename St, bool NB, bool INNER, int SIDE>
 __device__ __forceinline__ void load_edge_t(const StepParams &P, int x, int y, int z, int cell, float (&h)[27]) {
     int off[9];
     bool bb[9];
     row_offsets<-1, INNER>(P.g, y, z, off, bb);
-    const bool xlo = x == 0, xhi = x == P.g.nx - 1;
+    const bool xlo = SIDE != 1 && x == 0, xhi = SIDE != 0 && x == P.g.nx - 1;
     // every lane pulls as an interior node; the lanes at x = 0 / nx-1 read their own slot for
     // the directions whose source lies across the x face, and are fixed up below
 #pragma unroll
@@ -224,9 +226,9 @@ __device__ __forceinline__ void load_edge_t(const StepParams &P, int x, int y, i
     }
 }
 
-template <typename St, bool NB, bool INNER>
+template <typename St, bool NB, bool INNER, int SIDE>
 __device__ __forceinline__ void store_edge_t(const StepParams &P, int x, int y, int z, int cell, const float (&h)[27]) {
-    const bool xlo = x == 0, xhi = x == P.g.nx - 1, per = P.g.periodic[0];
+    const bool xlo = SIDE != 1 && x == 0, xhi = SIDE != 0 && x == P.g.nx - 1, per = P.g.periodic[0];
     if (NB) {
         int off[9];
         bool bb[9];
@@ -255,17 +257,24 @@ __device__ __forceinline__ void store_edge_t(const StepParams &P, int x, int y, 
     }
 }
 
-// edge-strip node of a block row: INNER when the row is away from the y/z faces
-template <typename St, bool NB>
+// edge-strip node of a warp row: INNER when the row is away from the y/z faces (warp-uniform)
+template <typename St, bool NB, int SIDE>
 __device__ __forceinline__ void load_edge(const StepParams &P, int x, int y, int z, int cell, float (&h)[27]) {
-    if (y >= 1 && y <= P.g.ny - 2 && z >= 1 && z <= P.g.nz - 2) load_edge_t<St, NB, true>(P, x, y, z, cell, h);
-    else load_edge_t<St, NB, false>(P, x, y, z, cell, h);
+    if (y >= 1 && y <= P.g.ny - 2 && z >= 1 && z <= P.g.nz - 2) load_edge_t<St, NB, true, SIDE>(P, x, y, z, cell, h);
+    else load_edge_t<St, NB, false, SIDE>(P, x, y, z, cell, h);
 }
 
-template <typename St, bool NB>
+template <typename St, bool NB, int SIDE>
 __device__ __forceinline__ void store_edge(const StepParams &P, int x, int y, int z, int cell, const float (&h)[27]) {
-    if (y >= 1 && y <= P.g.ny - 2 && z >= 1 && z <= P.g.nz - 2) store_edge_t<St, NB, true>(P, x, y, z, cell, h);
-    else store_edge_t<St, NB, false>(P, x, y, z, cell, h);
+    if (y >= 1 && y <= P.g.ny - 2 && z >= 1 && z <= P.g.nz - 2) store_edge_t<St, NB, true, SIDE>(P, x, y, z, cell, h);
+    else store_edge_t<St, NB, false, SIDE>(P, x, y, z, cell, h);
 }
+
+// x of an edge-strip thread: SIDE 0 / 1 = left / right strip of a row with a main range,
+// SIDE 2 = consecutive warps over a row too short for the main kernel
+template <int SIDE> __device__ __forceinline__ int edge_x(const Geometry &g) {
+    return SIDE == 0 ? (int)threadIdx.x : SIDE == 1 ? g.nx - XEDGE + (int)threadIdx.x : (int)(blockIdx.x * XEDGE + threadIdx.x);
+}
+constexpr int EDGE_ROWS = 4;   // rows (y) per edge-kernel block, one warp each
 
 }  // namespace lbm
