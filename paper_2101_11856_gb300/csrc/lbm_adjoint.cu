@@ -438,18 +438,32 @@ __device__ __forceinline__ void adj_push_edge(const StepParams &P, const AdjPara
 // Backward step of the edge strips (one warp per strip and row, EDGE_ROWS rows per block; the
 // x-face rules per lane): periodic x wraps, no-slip and inlet faces bounce back (the inlet also
 // feeds the inflow-coefficient gradient), the outlet ghost's use goes to the duplicate buffer
-// for k_adj_outlet.
+// for k_adj_outlet.  Layout as k_step_edges / k_step_rows.
 template <typename St, bool NB, bool BAND, int SIDE>
-__global__ void __launch_bounds__(XEDGE * EDGE_ROWS) k_adj_edges(StepParams P, AdjParams A) {
+__device__ __forceinline__ void adj_edge_node(const StepParams &P, const AdjParams &A, int y, int z) {
     const int x = edge_x<SIDE>(P.g);
-    const int y = blockIdx.y * EDGE_ROWS + threadIdx.y, z = blockIdx.z;
-    if (x >= P.g.nx || y >= P.g.ny) return;
+    if (x >= P.g.nx) return;
     const int cell = x + P.g.nx * (y + P.g.ny * z);
     float fs[27], lam[27];
     load_edge<St, NB, SIDE>(P, x, y, z, cell, fs);
     node_vjp<BAND>(P, A, x, cell, fs, lam);
     if (y >= 1 && y <= P.g.ny - 2 && z >= 1 && z <= P.g.nz - 2) adj_push_edge<true, SIDE>(P, A, x, y, z, cell, lam);
     else adj_push_edge<false, SIDE>(P, A, x, y, z, cell, lam);
+}
+
+template <typename St, bool NB, bool BAND>
+__global__ void __launch_bounds__(XEDGE * EDGE_ROWS) k_adj_edges(StepParams P, AdjParams A) {
+    const int y = blockIdx.y * EDGE_ROWS + threadIdx.y, z = blockIdx.z;
+    if (y >= P.g.ny) return;
+    if (blockIdx.x == 0) adj_edge_node<St, NB, BAND, 0>(P, A, y, z);
+    else adj_edge_node<St, NB, BAND, 1>(P, A, y, z);
+}
+
+template <typename St, bool NB, bool BAND>
+__global__ void __launch_bounds__(XEDGE * EDGE_ROWS) k_adj_rows(StepParams P, AdjParams A) {
+    const int y = blockIdx.y * EDGE_ROWS + threadIdx.y, z = blockIdx.z;
+    if (y >= P.g.ny) return;
+    adj_edge_node<St, NB, BAND, 2>(P, A, y, z);
 }
 
 // outlet plane: zero the slots of the populations that left through the outlet (no use in
@@ -533,14 +547,13 @@ cudaError_t launch_adj_step_tt(const StepParams &P, const AdjParams &A, cudaStre
     const Geometry &g = P.g;
     const dim3 eb(XEDGE, EDGE_ROWS);
     if (has_interior(g)) {
-        const dim3 ge(1, nblocks(g.ny, EDGE_ROWS), g.nz);
-        k_adj_edges<St, NB, BAND, 0><<<ge, eb, 0, st>>>(P, A);
-        k_adj_edges<St, NB, BAND, 1><<<ge, eb, 0, st>>>(P, A);
+        const dim3 ge(2, nblocks(g.ny, EDGE_ROWS), g.nz);
+        k_adj_edges<St, NB, BAND><<<ge, eb, 0, st>>>(P, A);
         const dim3 gm(nblocks(g.nx - 2 * XEDGE, STEP_BX), g.ny, g.nz);
         k_adj_main<St, NB, BAND><<<gm, STEP_BX, 0, st>>>(P, A);
     } else {
         const dim3 ge(nblocks(g.nx, XEDGE), nblocks(g.ny, EDGE_ROWS), g.nz);
-        k_adj_edges<St, NB, BAND, 2><<<ge, eb, 0, st>>>(P, A);
+        k_adj_rows<St, NB, BAND><<<ge, eb, 0, st>>>(P, A);
     }
     return cudaGetLastError();
 }

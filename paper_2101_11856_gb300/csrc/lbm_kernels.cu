@@ -35,12 +35,13 @@ __global__ void __launch_bounds__(STEP_BX) k_step_main(StepParams P) {
 }
 
 // one warp per edge strip of one row, EDGE_ROWS rows (y) per block: blockIdx.y * EDGE_ROWS +
-// threadIdx.y = y, blockIdx.z = z; SIDE picks the strip (see edge_x)
+// threadIdx.y = y, blockIdx.z = z.  With a main range, blockIdx.x picks the left (0) or right
+// (1) strip (one launch for both: measured faster than a launch per side); short rows run the
+// SIDE = 2 kernel over consecutive warps.
 template <typename St, bool NB, bool BAND, int SIDE>
-__global__ void __launch_bounds__(XEDGE * EDGE_ROWS) k_step_edges(StepParams P) {
+__device__ __forceinline__ void edge_node(const StepParams &P, int y, int z) {
     const int x = edge_x<SIDE>(P.g);
-    const int y = blockIdx.y * EDGE_ROWS + threadIdx.y, z = blockIdx.z;
-    if (x >= P.g.nx || y >= P.g.ny) return;
+    if (x >= P.g.nx) return;
     const int cell = x + P.g.nx * (y + P.g.ny * z);
     float h[27];
     load_edge<St, NB, SIDE>(P, x, y, z, cell, h);
@@ -49,6 +50,21 @@ __global__ void __launch_bounds__(XEDGE * EDGE_ROWS) k_step_edges(StepParams P) 
     float rho, ux, uy, uz;
     collide(h, Fx, Fy, Fz, P, rho, ux, uy, uz);
     store_edge<St, NB, SIDE>(P, x, y, z, cell, h);
+}
+
+template <typename St, bool NB, bool BAND>
+__global__ void __launch_bounds__(XEDGE * EDGE_ROWS) k_step_edges(StepParams P) {
+    const int y = blockIdx.y * EDGE_ROWS + threadIdx.y, z = blockIdx.z;
+    if (y >= P.g.ny) return;
+    if (blockIdx.x == 0) edge_node<St, NB, BAND, 0>(P, y, z);
+    else edge_node<St, NB, BAND, 1>(P, y, z);
+}
+
+template <typename St, bool NB, bool BAND>
+__global__ void __launch_bounds__(XEDGE * EDGE_ROWS) k_step_rows(StepParams P) {
+    const int y = blockIdx.y * EDGE_ROWS + threadIdx.y, z = blockIdx.z;
+    if (y >= P.g.ny) return;
+    edge_node<St, NB, BAND, 2>(P, y, z);
 }
 
 // ---- initialisation: f = f_eq(rho, u), stored as the post-collision state of t = 0 ------
@@ -312,12 +328,11 @@ static cudaError_t launch_step_tt(const StepParams &P, int part, cudaStream_t st
     if (part == STEP_BOUNDARY) {
         const dim3 block(XEDGE, EDGE_ROWS);
         if (has_interior(g)) {
-            const dim3 grid(1, blocks_for(g.ny, EDGE_ROWS), g.nz);
-            k_step_edges<St, NB, BAND, 0><<<grid, block, 0, st>>>(P);
-            k_step_edges<St, NB, BAND, 1><<<grid, block, 0, st>>>(P);
+            const dim3 grid(2, blocks_for(g.ny, EDGE_ROWS), g.nz);
+            k_step_edges<St, NB, BAND><<<grid, block, 0, st>>>(P);
         } else {
             const dim3 grid(blocks_for(g.nx, XEDGE), blocks_for(g.ny, EDGE_ROWS), g.nz);
-            k_step_edges<St, NB, BAND, 2><<<grid, block, 0, st>>>(P);
+            k_step_rows<St, NB, BAND><<<grid, block, 0, st>>>(P);
         }
     } else if (has_interior(g)) {
         const dim3 grid(blocks_for(g.nx - 2 * XEDGE, STEP_BX), g.ny, g.nz);
