@@ -220,3 +220,44 @@ def collide_factorised(f: torch.Tensor, F: torch.Tensor, rates: dict) -> torch.T
     out[0, 2, 0] = rho * m[2] + (tr - 2.0 * d1 + d2) / 3.0
     out[0, 0, 2] = rho * m[2] + (tr + d1 - 2.0 * d2) / 3.0
     return from_central_moments(out, u).reshape(27, *shape)
+
+
+# ---- comparison collision models (Sec. 6.1: D3Q27 BGK and raw-moment MRT) -------------
+# The paper compares ACM-MRT with the D3Q27 BGK and RM-MRT models under the same
+# streaming, forcing and boundary treatment.  Readings: BGK relaxes every population with
+# the shear rate towards the product equilibrium and adds the force term G = M(u)^-1 R^F
+# with the factor (1 - omega/2) (Guo); RM-MRT is Eq. 5 with the moment matrix taken at u = 0
+# (raw moments c_x^p c_y^q c_z^r, same rows and rate groups as above), equilibrium M f_eq and
+# force moments M G.
+
+def force_distribution(u: torch.Tensor, F: torch.Tensor) -> torch.Tensor:
+    """Discrete force term G = M(u)^-1 R^F of Eq. 4 at every node: u, F (3, N) -> (27, N)."""
+    G = torch.linalg.solve(moment_matrix(u), force_moments(F).unsqueeze(-1)).squeeze(-1)
+    return G.T
+
+
+def collide_bgk(f: torch.Tensor, F: torch.Tensor, omega: float) -> torch.Tensor:
+    """Single-relaxation-time (BGK) collision with Guo forcing:
+    f_post = f - omega (f - f_eq(rho, u)) + (1 - omega/2) G, u = (j + F/2)/rho."""
+    shape = f.shape[1:]
+    f2 = f.reshape(27, -1)
+    F2 = F.reshape(3, -1)
+    rho, j = density_momentum(f2)
+    u = guo_velocity(rho, j, F2)
+    out = f2 - omega * (f2 - equilibrium(rho, u)) + (1.0 - 0.5 * omega) * force_distribution(u, F2)
+    return out.reshape(27, *shape)
+
+
+def collide_raw(f: torch.Tensor, F: torch.Tensor, rates: dict) -> torch.Tensor:
+    """Raw-moment MRT: Eq. 5 with M = M(0) (u-independent raw moments)."""
+    shape = f.shape[1:]
+    f2 = f.reshape(27, -1)
+    F2 = F.reshape(3, -1)
+    rho, j = density_momentum(f2)
+    u = guo_velocity(rho, j, F2)
+    M0 = moment_matrix(torch.zeros(3, 1, dtype=DTYPE))[0]
+    D = rate_vector(rates)
+    m_neq = M0 @ (f2 - equilibrium(rho, u))
+    rf = M0 @ force_distribution(u, F2)
+    rhs = -D[:, None] * m_neq + (1.0 - 0.5 * D)[:, None] * rf
+    return (f2 + torch.linalg.solve(M0, rhs)).reshape(27, *shape)

@@ -46,7 +46,7 @@ class Problem:
     seed: int = 0
     omega_bulk: float = 1.0
     omega_hi: tuple = (1.0, 1.0, 1.0, 1.0)
-    collision: str = "factorised"          # or "matrix"
+    collision: str = "factorised"          # or "matrix" (same operator), "bgk", "raw" (comparison models)
     rates: dict = field(init=False)
 
     def __post_init__(self):
@@ -83,6 +83,10 @@ def inlet_velocity(p: Problem, t: int, coef: torch.Tensor | None) -> torch.Tenso
 def collide(p: Problem, fstar, F):
     if p.collision == "matrix":
         return col.collide_matrix(fstar, F, p.rates)
+    if p.collision == "bgk":
+        return col.collide_bgk(fstar, F, p.rates["shear"])
+    if p.collision == "raw":
+        return col.collide_raw(fstar, F, p.rates)
     return col.collide_factorised(fstar, F, p.rates)
 
 
