@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--no-fp16", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-models", action="store_true", help="skip the BGK / raw-MRT comparison runs")
     ap.add_argument("--adjoint-only", action="store_true", help="time only the adjoint workload")
     return ap.parse_args()
 
@@ -248,11 +249,29 @@ def main():
     u0[0] = d["u_in"]
     peak, peak_kind = measured_peak()
 
-    def make(storage):
-        s = Solver(nx, ny, nz, d["nu"], storage=storage, faces=d["faces"], u_in=d["u_in"], noise=d["noise"], seed=2101)
+    def make(storage, collision="acm"):
+        s = Solver(nx, ny, nz, d["nu"], storage=storage, faces=d["faces"], u_in=d["u_in"], noise=d["noise"], seed=2101,
+                   collision=collision)
         s.set_state(rho0, u0)
         s.set_solids(X, A)
         return s
+
+    def side_run(storage, collision, steps):
+        """Whole-step MLUPS and the main step kernel's roofline for one storage / collision."""
+        sx = make(storage, collision)
+        sx.step(args.warmup)
+        torch.cuda.synchronize()
+        msx, ktx = timed_steps(sx, steps, torch)
+        kx = ktx["step"][0] / max(ktx["step"][1], 1)
+        achx = BYTES_PER_CELL[storage] * n_int / (kx * 1e-3) / 1e9
+        massx, _, _ = sx.reductions()
+        sx.close()
+        torch.cuda.empty_cache()
+        if not math.isfinite(massx):
+            raise RuntimeError(f"non-finite state in the {storage}/{collision} run")
+        return {"mlups": world * N / (msx / steps * 1e-3) / 1e6, "ms_per_step": msx / steps, "step_kernel_ms": kx,
+                "roofline": {"bound": "hbm", "achieved": achx, "peak": peak, "unit": "GB/s", "frac": achx / peak,
+                             "bytes_per_cell": BYTES_PER_CELL[storage]}}
 
     # ---- FP32, device-resident: the headline value -----------------------------------
     s = make("f32")
@@ -309,20 +328,18 @@ def main():
     torch.cuda.empty_cache()
 
     # ---- FP16-stored deviations (same workload) ---------------------------------------
-    fp16 = None
-    if not args.no_fp16:
-        s16 = make("f16")
-        s16.step(args.warmup)
-        torch.cuda.synchronize()
-        n16 = max(10, args.steps // 2)
-        ms16, kt16 = timed_steps(s16, n16, torch)
-        k16 = kt16["step"][0] / max(kt16["step"][1], 1)
-        ach16 = BYTES_PER_CELL["f16"] * n_int / (k16 * 1e-3) / 1e9
-        fp16 = {"mlups": world * N / (ms16 / n16 * 1e-3) / 1e6, "ms_per_step": ms16 / n16,
-                "step_kernel_ms": k16, "roofline": {"bound": "hbm", "achieved": ach16, "peak": peak, "unit": "GB/s",
-                                                    "frac": ach16 / peak, "bytes_per_cell": 108}}
-        s16.close()
-        del s16
+    n_side = max(10, args.steps // 2)
+    fp16 = None if args.no_fp16 else side_run("f16", "acm", n_side)
+
+    # ---- comparison collisions of Sec. 6.1 (same workload, same step structure) -------------
+    models = None
+    if not args.no_models:
+        models = {"acm": {"f32": {"mlups": mlups, "ms_per_step": ms_step, "step_kernel_ms": k_ms,
+                                  "roofline": {"achieved": achieved, "frac": achieved / peak}}}}
+        if fp16 is not None:
+            models["acm"]["f16"] = fp16
+        for coll in ("bgk", "raw"):
+            models[coll] = {st: side_run(st, coll, n_side) for st in ("f32",) + (() if args.no_fp16 else ("f16",))}
 
     adjoint = None
     if not args.no_adjoint:
@@ -354,6 +371,7 @@ def main():
             "clocks": clk.summary(),
             "e2e": e2e,
             "fp16": fp16,
+            "collision_models": models,
             "adjoint": adjoint,
             "cpu_baseline": cpu,
             "checks": {"mass": mass, "drag": list(map(float, drag))},

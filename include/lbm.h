@@ -58,10 +58,24 @@ typedef struct lbm_config {
     double omega_bulk;           /* rate of the trace of the second-order central moments     */
     double omega_hi[4];          /* rates of the third-, fourth-, fifth-, sixth-order moments */
     void *cuda_stream;           /* cudaStream_t the context launches on (NULL = legacy)       */
+    int collision;               /* LBM_COLL_*: the collision of Eq. 4                         */
 } lbm_config;
 
+/* Collision models (lbm_config.collision).  LBM_COLL_ACM is the method: central-moment MRT
+ * with the rates of Eq. 5 (Sec. 2.1).  The other two are the comparison models of the
+ * results in Sec. 6.1, under the same streaming, faces, Guo forcing and immersed boundary:
+ * LBM_COLL_BGK relaxes every non-conserved moment at the shear rate (single-relaxation BGK
+ * with the D3Q27 product equilibrium), LBM_COLL_RAW is Eq. 5 with the velocity-independent
+ * raw moments c_x^p c_y^q c_z^r in place of the central ones and the same rate groups
+ * (omega_bulk and omega_hi apply to it as to ACM; BGK ignores them).  Only LBM_COLL_ACM has
+ * an adjoint: lbm_adjoint on a context of another model returns LBM_EINVAL. */
+#define LBM_COLL_ACM 0
+#define LBM_COLL_BGK 1
+#define LBM_COLL_RAW 2
+
 /* Fill *cfg with defaults: FP32 storage, all faces periodic, rho0 = 1, no inlet, no noise,
- * seed 2101, zero inflow coefficients, omega_bulk = omega_hi[*] = 1, default stream. */
+ * seed 2101, zero inflow coefficients, omega_bulk = omega_hi[*] = 1, default stream,
+ * collision LBM_COLL_ACM. */
 void lbm_config_default(lbm_config *cfg);
 
 /* Create a solver on an nx * ny * nz D3Q27 lattice (Eq. 1) with kinematic viscosity nu

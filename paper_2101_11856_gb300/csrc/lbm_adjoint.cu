@@ -571,6 +571,7 @@ extern "C" int lbm_adjoint(lbm_ctx *h, int n, int K, const lbm_loss *loss, doubl
     if (!h) return fail(nullptr, LBM_EINVAL, "null context");
     if (!h->has_state) return fail(h, LBM_ESTATE, "lbm_set_state (or lbm_load) has not been called");
     if (n < 1 || !loss) return fail(h, LBM_EINVAL, "n must be >= 1 and loss given");
+    if (h->cfg.collision != LBM_COLL_ACM) return fail(h, LBM_EINVAL, "the adjoint exists for the ACM-MRT collision only");
     if (loss->ke_x0 < 0 || loss->ke_x1 > h->nx || loss->ke_x0 > loss->ke_x1) return fail(h, LBM_EINVAL, "bad slab");
     K = std::max(1, std::min(K, n));
     const long long N = h->N, S = h->S, nb = h->nband;

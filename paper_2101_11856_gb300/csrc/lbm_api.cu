@@ -33,10 +33,10 @@ int step_with(lbm_ctx *h, const StepParams &P) {
         { Timed tm(h, LBM_KERNEL_INTERP); CK(launch_ib_interp(h->S, h->nband, h->X, h->area, h->ub, h->corner_band, h->band_rho, h->band_u, h->g, h->stream)); }
         { Timed tm(h, LBM_KERNEL_SPREAD); CK(launch_ib_spread(h->S, h->nband, h->X, h->g, h->base_nbr, h->cstart, h->ccount, h->bandF, h->stream)); }
     }
-    { Timed tm(h, LBM_KERNEL_BOUNDARY); CK(launch_step(h->storage, P, band, STEP_BOUNDARY, h->stream)); }
+    { Timed tm(h, LBM_KERNEL_BOUNDARY); CK(launch_step(h->storage, P, band, STEP_BOUNDARY, h->cfg.collision, h->stream)); }
     if (has_interior(P.g)) {
         Timed tm(h, LBM_KERNEL_STEP);
-        CK(launch_step(h->storage, P, band, STEP_INTERIOR, h->stream));
+        CK(launch_step(h->storage, P, band, STEP_INTERIOR, h->cfg.collision, h->stream));
     }
     return LBM_OK;
 }
@@ -86,6 +86,7 @@ void lbm_config_default(lbm_config *cfg) {
     cfg->omega_bulk = 1.0;
     for (int k = 0; k < 4; ++k) cfg->omega_hi[k] = 1.0;
     cfg->cuda_stream = nullptr;
+    cfg->collision = LBM_COLL_ACM;
 }
 
 int lbm_create(lbm_ctx **out, int nx, int ny, int nz, double nu, const double forcing[3], const lbm_config *cfg) {
@@ -101,6 +102,7 @@ int lbm_create(lbm_ctx **out, int nx, int ny, int nz, double nu, const double fo
     if (cfg) c = *cfg;
     else lbm_config_default(&c);
     if (c.storage < 0 || c.storage > 2) return fail(nullptr, LBM_EINVAL, "unknown storage type");
+    if (c.collision < LBM_COLL_ACM || c.collision > LBM_COLL_RAW) return fail(nullptr, LBM_EINVAL, "unknown collision model");
     for (int k = 0; k < 6; ++k)
         if (c.face_type[k] < 0 || c.face_type[k] > 3) return fail(nullptr, LBM_EINVAL, "unknown face type");
     for (int a = 0; a < 3; ++a)

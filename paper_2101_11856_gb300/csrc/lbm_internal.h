@@ -8,13 +8,17 @@
 namespace lbm {
 
 enum { STEP_BOUNDARY = 0, STEP_INTERIOR = 1 };
+// collision models, numbered as LBM_COLL_* of the C ABI
+enum CollisionModel { COLL_ACM = 0, COLL_BGK = 1, COLL_RAW = 2 };
 // The x range is split into two edge strips of XEDGE nodes per row, run by the general face
 // kernel in whole coalesced warps (STEP_BOUNDARY), and the nodes XEDGE <= x < nx - XEDGE,
 // run by the main kernel (STEP_INTERIOR).  Rows shorter than 2 XEDGE + 1 run entirely in the
 // face kernel.
 constexpr int XEDGE = 32;
 constexpr int STEP_BX = 64;   // threads per block of the main step kernels (along x)
-cudaError_t launch_step(int storage, const StepParams &P, bool band, int part, cudaStream_t st);
+cudaError_t launch_step(int storage, const StepParams &P, bool band, int part, int collision, cudaStream_t st);
+template <int COLL>
+cudaError_t launch_step_coll(int storage, const StepParams &P, bool band, int part, cudaStream_t st);
 long long boundary_count(const Geometry &g);
 __host__ __device__ inline bool has_interior(const Geometry &g) { return g.nx >= 2 * XEDGE + 1; }
 __host__ __device__ inline int edge_per_row(const Geometry &g) { return has_interior(g) ? 2 * XEDGE : g.nx; }

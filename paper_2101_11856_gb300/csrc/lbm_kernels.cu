@@ -8,65 +8,6 @@
 namespace lbm {
 
 
-// ---- the fused step ---------------------------------------------------------------------
-// One thread per cell: pull the 27 streamed populations, add the body force and the band's
-// immersed-boundary force, collide in registers, store in place.  k_step_main updates the
-// nodes XEDGE <= x < nx - XEDGE: one block row per (y, z), so a block's y/z face status is
-// uniform (interior rows use constant offsets; face rows of odd steps use wrapped or bounced
-// rows; even steps address only the node's own slots).  k_step_edges updates the two edge
-// strips of each row with the general face rules (inlet, outlet, x wrap) in whole warps.
-// Every node is updated by exactly one of the two, and the two touch disjoint slots.
-template <typename St, bool NB, bool BAND>
-__global__ void __launch_bounds__(STEP_BX) k_step_main(StepParams P) {
-    const int x = blockIdx.x * STEP_BX + threadIdx.x + XEDGE;
-    if (x >= P.g.nx - XEDGE) return;
-    const int y = blockIdx.y, z = blockIdx.z;
-    const int cell = x + P.g.nx * (y + P.g.ny * z);
-    const bool inner = y >= 1 && y <= P.g.ny - 2 && z >= 1 && z <= P.g.nz - 2;   // uniform per block
-    float h[27];
-    if (!NB || inner) load_interior<St, NB>(P, cell, h);
-    else load_yzface<St>(P, y, z, cell, h);
-    float Fx, Fy, Fz;
-    band_force<BAND>(P, cell, Fx, Fy, Fz);
-    float rho, ux, uy, uz;
-    collide(h, Fx, Fy, Fz, P, rho, ux, uy, uz);
-    if (!NB || inner) store_interior<St, NB>(P, cell, h);
-    else store_yzface<St>(P, y, z, cell, h);
-}
-
-// one warp per edge strip of one row, EDGE_ROWS rows (y) per block: blockIdx.y * EDGE_ROWS +
-// threadIdx.y = y, blockIdx.z = z.  With a main range, blockIdx.x picks the left (0) or right
-// (1) strip (one launch for both: measured faster than a launch per side); short rows run the
-// SIDE = 2 kernel over consecutive warps.
-template <typename St, bool NB, bool BAND, int SIDE>
-__device__ __forceinline__ void edge_node(const StepParams &P, int y, int z) {
-    const int x = edge_x<SIDE>(P.g);
-    if (x >= P.g.nx) return;
-    const int cell = x + P.g.nx * (y + P.g.ny * z);
-    float h[27];
-    load_edge<St, NB, SIDE>(P, x, y, z, cell, h);
-    float Fx, Fy, Fz;
-    band_force<BAND>(P, cell, Fx, Fy, Fz);
-    float rho, ux, uy, uz;
-    collide(h, Fx, Fy, Fz, P, rho, ux, uy, uz);
-    store_edge<St, NB, SIDE>(P, x, y, z, cell, h);
-}
-
-template <typename St, bool NB, bool BAND>
-__global__ void __launch_bounds__(XEDGE * EDGE_ROWS) k_step_edges(StepParams P) {
-    const int y = blockIdx.y * EDGE_ROWS + threadIdx.y, z = blockIdx.z;
-    if (y >= P.g.ny) return;
-    if (blockIdx.x == 0) edge_node<St, NB, BAND, 0>(P, y, z);
-    else edge_node<St, NB, BAND, 1>(P, y, z);
-}
-
-template <typename St, bool NB, bool BAND>
-__global__ void __launch_bounds__(XEDGE * EDGE_ROWS) k_step_rows(StepParams P) {
-    const int y = blockIdx.y * EDGE_ROWS + threadIdx.y, z = blockIdx.z;
-    if (y >= P.g.ny) return;
-    edge_node<St, NB, BAND, 2>(P, y, z);
-}
-
 // ---- initialisation: f = f_eq(rho, u), stored as the post-collision state of t = 0 ------
 
 __device__ __forceinline__ float phi1(int c, float u) {
@@ -322,32 +263,6 @@ static inline unsigned blocks_for(long long n, int threads) { return (unsigned)(
 
 long long boundary_count(const Geometry &g) { return (long long)edge_per_row(g) * g.ny * g.nz; }
 
-template <typename St, bool NB, bool BAND>
-static cudaError_t launch_step_tt(const StepParams &P, int part, cudaStream_t st) {
-    const Geometry &g = P.g;
-    if (part == STEP_BOUNDARY) {
-        const dim3 block(XEDGE, EDGE_ROWS);
-        if (has_interior(g)) {
-            const dim3 grid(2, blocks_for(g.ny, EDGE_ROWS), g.nz);
-            k_step_edges<St, NB, BAND><<<grid, block, 0, st>>>(P);
-        } else {
-            const dim3 grid(blocks_for(g.nx, XEDGE), blocks_for(g.ny, EDGE_ROWS), g.nz);
-            k_step_rows<St, NB, BAND><<<grid, block, 0, st>>>(P);
-        }
-    } else if (has_interior(g)) {
-        const dim3 grid(blocks_for(g.nx - 2 * XEDGE, STEP_BX), g.ny, g.nz);
-        k_step_main<St, NB, BAND><<<grid, STEP_BX, 0, st>>>(P);
-    }
-    return cudaGetLastError();
-}
-
-template <typename St>
-static cudaError_t launch_step_t(const StepParams &P, bool band, int part, cudaStream_t st) {
-    const bool nb = (P.t & 1) != 0;
-    if (nb) return band ? launch_step_tt<St, true, true>(P, part, st) : launch_step_tt<St, true, false>(P, part, st);
-    return band ? launch_step_tt<St, false, true>(P, part, st) : launch_step_tt<St, false, false>(P, part, st);
-}
-
 template <typename F>
 static cudaError_t dispatch_storage(int storage, F &&fn) {
     switch (storage) {
@@ -357,8 +272,12 @@ static cudaError_t dispatch_storage(int storage, F &&fn) {
     }
 }
 
-cudaError_t launch_step(int storage, const StepParams &P, bool band, int part, cudaStream_t st) {
-    return dispatch_storage(storage, [&](auto tag) { return launch_step_t<decltype(tag)>(P, band, part, st); });
+cudaError_t launch_step(int storage, const StepParams &P, bool band, int part, int collision, cudaStream_t st) {
+    switch (collision) {
+        case COLL_BGK: return launch_step_coll<COLL_BGK>(storage, P, band, part, st);
+        case COLL_RAW: return launch_step_coll<COLL_RAW>(storage, P, band, part, st);
+        default: return launch_step_coll<COLL_ACM>(storage, P, band, part, st);
+    }
 }
 
 cudaError_t launch_init(int storage, const StepParams &P, const float *rho, const float *u, cudaStream_t st) {

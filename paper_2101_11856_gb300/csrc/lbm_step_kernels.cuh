@@ -1,0 +1,109 @@
+// The fused step kernels (main range and edge strips) and their launchers, templated on the
+// storage type, the AA parity, the immersed-boundary force and the collision model.  Each
+// collision model is instantiated in its own translation unit (lbm_step_acm.cu,
+// lbm_step_bgk.cu, lbm_step_raw.cu) so that they compile in parallel.
+#pragma once
+
+#include "lbm_models.cuh"
+#include "lbm_step.cuh"
+
+namespace lbm {
+
+inline unsigned step_blocks(long long n, int threads) { return (unsigned)((n + threads - 1) / threads); }
+
+// ---- the fused step ---------------------------------------------------------------------
+// One thread per cell: pull the 27 streamed populations, add the body force and the band's
+// immersed-boundary force, collide in registers, store in place.  k_step_main updates the
+// nodes XEDGE <= x < nx - XEDGE: one block row per (y, z), so a block's y/z face status is
+// uniform (interior rows use constant offsets; face rows of odd steps use wrapped or bounced
+// rows; even steps address only the node's own slots).  k_step_edges updates the two edge
+// strips of each row with the general face rules (inlet, outlet, x wrap) in whole warps.
+// Every node is updated by exactly one of the two, and the two touch disjoint slots.
+template <typename St, bool NB, bool BAND, int COLL>
+__global__ void __launch_bounds__(STEP_BX) k_step_main(StepParams P) {
+    const int x = blockIdx.x * STEP_BX + threadIdx.x + XEDGE;
+    if (x >= P.g.nx - XEDGE) return;
+    const int y = blockIdx.y, z = blockIdx.z;
+    const int cell = x + P.g.nx * (y + P.g.ny * z);
+    const bool inner = y >= 1 && y <= P.g.ny - 2 && z >= 1 && z <= P.g.nz - 2;   // uniform per block
+    float h[27];
+    if (!NB || inner) load_interior<St, NB>(P, cell, h);
+    else load_yzface<St>(P, y, z, cell, h);
+    float Fx, Fy, Fz;
+    band_force<BAND>(P, cell, Fx, Fy, Fz);
+    float rho, ux, uy, uz;
+    collide_model<COLL>(h, Fx, Fy, Fz, P, rho, ux, uy, uz);
+    if (!NB || inner) store_interior<St, NB>(P, cell, h);
+    else store_yzface<St>(P, y, z, cell, h);
+}
+
+// one warp per edge strip of one row, EDGE_ROWS rows (y) per block: blockIdx.y * EDGE_ROWS +
+// threadIdx.y = y, blockIdx.z = z.  With a main range, blockIdx.x picks the left (0) or right
+// (1) strip (one launch for both: measured faster than a launch per side); short rows run the
+// SIDE = 2 kernel over consecutive warps.
+template <typename St, bool NB, bool BAND, int SIDE, int COLL>
+__device__ __forceinline__ void edge_node(const StepParams &P, int y, int z) {
+    const int x = edge_x<SIDE>(P.g);
+    if (x >= P.g.nx) return;
+    const int cell = x + P.g.nx * (y + P.g.ny * z);
+    float h[27];
+    load_edge<St, NB, SIDE>(P, x, y, z, cell, h);
+    float Fx, Fy, Fz;
+    band_force<BAND>(P, cell, Fx, Fy, Fz);
+    float rho, ux, uy, uz;
+    collide_model<COLL>(h, Fx, Fy, Fz, P, rho, ux, uy, uz);
+    store_edge<St, NB, SIDE>(P, x, y, z, cell, h);
+}
+
+template <typename St, bool NB, bool BAND, int COLL>
+__global__ void __launch_bounds__(XEDGE * EDGE_ROWS) k_step_edges(StepParams P) {
+    const int y = blockIdx.y * EDGE_ROWS + threadIdx.y, z = blockIdx.z;
+    if (y >= P.g.ny) return;
+    if (blockIdx.x == 0) edge_node<St, NB, BAND, 0, COLL>(P, y, z);
+    else edge_node<St, NB, BAND, 1, COLL>(P, y, z);
+}
+
+template <typename St, bool NB, bool BAND, int COLL>
+__global__ void __launch_bounds__(XEDGE * EDGE_ROWS) k_step_rows(StepParams P) {
+    const int y = blockIdx.y * EDGE_ROWS + threadIdx.y, z = blockIdx.z;
+    if (y >= P.g.ny) return;
+    edge_node<St, NB, BAND, 2, COLL>(P, y, z);
+}
+
+template <typename St, bool NB, bool BAND, int COLL>
+cudaError_t launch_step_tt(const StepParams &P, int part, cudaStream_t st) {
+    const Geometry &g = P.g;
+    if (part == STEP_BOUNDARY) {
+        const dim3 block(XEDGE, EDGE_ROWS);
+        if (has_interior(g)) {
+            const dim3 grid(2, step_blocks(g.ny, EDGE_ROWS), g.nz);
+            k_step_edges<St, NB, BAND, COLL><<<grid, block, 0, st>>>(P);
+        } else {
+            const dim3 grid(step_blocks(g.nx, XEDGE), step_blocks(g.ny, EDGE_ROWS), g.nz);
+            k_step_rows<St, NB, BAND, COLL><<<grid, block, 0, st>>>(P);
+        }
+    } else if (has_interior(g)) {
+        const dim3 grid(step_blocks(g.nx - 2 * XEDGE, STEP_BX), g.ny, g.nz);
+        k_step_main<St, NB, BAND, COLL><<<grid, STEP_BX, 0, st>>>(P);
+    }
+    return cudaGetLastError();
+}
+
+template <typename St, int COLL>
+cudaError_t launch_step_t(const StepParams &P, bool band, int part, cudaStream_t st) {
+    const bool nb = (P.t & 1) != 0;
+    if (nb) return band ? launch_step_tt<St, true, true, COLL>(P, part, st) : launch_step_tt<St, true, false, COLL>(P, part, st);
+    return band ? launch_step_tt<St, false, true, COLL>(P, part, st) : launch_step_tt<St, false, false, COLL>(P, part, st);
+}
+
+// one part of one step for the collision model COLL; instantiated in lbm_step_<model>.cu
+template <int COLL>
+cudaError_t launch_step_coll(int storage, const StepParams &P, bool band, int part, cudaStream_t st) {
+    switch (storage) {
+        case 0: return launch_step_t<float, COLL>(P, band, part, st);
+        case 1: return launch_step_t<__half, COLL>(P, band, part, st);
+        default: return launch_step_t<__nv_bfloat16, COLL>(P, band, part, st);
+    }
+}
+
+}  // namespace lbm

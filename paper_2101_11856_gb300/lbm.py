@@ -19,6 +19,7 @@ _lib = None
 LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ETIMEOUT, LBM_ESTATE = 0, -1, -2, -3, -4, -5, -6
 STORAGE = {"f32": 0, "f16": 1, "bf16": 2}
 FACE = {"periodic": 0, "noslip": 1, "inlet": 2, "outlet": 3}
+COLLISION = {"acm": 0, "bgk": 1, "raw": 2}
 KERNEL_KINDS = ("step", "band", "interp", "spread", "boundary", "other")
 
 
@@ -31,7 +32,8 @@ class LBMError(RuntimeError):
 class lbm_config(C.Structure):
     _fields_ = [("storage", C.c_int), ("face_type", C.c_int * 6), ("rho0", C.c_double), ("u_in", C.c_double),
                 ("inlet_noise", C.c_double), ("seed", C.c_ulonglong), ("inflow_coef", C.c_double * 16),
-                ("omega_bulk", C.c_double), ("omega_hi", C.c_double * 4), ("cuda_stream", C.c_void_p)]
+                ("omega_bulk", C.c_double), ("omega_hi", C.c_double * 4), ("cuda_stream", C.c_void_p),
+                ("collision", C.c_int)]
 
 
 class lbm_loss(C.Structure):
@@ -237,9 +239,10 @@ class Solver:
 
     def __init__(self, nx, ny, nz, nu, forcing=(0.0, 0.0, 0.0), storage="f32", faces=("periodic",) * 6,
                  rho0=1.0, u_in=0.0, noise=0.0, seed=2101, inflow_coef=None, omega_bulk=1.0,
-                 omega_hi=(1.0, 1.0, 1.0, 1.0), stream=None):
+                 omega_hi=(1.0, 1.0, 1.0, 1.0), stream=None, collision="acm"):
         cfg = lbm_config_default()
         cfg.storage = STORAGE[storage]
+        cfg.collision = COLLISION[collision]
         for k, t in enumerate(faces):
             cfg.face_type[k] = FACE[t]
         cfg.rho0, cfg.u_in, cfg.inlet_noise, cfg.seed = rho0, u_in, noise, seed

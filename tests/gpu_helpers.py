@@ -27,10 +27,15 @@ def gpu_order():
 
 def run_pair(nx, ny, nz, nu, steps, rho, u, faces=("periodic",) * 6, forcing=(0.0, 0.0, 0.0), samples=None,
              area=None, u_b=None, storage="f32", u_in=0.0, noise=0.0, seed=2101, inflow_coef=None,
-             omega_bulk=1.0, omega_hi=(1.0, 1.0, 1.0, 1.0), oracle_collision="factorised"):
-    """Run both sides; return (gpu solver, oracle solver) after `steps` steps."""
+             omega_bulk=1.0, omega_hi=(1.0, 1.0, 1.0, 1.0), oracle_collision=None, collision="acm"):
+    """Run both sides; return (gpu solver, oracle solver) after `steps` steps.  ``collision`` is
+    the library's model ("acm", "bgk", "raw"); the oracle runs the same model unless
+    ``oracle_collision`` names one of its forms explicitly."""
+    if oracle_collision is None:
+        oracle_collision = {"acm": "factorised", "bgk": "bgk", "raw": "raw"}[collision]
     g = lib_solver(nx=nx, ny=ny, nz=nz, nu=nu, forcing=forcing, storage=storage, faces=faces, u_in=u_in,
-                   noise=noise, seed=seed, inflow_coef=inflow_coef, omega_bulk=omega_bulk, omega_hi=omega_hi)
+                   noise=noise, seed=seed, inflow_coef=inflow_coef, omega_bulk=omega_bulk, omega_hi=omega_hi,
+                   collision=collision)
     g.set_state(rho, u)
     o = OracleSolver(Problem(nx, ny, nz, nu=nu, forcing=tuple(forcing), faces=tuple(faces), u_in=u_in, noise=noise,
                              seed=seed, omega_bulk=omega_bulk, omega_hi=tuple(omega_hi), collision=oracle_collision),

@@ -45,7 +45,7 @@ def test_binding_config_layout_matches_header(lib):
     lib.lbm_config_default(ctypes.byref(cfg))
     assert cfg.storage == 0 and list(cfg.face_type) == [0] * 6
     assert cfg.rho0 == 1.0 and cfg.seed == 2101 and cfg.omega_bulk == 1.0 and list(cfg.omega_hi) == [1.0] * 4
-    assert cfg.cuda_stream is None
+    assert cfg.cuda_stream is None and cfg.collision == lbm.COLLISION["acm"] == 0
 
 
 def test_velocity_table_is_d3q27(lib):
@@ -72,3 +72,9 @@ def test_create_rejects_bad_arguments_without_touching_the_gpu(lib):
     bad.face_type[2], bad.face_type[3] = lbm.FACE["inlet"], lbm.FACE["noslip"]   # inlet on -y
     with pytest.raises(lbm.LBMError):
         lbm.lbm_create(4, 4, 4, 0.1, cfg=bad)
+    for coll in (-1, 3):
+        bad = lbm.lbm_config_default()
+        bad.collision = coll
+        with pytest.raises(lbm.LBMError) as e:
+            lbm.lbm_create(4, 4, 4, 0.1, cfg=bad)
+        assert e.value.code == lbm.LBM_EINVAL
