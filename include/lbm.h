@@ -182,16 +182,64 @@ int lbm_load(lbm_ctx *h, const void *buf, size_t bytes);
 
 /* Per-kernel device timing (CUDA events on the context's stream around every launch).
  * lbm_profile(h, 1) enables and clears the counters; lbm_profile(h, 0) disables. */
-#define LBM_KERNEL_STEP        0   /* fused stream + collide, 1 <= x <= nx-2  */
-#define LBM_KERNEL_BAND        1   /* immersed-boundary band moments          */
-#define LBM_KERNEL_INTERP      2   /* interpolation + penalty (Eqs. 6-7)       */
-#define LBM_KERNEL_SPREAD      3   /* spreading (Eq. 8)                        */
-#define LBM_KERNEL_BOUNDARY    4   /* fused stream + collide, x = 0, nx-1     */
-#define LBM_KERNEL_OTHER       5   /* init, macroscopic, reductions, copies   */
-#define LBM_NUM_KERNEL_KINDS   6
+#define LBM_KERNEL_STEP        0   /* fused stream + collide, 32 <= x < nx-32              */
+#define LBM_KERNEL_BAND        1   /* immersed-boundary band moments                      */
+#define LBM_KERNEL_INTERP      2   /* interpolation + penalty (Eqs. 6-7)                   */
+#define LBM_KERNEL_SPREAD      3   /* spreading (Eq. 8)                                    */
+#define LBM_KERNEL_BOUNDARY    4   /* fused stream + collide, the 32-node strips at both
+                                      row ends (whole rows when nx < 65)                   */
+#define LBM_KERNEL_OTHER       5   /* init, macroscopic, reductions, copies, density      */
+#define LBM_KERNEL_TRACER      6   /* smoke tracer advection                              */
+#define LBM_NUM_KERNEL_KINDS   7
 int lbm_profile(lbm_ctx *h, int enable);
 /* ms[k], launches[k] for k < LBM_NUM_KERNEL_KINDS; waits for the stream. */
 int lbm_kernel_times(lbm_ctx *h, double ms[LBM_NUM_KERNEL_KINDS], long long launches[LBM_NUM_KERNEL_KINDS]);
+
+/* ---- Smoke tracers (Sec. 6: smoke particles traced on the GPU and their density projected
+ * onto a uniform volume grid for rendering; the paper prints no formulas, so the readings
+ * are stated here).  Positions are in lattice units, node (i, j, k) at (i, j, k).
+ *
+ * While tracers exist, every lbm_step also writes the velocity field of the step (FP32,
+ * 12 bytes per cell) and then moves each tracer by the explicit midpoint rule with dt = 1:
+ * x_mid = x + u(x)/2, x' = x + u(x_mid), u the trilinear interpolation of the step's
+ * Guo-shifted velocity (periodic axes wrap; along a non-periodic axis of n nodes the base
+ * node is min(floor(x), n-2)).  Periodic coordinates are wrapped into [0, n) after each
+ * stage.  A tracer whose midpoint or end point leaves [0, n-1] along a non-periodic axis is
+ * re-injected at lo + (hi - lo) U, U_a = (SplitMix64(seed, ((t-1) P + i) 3 + a) >> 40) 2^-24
+ * (t the 1-based step, P the tracer count, i the tracer's index): smoke injected
+ * continuously at a fixed tracer count. */
+typedef struct lbm_emitter {
+    double lo[3], hi[3];         /* re-injection box [lo, hi) in lattice units               */
+    unsigned long long seed;     /* SplitMix64 seed of the re-injection positions            */
+} lbm_emitter;
+
+/* Set (count > 0) or remove (count = 0) the tracers.  X: host or device pointer to count*3
+ * floats (x, y, z per tracer), each inside the domain ([0, n) along periodic axes, [0, n-1]
+ * along the others); non-periodic axes need n >= 2.  em: the re-injection box, inside the
+ * same domain (lo <= hi); required unless every axis is periodic.  Allocates 12 (count + N)
+ * bytes on the device; count < 2^28.  Tracers are not part of lbm_save checkpoints.
+ * Errors: LBM_EINVAL (bad position, box or count; X or em NULL), LBM_ENOMEM. */
+int lbm_set_tracers(lbm_ctx *h, const float *X, long long count, const lbm_emitter *em);
+
+/* Number of tracers. */
+long long lbm_tracer_count(const lbm_ctx *h);
+
+/* Copy the tracer positions to X (host or device, count*3 floats as in lbm_set_tracers). */
+int lbm_tracers(lbm_ctx *h, float *X);
+
+/* Voxels of the density grid of spacing s (integer >= 1, voxel j at coordinate j s): n/s
+ * along a periodic axis (n divisible by s, else LBM_EINVAL), ceil((n-1)/s) + 1 along a
+ * non-periodic one.  dims = {gx, gy, gz}. */
+int lbm_tracer_dims(const lbm_ctx *h, int s, int dims[3]);
+
+/* Density projection: every tracer adds unit mass to the 8 voxels around x/s with the
+ * trilinear (cloud-in-cell) weights (periodic axes wrap; along a non-periodic axis the base
+ * voxel is min(floor(x/s), g-2)).  out: host or device, gx*gy*gz floats, x fastest.  The 8
+ * contributions of every tracer are sorted by voxel (stable radix sort) and each run of
+ * equal voxels is summed in FP64 in that order, so the result is deterministic.
+ * Works with zero tracers (all zeros).  Errors: LBM_EINVAL (s, out NULL, grid >= 2^31
+ * voxels), LBM_ENOMEM (workspace: about 130 bytes per tracer). */
+int lbm_tracer_density(lbm_ctx *h, int s, float *out);
 
 /* Number of band nodes (nodes within the 2x2x2 stencil of a sample) of the solid. */
 long long lbm_band_size(const lbm_ctx *h);

@@ -175,6 +175,7 @@ int lbm_destroy(lbm_ctx *h) {
     if (!h) return LBM_OK;
     if (h->f) cudaStreamSynchronize(h->stream);
     free_solid(h);
+    free_tracers(h);
     dev_free(h->f);
     dev_free(h->outlet);
     dev_free(h->inlet_profile);
@@ -347,7 +348,10 @@ int lbm_step(lbm_ctx *h, int n) {
     if (n < 0) return fail(h, LBM_EINVAL, "negative step count");
     for (int k = 0; k < n; ++k) {
         const long long t = h->t + 1;
-        if ((rc = step_with(h, make_params(h, t)))) return rc;
+        lbm::StepParams P = make_params(h, t);
+        if (h->ntracer) P.u_out = h->tracer_u;   // the tracers move in this step's velocity
+        if ((rc = step_with(h, P))) return rc;
+        if ((rc = advect_tracers(h, t))) return rc;
         h->t = t;
     }
     return LBM_OK;

@@ -42,6 +42,14 @@ struct lbm_ctx {
     int *tile_off = nullptr;
     std::vector<long long> order;   // sorted position -> caller's sample index
 
+    // smoke tracers: positions [3][ntracer] (SoA), the velocity field [3][N] written by each
+    // step while tracers exist, the emitter of re-injected tracers, density workspace
+    long long ntracer = 0;
+    float *tx = nullptr, *tracer_u = nullptr;
+    lbm_emitter emitter{};
+    void *tracer_ws = nullptr;
+    size_t tracer_ws_bytes = 0;
+
     // scratch of the reductions
     double *partial = nullptr;
     size_t partial_cap = 0;         // doubles
@@ -184,6 +192,9 @@ inline void point_states(lbm::StepParams &P, const lbm_ctx *h, void *src, void *
 // destination; defined in lbm_api.cu
 int step_with(lbm_ctx *h, const lbm::StepParams &P);
 
+// move the smoke tracers by one step in the velocity field the step wrote (lbm_tracers.cu)
+int advect_tracers(lbm_ctx *h, long long t);
+
 inline int ensure_partial(lbm_ctx *h, size_t doubles) {
     if (doubles <= h->partial_cap) return LBM_OK;
     dev_free(h->partial);
@@ -192,6 +203,15 @@ inline int ensure_partial(lbm_ctx *h, size_t doubles) {
     if (rc) return rc;
     h->partial_cap = doubles;
     return LBM_OK;
+}
+
+inline void free_tracers(lbm_ctx *h) {
+    dev_free(h->tx);
+    dev_free(h->tracer_u);
+    if (h->tracer_ws) cudaFree(h->tracer_ws);
+    h->tracer_ws = nullptr;
+    h->tracer_ws_bytes = 0;
+    h->ntracer = 0;
 }
 
 inline void free_solid(lbm_ctx *h) {

@@ -79,6 +79,7 @@ struct StepParams {
     const int *tile_off;         // band index of the first band node of word w
     const float *bandF;          // [3][nband] immersed-boundary force of the band nodes
     long long nband;
+    float *u_out;                // [3][ncell] Guo-shifted velocity of the step, or nullptr
 };
 
 // ---- inlet noise: counter-based SplitMix64 (Steele, Lea, Flood 2014) ------------------

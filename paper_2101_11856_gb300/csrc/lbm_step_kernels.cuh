@@ -11,6 +11,16 @@ namespace lbm {
 
 inline unsigned step_blocks(long long n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
+// the velocity field output of a step (for the smoke tracers): one branch, uniform per launch
+__device__ __forceinline__ void store_velocity(const StepParams &P, int cell, float ux, float uy, float uz) {
+    if (P.u_out) {
+        const long long n = P.g.ncell;
+        P.u_out[cell] = ux;
+        P.u_out[n + cell] = uy;
+        P.u_out[2 * n + cell] = uz;
+    }
+}
+
 // ---- the fused step ---------------------------------------------------------------------
 // One thread per cell: pull the 27 streamed populations, add the body force and the band's
 // immersed-boundary force, collide in registers, store in place.  k_step_main updates the
@@ -35,6 +45,7 @@ __global__ void __launch_bounds__(STEP_BX) k_step_main(StepParams P) {
     collide_model<COLL>(h, Fx, Fy, Fz, P, rho, ux, uy, uz);
     if (!NB || inner) store_interior<St, NB>(P, cell, h);
     else store_yzface<St>(P, y, z, cell, h);
+    store_velocity(P, cell, ux, uy, uz);
 }
 
 // one warp per edge strip of one row, EDGE_ROWS rows (y) per block: blockIdx.y * EDGE_ROWS +
@@ -53,6 +64,7 @@ __device__ __forceinline__ void edge_node(const StepParams &P, int y, int z) {
     float rho, ux, uy, uz;
     collide_model<COLL>(h, Fx, Fy, Fz, P, rho, ux, uy, uz);
     store_edge<St, NB, SIDE>(P, x, y, z, cell, h);
+    store_velocity(P, cell, ux, uy, uz);
 }
 
 template <typename St, bool NB, bool BAND, int COLL>

@@ -20,7 +20,7 @@ LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ETIMEOUT, LBM_ESTA
 STORAGE = {"f32": 0, "f16": 1, "bf16": 2}
 FACE = {"periodic": 0, "noslip": 1, "inlet": 2, "outlet": 3}
 COLLISION = {"acm": 0, "bgk": 1, "raw": 2}
-KERNEL_KINDS = ("step", "band", "interp", "spread", "boundary", "other")
+KERNEL_KINDS = ("step", "band", "interp", "spread", "boundary", "other", "tracer")
 
 
 class LBMError(RuntimeError):
@@ -34,6 +34,10 @@ class lbm_config(C.Structure):
                 ("inlet_noise", C.c_double), ("seed", C.c_ulonglong), ("inflow_coef", C.c_double * 16),
                 ("omega_bulk", C.c_double), ("omega_hi", C.c_double * 4), ("cuda_stream", C.c_void_p),
                 ("collision", C.c_int)]
+
+
+class lbm_emitter(C.Structure):
+    _fields_ = [("lo", C.c_double * 3), ("hi", C.c_double * 3), ("seed", C.c_ulonglong)]
 
 
 class lbm_loss(C.Structure):
@@ -61,6 +65,11 @@ _SIGS = {
     "lbm_profile": (C.c_int, [C.c_void_p, C.c_int]),
     "lbm_kernel_times": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
     "lbm_band_size": (C.c_longlong, [C.c_void_p]),
+    "lbm_set_tracers": (C.c_int, [C.c_void_p, C.c_void_p, C.c_longlong, C.POINTER(lbm_emitter)]),
+    "lbm_tracer_count": (C.c_longlong, [C.c_void_p]),
+    "lbm_tracers": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "lbm_tracer_dims": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int)]),
+    "lbm_tracer_density": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "lbm_adjoint": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.POINTER(lbm_loss), C.POINTER(C.c_double),
                               C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "lbm_sum_forces_static": (C.c_int, [C.c_void_p, C.c_longlong, C.c_void_p, C.c_void_p]),
@@ -210,6 +219,37 @@ def lbm_band_size(h):
     return library().lbm_band_size(h)
 
 
+def lbm_set_tracers(h, X, emitter=None):
+    """X: (count, 3) positions (numpy or torch); emitter = (lo, hi, seed) or None."""
+    count = 0 if X is None else int(np.prod(X.shape) // 3)
+    px, kx = _ptr(X) if count else (None, None)
+    em = None
+    if emitter is not None:
+        lo, hi, seed = emitter
+        em = lbm_emitter((C.c_double * 3)(*lo), (C.c_double * 3)(*hi), int(seed))
+    _check(library().lbm_set_tracers(h, px, count, C.byref(em) if em is not None else None), h)
+
+
+def lbm_tracer_count(h):
+    return library().lbm_tracer_count(h)
+
+
+def lbm_tracers(h, out):
+    p, k = _ptr(out)
+    _check(library().lbm_tracers(h, p), h)
+
+
+def lbm_tracer_dims(h, s):
+    d = (C.c_int * 3)()
+    _check(library().lbm_tracer_dims(h, int(s), d), h)
+    return tuple(d[:])
+
+
+def lbm_tracer_density(h, s, out):
+    p, k = _ptr(out)
+    _check(library().lbm_tracer_density(h, int(s), p), h)
+
+
 def lbm_adjoint(h, n, K, w_drag=1.0, w_ke=0.0, ke_x0=0, ke_x1=0, count=0):
     """Run n steps with the adjoint; returns (L, dL/d inflow coefficients (16,), dL/dX (count, 3))."""
     loss = lbm_loss(w_drag, w_ke, ke_x0, ke_x1)
@@ -293,6 +333,23 @@ class Solver:
 
     def reductions(self):
         return lbm_reductions(self.h)
+
+    def set_tracers(self, X, emitter=None):
+        lbm_set_tracers(self.h, X, emitter)
+
+    def tracers(self):
+        """Tracer positions (count, 3) as a float32 numpy array."""
+        out = np.empty((lbm_tracer_count(self.h), 3), np.float32)
+        if out.shape[0]:
+            lbm_tracers(self.h, out)
+        return out
+
+    def tracer_density(self, s=1):
+        """Cloud-in-cell tracer density on the grid of spacing s, (gz, gy, gx) float32."""
+        gx, gy, gz = lbm_tracer_dims(self.h, s)
+        out = np.empty((gz, gy, gx), np.float32)
+        lbm_tracer_density(self.h, s, out)
+        return out
 
     def ib_forces(self, count):
         g = np.empty((count, 3), np.float32)
