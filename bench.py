@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-models", action="store_true", help="skip the BGK / raw-MRT comparison runs")
+    ap.add_argument("--no-tracers", action="store_true", help="skip the smoke-tracer run")
+    ap.add_argument("--tracers", type=int, default=4_000_000, help="smoke tracers of the tracer run")
     ap.add_argument("--adjoint-only", action="store_true", help="time only the adjoint workload")
     return ap.parse_args()
 
@@ -203,6 +205,53 @@ def adjoint_cost(torch, args):
             "what": "lbm_adjoint (forward with checkpoints + segment recompute + backward) vs lbm_step x 200"}
 
 
+def tracer_run(torch, lbm, make, d, args, N, n_int, peak, world, steps):
+    """Box city with smoke injected at the inlet: tracers seeded in the emitter slab
+    1 <= x < 41, 1 <= y < 121 (all z) and re-injected there.  Reports the whole step with the
+    velocity output and the advection, the advection kernel against its algorithmic bytes
+    (positions read + written, 2 x 8 corners x 3 velocity components gathered: 216 B per
+    tracer) and one density projection on the grid of spacing 2."""
+    nx, ny, nz = d["nx"], d["ny"], d["nz"]
+    P = args.tracers
+    lo, hi = (1.0, 1.0, 0.0), (float(min(41, nx - 2)), float(min(121, ny - 2)), float(nz))
+    rng = np.random.default_rng(2101)
+    X = (np.array(lo) + rng.uniform(0, 1, (P, 3)) * (np.array(hi) - np.array(lo))).astype(np.float32)
+    s = make("f32")
+    s.set_tracers(X, (lo, hi, 2101))
+    del X
+    s.step(args.warmup)
+    torch.cuda.synchronize()
+    ms, kt = timed_steps(s, steps, torch)
+    adv_ms = kt["tracer"][0] / max(kt["tracer"][1], 1)
+    step_ms = kt["step"][0] / max(kt["step"][1], 1)
+    adv_bytes = 216 * P
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    dims = lbm.lbm_tracer_dims(s.h, 2)
+    grid = torch.empty(dims[2], dims[1], dims[0], device="cuda")
+    lbm.lbm_tracer_density(s.h, 2, grid)           # allocates the workspace once
+    torch.cuda.synchronize()
+    e0.record()
+    lbm.lbm_tracer_density(s.h, 2, grid)
+    e1.record()
+    torch.cuda.synchronize()
+    dens_ms = e0.elapsed_time(e1)
+    mass = float(grid.double().sum())
+    s.close()
+    torch.cuda.empty_cache()
+    if abs(mass - P) > 1e-4 * P:
+        raise RuntimeError(f"tracer density mass {mass} != {P}")
+    ach = adv_bytes / (adv_ms * 1e-3) / 1e9
+    step_ach = 228 * n_int / (step_ms * 1e-3) / 1e9
+    return {"count": P, "emitter": [lo, hi], "mlups": world * N / (ms / steps * 1e-3) / 1e6, "ms_per_step": ms / steps,
+            "step_kernel_ms": step_ms,
+            "step_kernel_roofline": {"achieved": step_ach, "frac": step_ach / peak, "bytes_per_cell": 228,
+                                     "what": "216 B populations + 12 B velocity output"},
+            "advect_ms": adv_ms,
+            "advect_roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                                "bytes_per_tracer": 216},
+            "density_ms": dens_ms, "density_grid": list(dims), "density_mass": mass}
+
+
 def timed_steps(solver, steps, torch):
     from paper_2101_11856_gb300 import lbm
     s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -341,6 +390,11 @@ def main():
         for coll in ("bgk", "raw"):
             models[coll] = {st: side_run(st, coll, n_side) for st in ("f32",) + (() if args.no_fp16 else ("f16",))}
 
+    # ---- smoke tracers in the same flow (velocity output + advection, density projection) ------
+    tracers = None
+    if not args.no_tracers:
+        tracers = tracer_run(torch, lbm, make, d, args, N, n_int, peak, world, n_side)
+
     adjoint = None
     if not args.no_adjoint:
         adjoint = adjoint_cost(torch, args)
@@ -372,6 +426,7 @@ def main():
             "e2e": e2e,
             "fp16": fp16,
             "collision_models": models,
+            "tracers": tracers,
             "adjoint": adjoint,
             "cpu_baseline": cpu,
             "checks": {"mass": mass, "drag": list(map(float, drag))},

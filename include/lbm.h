@@ -216,8 +216,10 @@ typedef struct lbm_emitter {
 /* Set (count > 0) or remove (count = 0) the tracers.  X: host or device pointer to count*3
  * floats (x, y, z per tracer), each inside the domain ([0, n) along periodic axes, [0, n-1]
  * along the others); non-periodic axes need n >= 2.  em: the re-injection box, inside the
- * same domain (lo <= hi); required unless every axis is periodic.  Allocates 12 (count + N)
- * bytes on the device; count < 2^28.  Tracers are not part of lbm_save checkpoints.
+ * same domain (lo <= hi); required unless every axis is periodic.  Allocates about
+ * 50 bytes per tracer and 12 bytes per cell on the device; count < 2^28.  The library keeps
+ * the tracers in its own (spatially sorted) order; lbm_tracers returns them in the caller's
+ * order.  Tracers are not part of lbm_save checkpoints.
  * Errors: LBM_EINVAL (bad position, box or count; X or em NULL), LBM_ENOMEM. */
 int lbm_set_tracers(lbm_ctx *h, const float *X, long long count, const lbm_emitter *em);
 
@@ -234,11 +236,11 @@ int lbm_tracer_dims(const lbm_ctx *h, int s, int dims[3]);
 
 /* Density projection: every tracer adds unit mass to the 8 voxels around x/s with the
  * trilinear (cloud-in-cell) weights (periodic axes wrap; along a non-periodic axis the base
- * voxel is min(floor(x/s), g-2)).  out: host or device, gx*gy*gz floats, x fastest.  The 8
- * contributions of every tracer are sorted by voxel (stable radix sort) and each run of
- * equal voxels is summed in FP64 in that order, so the result is deterministic.
+ * voxel is min(floor(x/s), g-2)).  out: host or device, gx*gy*gz floats, x fastest.  The
+ * tracers are sorted by base voxel (stable radix sort) and every voxel sums the runs of its
+ * eight lower neighbours in FP64 in a fixed order, so the result is deterministic.
  * Works with zero tracers (all zeros).  Errors: LBM_EINVAL (s, out NULL, grid >= 2^31
- * voxels), LBM_ENOMEM (workspace: about 130 bytes per tracer). */
+ * voxels), LBM_ENOMEM (workspace: 4 bytes per voxel, 8 with a host out). */
 int lbm_tracer_density(lbm_ctx *h, int s, float *out);
 
 /* Number of band nodes (nodes within the 2x2x2 stencil of a sample) of the solid. */

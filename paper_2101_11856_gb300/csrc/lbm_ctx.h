@@ -42,10 +42,13 @@ struct lbm_ctx {
     int *tile_off = nullptr;
     std::vector<long long> order;   // sorted position -> caller's sample index
 
-    // smoke tracers: positions [3][ntracer] (SoA), the velocity field [3][N] written by each
-    // step while tracers exist, the emitter of re-injected tracers, density workspace
+    // smoke tracers, stored in 4x4x4-cell brick order (re-sorted after every advection):
+    // positions [3][ntracer] (SoA) and the caller's index of each stored tracer, a second
+    // copy of both for the reordering, the velocity field [3][N] written by each step while
+    // tracers exist, the emitter of re-injected tracers, and the sort / density workspace
     long long ntracer = 0;
-    float *tx = nullptr, *tracer_u = nullptr;
+    float *tx = nullptr, *tx_alt = nullptr, *tracer_u = nullptr;
+    uint32_t *tid = nullptr, *tid_alt = nullptr;
     lbm_emitter emitter{};
     void *tracer_ws = nullptr;
     size_t tracer_ws_bytes = 0;
@@ -207,6 +210,9 @@ inline int ensure_partial(lbm_ctx *h, size_t doubles) {
 
 inline void free_tracers(lbm_ctx *h) {
     dev_free(h->tx);
+    dev_free(h->tx_alt);
+    dev_free(h->tid);
+    dev_free(h->tid_alt);
     dev_free(h->tracer_u);
     if (h->tracer_ws) cudaFree(h->tracer_ws);
     h->tracer_ws = nullptr;

@@ -1,4 +1,4 @@
-// Stable radix sort, exclusive scan and segmented sum (see lbm_sort.cuh).
+// Stable radix sort and exclusive scan (see lbm_sort.cuh).
 #include "lbm_sort.cuh"
 
 namespace lbm {
@@ -120,19 +120,6 @@ __global__ void __launch_bounds__(SORT_THREADS) k_digit_scatter(const uint32_t *
     }
 }
 
-// ---- segmented sum -----------------------------------------------------------------------------
-
-__global__ void __launch_bounds__(256) k_segmented_sum(const uint32_t *keys, const float *vals, long long n,
-                                                       float *out) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const uint32_t k = keys[i];
-    if (i > 0 && keys[i - 1] == k) return;   // not the head of a run
-    double acc = 0.0;
-    for (long long j = i; j < n && keys[j] == k; ++j) acc += (double)vals[j];
-    out[k] = (float)acc;
-}
-
 }  // namespace
 
 size_t scan_workspace_bytes(long long n) {
@@ -181,12 +168,6 @@ cudaError_t sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *tmp_keys, uint3
         return e;
     }
     return cudaSuccess;
-}
-
-cudaError_t segmented_sum(const uint32_t *keys, const float *vals, long long n, float *out, cudaStream_t st) {
-    if (n <= 0) return cudaSuccess;
-    k_segmented_sum<<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(keys, vals, n, out);
-    return cudaGetLastError();
 }
 
 }  // namespace lbm

@@ -1,7 +1,6 @@
 // Device primitives for regrouping points by grid cell: a stable least-significant-digit
-// radix sort of (32-bit key, 32-bit value) pairs, an exclusive scan of ints, and a
-// segmented FP64 sum over the runs of equal keys of a sorted sequence.  All counts are
-// integers and every output position is a function of the input order alone, so the
+// radix sort of (32-bit key, 32-bit value) pairs and an exclusive scan of ints.  All counts
+// are integers and every output position is a function of the input order alone, so the
 // results are deterministic (no float atomics anywhere).
 #pragma once
 
@@ -28,11 +27,7 @@ cudaError_t sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *tmp_keys, uint3
 // bytes of device workspace that exclusive_scan needs for n ints
 size_t scan_workspace_bytes(long long n);
 
-// out[i] = sum_{j < i} in[i] (in == out allowed); optional *total = sum of all (device int)
+// out[i] = sum_{j < i} in[j] (in == out allowed)
 cudaError_t exclusive_scan(const int *in, int *out, long long n, void *work, cudaStream_t st);
-
-// For sorted keys: out[key] = sum (in FP64, in sequence order) of vals over each run of
-// equal keys, written as float; entries of out without a key are left untouched.
-cudaError_t segmented_sum(const uint32_t *keys, const float *vals, long long n, float *out, cudaStream_t st);
 
 }  // namespace lbm

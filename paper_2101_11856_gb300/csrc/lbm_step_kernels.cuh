@@ -11,9 +11,9 @@ namespace lbm {
 
 inline unsigned step_blocks(long long n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
-// the velocity field output of a step (for the smoke tracers): one branch, uniform per launch
+// the velocity field output of a step (for the smoke tracers; kernels with VOUT only)
 __device__ __forceinline__ void store_velocity(const StepParams &P, int cell, float ux, float uy, float uz) {
-    if (P.u_out) {
+    {
         const long long n = P.g.ncell;
         P.u_out[cell] = ux;
         P.u_out[n + cell] = uy;
@@ -29,7 +29,7 @@ __device__ __forceinline__ void store_velocity(const StepParams &P, int cell, fl
 // rows; even steps address only the node's own slots).  k_step_edges updates the two edge
 // strips of each row with the general face rules (inlet, outlet, x wrap) in whole warps.
 // Every node is updated by exactly one of the two, and the two touch disjoint slots.
-template <typename St, bool NB, bool BAND, int COLL>
+template <typename St, bool NB, bool BAND, int COLL, bool VOUT>
 __global__ void __launch_bounds__(STEP_BX) k_step_main(StepParams P) {
     const int x = blockIdx.x * STEP_BX + threadIdx.x + XEDGE;
     if (x >= P.g.nx - XEDGE) return;
@@ -45,14 +45,14 @@ __global__ void __launch_bounds__(STEP_BX) k_step_main(StepParams P) {
     collide_model<COLL>(h, Fx, Fy, Fz, P, rho, ux, uy, uz);
     if (!NB || inner) store_interior<St, NB>(P, cell, h);
     else store_yzface<St>(P, y, z, cell, h);
-    store_velocity(P, cell, ux, uy, uz);
+    if (VOUT) store_velocity(P, cell, ux, uy, uz);
 }
 
 // one warp per edge strip of one row, EDGE_ROWS rows (y) per block: blockIdx.y * EDGE_ROWS +
 // threadIdx.y = y, blockIdx.z = z.  With a main range, blockIdx.x picks the left (0) or right
 // (1) strip (one launch for both: measured faster than a launch per side); short rows run the
 // SIDE = 2 kernel over consecutive warps.
-template <typename St, bool NB, bool BAND, int SIDE, int COLL>
+template <typename St, bool NB, bool BAND, int SIDE, int COLL, bool VOUT>
 __device__ __forceinline__ void edge_node(const StepParams &P, int y, int z) {
     const int x = edge_x<SIDE>(P.g);
     if (x >= P.g.nx) return;
@@ -64,48 +64,55 @@ __device__ __forceinline__ void edge_node(const StepParams &P, int y, int z) {
     float rho, ux, uy, uz;
     collide_model<COLL>(h, Fx, Fy, Fz, P, rho, ux, uy, uz);
     store_edge<St, NB, SIDE>(P, x, y, z, cell, h);
-    store_velocity(P, cell, ux, uy, uz);
+    if (VOUT) store_velocity(P, cell, ux, uy, uz);
 }
 
-template <typename St, bool NB, bool BAND, int COLL>
+template <typename St, bool NB, bool BAND, int COLL, bool VOUT>
 __global__ void __launch_bounds__(XEDGE * EDGE_ROWS) k_step_edges(StepParams P) {
     const int y = blockIdx.y * EDGE_ROWS + threadIdx.y, z = blockIdx.z;
     if (y >= P.g.ny) return;
-    if (blockIdx.x == 0) edge_node<St, NB, BAND, 0, COLL>(P, y, z);
-    else edge_node<St, NB, BAND, 1, COLL>(P, y, z);
+    if (blockIdx.x == 0) edge_node<St, NB, BAND, 0, COLL, VOUT>(P, y, z);
+    else edge_node<St, NB, BAND, 1, COLL, VOUT>(P, y, z);
 }
 
-template <typename St, bool NB, bool BAND, int COLL>
+template <typename St, bool NB, bool BAND, int COLL, bool VOUT>
 __global__ void __launch_bounds__(XEDGE * EDGE_ROWS) k_step_rows(StepParams P) {
     const int y = blockIdx.y * EDGE_ROWS + threadIdx.y, z = blockIdx.z;
     if (y >= P.g.ny) return;
-    edge_node<St, NB, BAND, 2, COLL>(P, y, z);
+    edge_node<St, NB, BAND, 2, COLL, VOUT>(P, y, z);
 }
 
-template <typename St, bool NB, bool BAND, int COLL>
+template <typename St, bool NB, bool BAND, int COLL, bool VOUT>
 cudaError_t launch_step_tt(const StepParams &P, int part, cudaStream_t st) {
     const Geometry &g = P.g;
     if (part == STEP_BOUNDARY) {
         const dim3 block(XEDGE, EDGE_ROWS);
         if (has_interior(g)) {
             const dim3 grid(2, step_blocks(g.ny, EDGE_ROWS), g.nz);
-            k_step_edges<St, NB, BAND, COLL><<<grid, block, 0, st>>>(P);
+            k_step_edges<St, NB, BAND, COLL, VOUT><<<grid, block, 0, st>>>(P);
         } else {
             const dim3 grid(step_blocks(g.nx, XEDGE), step_blocks(g.ny, EDGE_ROWS), g.nz);
-            k_step_rows<St, NB, BAND, COLL><<<grid, block, 0, st>>>(P);
+            k_step_rows<St, NB, BAND, COLL, VOUT><<<grid, block, 0, st>>>(P);
         }
     } else if (has_interior(g)) {
         const dim3 grid(step_blocks(g.nx - 2 * XEDGE, STEP_BX), g.ny, g.nz);
-        k_step_main<St, NB, BAND, COLL><<<grid, STEP_BX, 0, st>>>(P);
+        k_step_main<St, NB, BAND, COLL, VOUT><<<grid, STEP_BX, 0, st>>>(P);
     }
     return cudaGetLastError();
 }
 
+template <typename St, int COLL, bool VOUT>
+cudaError_t launch_step_v(const StepParams &P, bool band, int part, cudaStream_t st) {
+    const bool nb = (P.t & 1) != 0;
+    if (nb) return band ? launch_step_tt<St, true, true, COLL, VOUT>(P, part, st)
+                        : launch_step_tt<St, true, false, COLL, VOUT>(P, part, st);
+    return band ? launch_step_tt<St, false, true, COLL, VOUT>(P, part, st)
+                : launch_step_tt<St, false, false, COLL, VOUT>(P, part, st);
+}
+
 template <typename St, int COLL>
 cudaError_t launch_step_t(const StepParams &P, bool band, int part, cudaStream_t st) {
-    const bool nb = (P.t & 1) != 0;
-    if (nb) return band ? launch_step_tt<St, true, true, COLL>(P, part, st) : launch_step_tt<St, true, false, COLL>(P, part, st);
-    return band ? launch_step_tt<St, false, true, COLL>(P, part, st) : launch_step_tt<St, false, false, COLL>(P, part, st);
+    return P.u_out ? launch_step_v<St, COLL, true>(P, band, part, st) : launch_step_v<St, COLL, false>(P, band, part, st);
 }
 
 // one part of one step for the collision model COLL; instantiated in lbm_step_<model>.cu
