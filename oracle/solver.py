@@ -27,6 +27,7 @@ import torch
 
 from . import collision as col
 from . import ib
+from . import motion as mo
 from .lattice import DTYPE
 from .noise import inlet_noise
 from .streaming import check_faces, stream
@@ -121,6 +122,8 @@ class OracleSolver:
         self.p = p
         self.coef = None if inflow_coef is None else torch.as_tensor(np.asarray(inflow_coef), dtype=DTYPE)
         self.solids = None
+        self.motion = None
+        self.X0 = None
         self.t = 0
         self.f = None
         self.diag = None
@@ -138,11 +141,29 @@ class OracleSolver:
         area = torch.ones(S, dtype=DTYPE) if area is None else torch.as_tensor(np.asarray(area), dtype=DTYPE)
         u_b = torch.zeros(3, S, dtype=DTYPE) if u_b is None else torch.as_tensor(np.asarray(u_b), dtype=DTYPE).T
         self.solids = (X, area, u_b)
+        self.motion = None
+
+    def set_motion(self, motion):
+        """Prescribed rigid motion (c0, V, axis, w) of the current samples (``motion``)."""
+        self.motion = motion
+        self.X0 = self.solids[0].numpy().copy()
+        self._pose(self.t)
+
+    def _pose(self, tau):
+        X = mo.sample_positions(self.X0, self.motion, tau)
+        ub = mo.boundary_velocity(X, self.motion, tau)
+        self.solids = (torch.from_numpy(X), self.solids[1], torch.from_numpy(ub.T.copy()))
 
     def step(self, n: int = 1):
         for _ in range(n):
             self.t += 1
+            if self.motion is not None:
+                self._pose(self.t - 1)        # Algorithm 2 (c): the update after the previous IB stage
             self.f, self.diag = step(self.p, self.f, self.t, self.coef, self.solids)
+
+    def torque(self, center):
+        """Torque on the solid about ``center`` from the last step's samples and forces."""
+        return mo.torque(self.solids[0].numpy(), self.diag["g"].numpy().T, center)
 
     def macroscopic(self):
         return self.diag["rho"], self.diag["u"]
