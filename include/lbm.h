@@ -190,10 +190,44 @@ int lbm_load(lbm_ctx *h, const void *buf, size_t bytes);
                                       row ends (whole rows when nx < 65)                   */
 #define LBM_KERNEL_OTHER       5   /* init, macroscopic, reductions, copies, density      */
 #define LBM_KERNEL_TRACER      6   /* smoke tracer advection                              */
-#define LBM_NUM_KERNEL_KINDS   7
+#define LBM_KERNEL_MOTION      7   /* moving solids: pose, re-sort and band rebuild       */
+#define LBM_NUM_KERNEL_KINDS   8
 int lbm_profile(lbm_ctx *h, int enable);
 /* ms[k], launches[k] for k < LBM_NUM_KERNEL_KINDS; waits for the stream. */
 int lbm_kernel_times(lbm_ctx *h, double ms[LBM_NUM_KERNEL_KINDS], long long launches[LBM_NUM_KERNEL_KINDS]);
+
+/* ---- Moving and rotating solids (Algorithm 2 (c): after the penalty forces are spread the
+ * total force and torque are reduced and the solid samples are updated; the paper's dynamic
+ * solids are a rotating torus and a moving airplane, Sec. 6).  Prescribed rigid motion: the
+ * samples of lbm_set_solids are the pose at the current time t0, with rotation centre
+ * `center`; at time t0 + tau the centre is center + velocity tau and the samples are rotated
+ * by omega tau (radians) about `axis` (Rodrigues).  Step t runs its immersed-boundary stage
+ * with the samples at the pose of time t - 1 (the update that follows the previous step's
+ * IB stage) and boundary velocity u_b = velocity + omega axis x (X - centre).  At the start
+ * of every step the library re-poses the samples in FP64, re-sorts them by base cell (stable
+ * radix sort) and rebuilds the band and the spreading lists on the device. */
+typedef struct lbm_motion {
+    double center[3];            /* rotation centre of the samples' current pose (lattice units) */
+    double velocity[3];          /* translation per step                                         */
+    double axis[3];              /* rotation axis (any length; zero vector: no rotation)         */
+    double omega;                /* angular velocity, radians per step                           */
+} lbm_motion;
+
+/* Start (m != NULL) or stop (m = NULL: the samples stay at their last pose) the motion of
+ * the solid of lbm_set_solids; lbm_set_solids ends any motion.  Needs a solid.  Replaces
+ * the boundary velocities by the rigid-body ones.  A step whose pose would bring a sample
+ * within 1e-3 of the domain's faces (the sphere of radius max |X0 - centre| about the
+ * centre) returns LBM_EINVAL before running.  After this call lbm_adjoint returns
+ * LBM_EINVAL (static solids only).  Errors: LBM_EINVAL, LBM_ESTATE (no solid), LBM_ENOMEM. */
+int lbm_set_motion(lbm_ctx *h, const lbm_motion *m);
+
+/* Current sample positions (of the last step's IB stage), count*3 floats in the caller's
+ * order of lbm_set_solids (host or device pointer). */
+int lbm_solid_samples(lbm_ctx *h, float *X);
+
+/* Torque on the solid from the last step: sum_s (X_s - c) x (-g_s) in FP64 about c = center,
+ * or about the motion's current centre when center is NULL (the origin without motion). */
+int lbm_solid_torque(lbm_ctx *h, const double center[3], double torque[3]);
 
 /* ---- Smoke tracers (Sec. 6: smoke particles traced on the GPU and their density projected
  * onto a uniform volume grid for rendering; the paper prints no formulas, so the readings

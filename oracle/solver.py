@@ -147,9 +147,11 @@ class OracleSolver:
         """Prescribed rigid motion (c0, V, axis, w) of the current samples (``motion``)."""
         self.motion = motion
         self.X0 = self.solids[0].numpy().copy()
+        self.t0 = self.t                      # the samples now are the pose of time 0
         self._pose(self.t)
 
-    def _pose(self, tau):
+    def _pose(self, t_abs):
+        tau = t_abs - self.t0
         X = mo.sample_positions(self.X0, self.motion, tau)
         ub = mo.boundary_velocity(X, self.motion, tau)
         self.solids = (torch.from_numpy(X), self.solids[1], torch.from_numpy(ub.T.copy()))

@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "liblbm.so")
 SOURCES = ["lbm_adjoint.cu", "lbm_step_acm.cu", "lbm_step_bgk.cu", "lbm_step_raw.cu", "lbm_kernels.cu", "lbm_api.cu",
-           "lbm_tracers.cu", "lbm_sort.cu", "lbm_static.cu"]
+           "lbm_tracers.cu", "lbm_motion.cu", "lbm_sort.cu", "lbm_static.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

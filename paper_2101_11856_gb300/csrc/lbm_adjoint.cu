@@ -572,6 +572,7 @@ extern "C" int lbm_adjoint(lbm_ctx *h, int n, int K, const lbm_loss *loss, doubl
     if (!h->has_state) return fail(h, LBM_ESTATE, "lbm_set_state (or lbm_load) has not been called");
     if (n < 1 || !loss) return fail(h, LBM_EINVAL, "n must be >= 1 and loss given");
     if (h->cfg.collision != LBM_COLL_ACM) return fail(h, LBM_EINVAL, "the adjoint exists for the ACM-MRT collision only");
+    if (h->band_count_dev) return fail(h, LBM_EINVAL, "the adjoint exists for static solids only (lbm_set_motion was called)");
     if (loss->ke_x0 < 0 || loss->ke_x1 > h->nx || loss->ke_x0 > loss->ke_x1) return fail(h, LBM_EINVAL, "bad slab");
     K = std::max(1, std::min(K, n));
     const long long N = h->N, S = h->S, nb = h->nband;
@@ -662,7 +663,7 @@ extern "C" int lbm_adjoint(lbm_ctx *h, int n, int K, const lbm_loss *loss, doubl
             if (S > 0) {
                 CK(launch_band_moments(h->storage, P, h->band_cell, h->band_rho, h->band_u, st));
                 CK(launch_ib_interp(S, nb, h->X, h->area, h->ub, h->corner_band, h->band_rho, h->band_u, h->g, st));
-                CK(launch_ib_spread(S, nb, h->X, h->g, h->base_nbr, h->cstart, h->ccount, h->bandF, st));
+                CK(launch_ib_spread(S, nb, nullptr, h->X, h->g, h->base_nbr, h->cstart, h->ccount, h->bandF, st));
                 CK(with_storage(h->storage, [&](auto tag) {
                     using St = decltype(tag);
                     if (nbp) k_adj_band_force<St, true><<<nblocks(nb, 128), 128, 0, st>>>(P, A, h->band_cell);

@@ -31,7 +31,7 @@ int step_with(lbm_ctx *h, const StepParams &P) {
     if (band) {
         { Timed tm(h, LBM_KERNEL_BAND); CK(launch_band_moments(h->storage, P, h->band_cell, h->band_rho, h->band_u, h->stream)); }
         { Timed tm(h, LBM_KERNEL_INTERP); CK(launch_ib_interp(h->S, h->nband, h->X, h->area, h->ub, h->corner_band, h->band_rho, h->band_u, h->g, h->stream)); }
-        { Timed tm(h, LBM_KERNEL_SPREAD); CK(launch_ib_spread(h->S, h->nband, h->X, h->g, h->base_nbr, h->cstart, h->ccount, h->bandF, h->stream)); }
+        { Timed tm(h, LBM_KERNEL_SPREAD); CK(launch_ib_spread(h->S, h->nband, h->band_count_dev, h->X, h->g, h->base_nbr, h->cstart, h->ccount, h->bandF, h->stream)); }
     }
     { Timed tm(h, LBM_KERNEL_BOUNDARY); CK(launch_step(h->storage, P, band, STEP_BOUNDARY, h->cfg.collision, h->stream)); }
     if (has_interior(P.g)) {
@@ -348,6 +348,7 @@ int lbm_step(lbm_ctx *h, int n) {
     if (n < 0) return fail(h, LBM_EINVAL, "negative step count");
     for (int k = 0; k < n; ++k) {
         const long long t = h->t + 1;
+        if ((rc = motion_before_step(h, t))) return rc;
         lbm::StepParams P = make_params(h, t);
         if (h->ntracer) P.u_out = h->tracer_u;   // the tracers move in this step's velocity
         if ((rc = step_with(h, P))) return rc;
@@ -417,6 +418,7 @@ int lbm_ib_forces(lbm_ctx *h, float *g) {
     if (!g) return fail(h, LBM_EINVAL, "g is NULL");
     const size_t S = (size_t)h->S;
     if (S == 0) return LBM_OK;
+    if ((rc = sync_order(h))) return rc;
     std::vector<float> sorted(3 * S), out(3 * S);
     CK(cudaMemcpyAsync(sorted.data(), h->g, 3 * S * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
@@ -460,7 +462,17 @@ int lbm_velocity(int i, int c[3]) {
 
 long long lbm_time(const lbm_ctx *h) { return h ? h->t : -1; }
 
-long long lbm_band_size(const lbm_ctx *h) { return h ? h->nband : -1; }
+long long lbm_band_size(const lbm_ctx *h) {
+    if (!h) return -1;
+    if (!h->band_count_dev) return h->nband;
+    int n = 0;   // moving solids: the count of the last rebuild
+    if (cudaMemcpyAsync(&n, h->band_count_dev, sizeof(int), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+        cudaStreamSynchronize(h->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
+    return n;
+}
 
 int lbm_check(lbm_ctx *h) {
     int rc = require_state(h);

@@ -42,6 +42,20 @@ struct lbm_ctx {
     int *tile_off = nullptr;
     std::vector<long long> order;   // sorted position -> caller's sample index
 
+    // moving solids (lbm_set_motion): the band arrays use the fixed stride nband = 8 S (or
+    // N) and the device count band_count_dev; the samples are re-posed, re-sorted and the
+    // band rebuilt on the device at the start of every step
+    bool moving = false;
+    lbm_motion motion{};
+    double r_max = 0.0;             // largest |X0 - c0| of the reference samples
+    long long posed_tau0 = 0;       // step count at lbm_set_motion (the reference pose's time)
+    long long posed_tau = -1;       // time of the pose the band was last built for
+    int *band_count_dev = nullptr;
+    float *X0 = nullptr, *X0_alt = nullptr, *area_alt = nullptr, *Xtmp = nullptr;
+    int *sid = nullptr, *sid_alt = nullptr;
+    void *motion_ws = nullptr;
+    size_t motion_ws_bytes = 0;
+
     // smoke tracers, stored in 4x4x4-cell brick order (re-sorted after every advection):
     // positions [3][ntracer] (SoA) and the caller's index of each stored tracer, a second
     // copy of both for the reordering, the velocity field [3][N] written by each step while
@@ -175,6 +189,7 @@ inline lbm::StepParams make_params(const lbm_ctx *h, long long t) {
     P.tile_off = h->tile_off;
     P.bandF = h->bandF;
     P.nband = h->nband;
+    P.band_count = h->band_count_dev;
     return P;
 }
 
@@ -197,6 +212,11 @@ int step_with(lbm_ctx *h, const lbm::StepParams &P);
 
 // move the smoke tracers by one step in the velocity field the step wrote (lbm_tracers.cu)
 int advect_tracers(lbm_ctx *h, long long t);
+
+// moving solids (lbm_motion.cu): pose the samples for step t (the pose of time t - 1) and
+// rebuild the band; refresh the host copy of the samples' caller order
+int motion_before_step(lbm_ctx *h, long long t);
+int sync_order(lbm_ctx *h);
 
 inline int ensure_partial(lbm_ctx *h, size_t doubles) {
     if (doubles <= h->partial_cap) return LBM_OK;
@@ -226,6 +246,14 @@ inline void free_solid(lbm_ctx *h) {
     dev_free(h->cstart); dev_free(h->ccount);
     dev_free(h->band_rho); dev_free(h->band_u); dev_free(h->bandF);
     dev_free(h->tile_mask); dev_free(h->tile_off);
+    dev_free(h->band_count_dev);
+    dev_free(h->X0); dev_free(h->X0_alt); dev_free(h->area_alt); dev_free(h->Xtmp);
+    dev_free(h->sid); dev_free(h->sid_alt);
+    if (h->motion_ws) cudaFree(h->motion_ws);
+    h->motion_ws = nullptr;
+    h->motion_ws_bytes = 0;
+    h->moving = false;
+    h->posed_tau = -1;
     h->S = h->nband = h->ntiles = 0;
     h->order.clear();
 }

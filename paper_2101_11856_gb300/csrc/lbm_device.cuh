@@ -78,7 +78,8 @@ struct StepParams {
     const uint32_t *tile_mask;   // bit l of word w: cell 32 w + l is a band node
     const int *tile_off;         // band index of the first band node of word w
     const float *bandF;          // [3][nband] immersed-boundary force of the band nodes
-    long long nband;
+    long long nband;             // band nodes, or the stride of the band arrays when band_count is set
+    const int *band_count;       // device count of band nodes (moving solids), or nullptr
     float *u_out;                // [3][ncell] Guo-shifted velocity of the step, or nullptr
 };
 

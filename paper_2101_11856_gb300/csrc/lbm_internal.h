@@ -34,8 +34,10 @@ cudaError_t launch_band_moments(int storage, const StepParams &P, const int *ban
 cudaError_t launch_ib_interp(long long S, long long nband, const float *X, const float *area, const float *ub,
                              const int *corner_band, const float *band_rho, const float *band_u, float *g,
                              cudaStream_t st);
-cudaError_t launch_ib_spread(long long S, long long nband, const float *X, const float *g, const int *base_nbr,
-                             const int *cstart, const int *ccount, float *bandF, cudaStream_t st);
+// nband: band nodes (or the stride of the band arrays when count is set); count: device
+// count of band nodes (moving solids) or nullptr
+cudaError_t launch_ib_spread(long long S, long long nband, const int *count, const float *X, const float *g,
+                             const int *base_nbr, const int *cstart, const int *ccount, float *bandF, cudaStream_t st);
 int force_sum_blocks();
 cudaError_t launch_sum_forces(long long S, const float *g, double *partial, cudaStream_t st);
 

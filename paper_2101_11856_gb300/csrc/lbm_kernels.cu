@@ -154,7 +154,7 @@ template <typename St, bool NB>
 __global__ void __launch_bounds__(256) k_band_moments(StepParams P, const int *__restrict__ band_cell,
                                                       float *__restrict__ band_rho, float *__restrict__ band_u) {
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= P.nband) return;
+    if (k >= (P.band_count ? (long long)*P.band_count : P.nband)) return;
     const int cell = band_cell[k];
     int x, y, z;
     decompose(P.g, cell, x, y, z);
@@ -212,12 +212,12 @@ __global__ void __launch_bounds__(256) k_ib_interp(long long S, long long nband,
 
 // spreading (Eq. 8) as a deterministic gather: band node k sums K g over the samples whose
 // base cell is x_k - c for the 8 corners c, in sample order (samples sorted by base cell)
-__global__ void __launch_bounds__(256) k_ib_spread(long long S, long long nband, const float *__restrict__ X,
-                                                   const float *__restrict__ g, const int *__restrict__ base_nbr,
-                                                   const int *__restrict__ cstart, const int *__restrict__ ccount,
-                                                   float *__restrict__ bandF) {
+__global__ void __launch_bounds__(256) k_ib_spread(long long S, long long nband, const int *__restrict__ count,
+                                                   const float *__restrict__ X, const float *__restrict__ g,
+                                                   const int *__restrict__ base_nbr, const int *__restrict__ cstart,
+                                                   const int *__restrict__ ccount, float *__restrict__ bandF) {
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= nband) return;
+    if (k >= (count ? (long long)*count : nband)) return;
     float fx = 0.0f, fy = 0.0f, fz = 0.0f;
 #pragma unroll 1
     for (int c = 0; c < 8; ++c) {
@@ -331,9 +331,9 @@ cudaError_t launch_ib_interp(long long S, long long nband, const float *X, const
     return cudaGetLastError();
 }
 
-cudaError_t launch_ib_spread(long long S, long long nband, const float *X, const float *g, const int *base_nbr,
-                             const int *cstart, const int *ccount, float *bandF, cudaStream_t st) {
-    k_ib_spread<<<blocks_for(nband, 256), 256, 0, st>>>(S, nband, X, g, base_nbr, cstart, ccount, bandF);
+cudaError_t launch_ib_spread(long long S, long long nband, const int *count, const float *X, const float *g,
+                             const int *base_nbr, const int *cstart, const int *ccount, float *bandF, cudaStream_t st) {
+    k_ib_spread<<<blocks_for(nband, 256), 256, 0, st>>>(S, nband, count, X, g, base_nbr, cstart, ccount, bandF);
     return cudaGetLastError();
 }
 

@@ -20,7 +20,7 @@ LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ETIMEOUT, LBM_ESTA
 STORAGE = {"f32": 0, "f16": 1, "bf16": 2}
 FACE = {"periodic": 0, "noslip": 1, "inlet": 2, "outlet": 3}
 COLLISION = {"acm": 0, "bgk": 1, "raw": 2}
-KERNEL_KINDS = ("step", "band", "interp", "spread", "boundary", "other", "tracer")
+KERNEL_KINDS = ("step", "band", "interp", "spread", "boundary", "other", "tracer", "motion")
 
 
 class LBMError(RuntimeError):
@@ -34,6 +34,11 @@ class lbm_config(C.Structure):
                 ("inlet_noise", C.c_double), ("seed", C.c_ulonglong), ("inflow_coef", C.c_double * 16),
                 ("omega_bulk", C.c_double), ("omega_hi", C.c_double * 4), ("cuda_stream", C.c_void_p),
                 ("collision", C.c_int)]
+
+
+class lbm_motion(C.Structure):
+    _fields_ = [("center", C.c_double * 3), ("velocity", C.c_double * 3), ("axis", C.c_double * 3),
+                ("omega", C.c_double)]
 
 
 class lbm_emitter(C.Structure):
@@ -65,6 +70,9 @@ _SIGS = {
     "lbm_profile": (C.c_int, [C.c_void_p, C.c_int]),
     "lbm_kernel_times": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
     "lbm_band_size": (C.c_longlong, [C.c_void_p]),
+    "lbm_set_motion": (C.c_int, [C.c_void_p, C.POINTER(lbm_motion)]),
+    "lbm_solid_samples": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "lbm_solid_torque": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "lbm_set_tracers": (C.c_int, [C.c_void_p, C.c_void_p, C.c_longlong, C.POINTER(lbm_emitter)]),
     "lbm_tracer_count": (C.c_longlong, [C.c_void_p]),
     "lbm_tracers": (C.c_int, [C.c_void_p, C.c_void_p]),
@@ -219,6 +227,27 @@ def lbm_band_size(h):
     return library().lbm_band_size(h)
 
 
+def lbm_set_motion(h, motion=None):
+    """motion = (center, velocity, axis, omega) or None (stop)."""
+    m = None
+    if motion is not None:
+        c, v, a, w = motion
+        m = lbm_motion((C.c_double * 3)(*c), (C.c_double * 3)(*v), (C.c_double * 3)(*a), float(w))
+    _check(library().lbm_set_motion(h, C.byref(m) if m is not None else None), h)
+
+
+def lbm_solid_samples(h, out):
+    p, k = _ptr(out)
+    _check(library().lbm_solid_samples(h, p), h)
+
+
+def lbm_solid_torque(h, center=None):
+    t = (C.c_double * 3)()
+    c = (C.c_double * 3)(*center) if center is not None else None
+    _check(library().lbm_solid_torque(h, c, t), h)
+    return np.array(t[:])
+
+
 def lbm_set_tracers(h, X, emitter=None):
     """X: (count, 3) positions (numpy or torch); emitter = (lo, hi, seed) or None."""
     count = 0 if X is None else int(np.prod(X.shape) // 3)
@@ -333,6 +362,18 @@ class Solver:
 
     def reductions(self):
         return lbm_reductions(self.h)
+
+    def set_motion(self, motion=None):
+        lbm_set_motion(self.h, motion)
+
+    def solid_samples(self, count):
+        """Current sample positions (count, 3), in the order given to set_solids."""
+        out = np.empty((count, 3), np.float32)
+        lbm_solid_samples(self.h, out)
+        return out
+
+    def torque(self, center=None):
+        return lbm_solid_torque(self.h, center)
 
     def set_tracers(self, X, emitter=None):
         lbm_set_tracers(self.h, X, emitter)
