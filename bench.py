@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-models", action="store_true", help="skip the BGK / raw-MRT comparison runs")
     ap.add_argument("--no-tracers", action="store_true", help="skip the smoke-tracer run")
+    ap.add_argument("--no-moving", action="store_true", help="skip the rotating-torus run")
     ap.add_argument("--tracers", type=int, default=4_000_000, help="smoke tracers of the tracer run")
     ap.add_argument("--adjoint-only", action="store_true", help="time only the adjoint workload")
     return ap.parse_args()
@@ -252,6 +253,36 @@ def tracer_run(torch, lbm, make, d, args, N, n_int, peak, world, steps):
             "density_ms": dens_ms, "density_grid": list(dims), "density_mass": mass}
 
 
+def moving_run(torch, lbm, Solver, args, peak, world):
+    """Rotating torus (53,280 samples, 400 x 200 x 400, tumbling about x): whole steps with
+    the per-step re-pose, re-sort and band rebuild of the moving solid."""
+    sc = scenes.scene_rotating_torus()
+    nx, ny, nz = sc["nx"], sc["ny"], sc["nz"]
+    N = nx * ny * nz
+    s = Solver(nx, ny, nz, sc["nu"], faces=sc["faces"])
+    s.set_state(sc["rho"], sc["u"])
+    s.set_solids(sc["samples"].astype(np.float32), sc["area"].astype(np.float32))
+    s.set_motion(sc["motion"])
+    s.step(args.warmup)
+    torch.cuda.synchronize()
+    steps = max(20, args.steps // 2)
+    ms, kt = timed_steps(s, steps, torch)
+    band = int(lbm.lbm_band_size(s.h))
+    torque = s.torque()
+    s.close()
+    torch.cuda.empty_cache()
+    k = kt["step"][0] / max(kt["step"][1], 1)
+    n_int = (nx - 64) * ny * nz
+    ach = 216 * n_int / (k * 1e-3) / 1e9
+    if not np.all(np.isfinite(torque)):
+        raise RuntimeError("non-finite torque in the rotating-torus run")
+    return {"workload": sc["name"], "samples": int(sc["samples"].shape[0]), "band_nodes": band,
+            "mlups": world * N / (ms / steps * 1e-3) / 1e6, "ms_per_step": ms / steps,
+            "kernel_ms_per_step": {kk: round(v[0] / steps, 4) for kk, v in kt.items() if v[1]},
+            "step_kernel_roofline": {"achieved": ach, "frac": ach / peak},
+            "torque": list(map(float, torque))}
+
+
 def timed_steps(solver, steps, torch):
     from paper_2101_11856_gb300 import lbm
     s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -395,6 +426,10 @@ def main():
     if not args.no_tracers:
         tracers = tracer_run(torch, lbm, make, d, args, N, n_int, peak, world, n_side)
 
+    moving = None
+    if not args.no_moving:
+        moving = moving_run(torch, lbm, Solver, args, peak, world)
+
     adjoint = None
     if not args.no_adjoint:
         adjoint = adjoint_cost(torch, args)
@@ -427,6 +462,7 @@ def main():
             "fp16": fp16,
             "collision_models": models,
             "tracers": tracers,
+            "moving_solid": moving,
             "adjoint": adjoint,
             "cpu_baseline": cpu,
             "checks": {"mass": mass, "drag": list(map(float, drag))},

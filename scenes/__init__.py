@@ -103,6 +103,22 @@ def fibonacci_sphere(center, radius: float, count: int):
     return pts, area
 
 
+def torus(center, R: float, r: float, spacing: float):
+    """Samples on a torus of major radius R and minor radius r about the z axis through
+    ``center``: a (theta, phi) grid with ~``spacing`` between neighbours on the outer
+    equator, each sample weighted by its patch area r (R + r cos phi) dtheta dphi."""
+    nt = max(3, int(round(2.0 * math.pi * (R + r) / spacing)))
+    nph = max(3, int(round(2.0 * math.pi * r / spacing)))
+    th = (np.arange(nt) + 0.5) * 2.0 * math.pi / nt
+    ph = (np.arange(nph) + 0.5) * 2.0 * math.pi / nph
+    T, P = np.meshgrid(th, ph, indexing="ij")
+    ring = R + r * np.cos(P)
+    pts = np.stack([ring * np.cos(T), ring * np.sin(T), r * np.sin(P)], axis=-1).reshape(-1, 3)
+    pts += np.asarray(center, dtype=np.float64)[None, :]
+    area = (r * ring * (2.0 * math.pi / nt) * (2.0 * math.pi / nph)).reshape(-1)
+    return pts, area
+
+
 def _face_lattice(u_lo, u_hi, v_lo, v_hi, spacing):
     nu_ = max(1, int(round((u_hi - u_lo) / spacing)))
     nv_ = max(1, int(round((v_hi - v_lo) / spacing)))
@@ -181,6 +197,18 @@ def scene_sphere_channel(nx=256, ny=128, nz=128, radius=16.0, count=3200, u_in=0
     return dict(name=f"sphere_channel_{nx}x{ny}x{nz}", nx=nx, ny=ny, nz=nz, nu=nu, rho=rho, u=u,
                 faces=("inlet", "outlet", "periodic", "periodic", "periodic", "periodic"),
                 samples=X, area=A, u_in=u_in, noise=noise)
+
+
+def scene_rotating_torus(nx=400, ny=200, nz=400, R=40.0, r=12.0, spacing=0.68, omega=0.0015, nu=1e-4):
+    """A torus tumbling about the x axis in still air (the rotating-torus scene of the
+    paper's Table 3: 400 x 200 x 400, about 53k samples): no-slip ground and top, periodic
+    x and z; tip speed omega (R + r) = 0.078."""
+    c = (nx / 2.0, ny / 2.0, nz / 2.0)
+    X, A = torus(c, R, r, spacing)
+    rho, u = uniform_flow(nx, ny, nz, (0.0, 0.0, 0.0))
+    return dict(name=f"rotating_torus_{nx}x{ny}x{nz}", nx=nx, ny=ny, nz=nz, nu=nu, rho=rho, u=u,
+                faces=("periodic", "periodic", "noslip", "noslip", "periodic", "periodic"), samples=X, area=A,
+                motion=(c, (0.0, 0.0, 0.0), (1.0, 0.0, 0.0), omega))
 
 
 def scene_box_city(nx=1200, ny=250, nz=840, n_boxes=200, side_range=(8, 24), u_in=0.08, nu=1e-4,
