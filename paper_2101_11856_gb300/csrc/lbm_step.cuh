@@ -151,6 +151,63 @@ __device__ __forceinline__ void store_yzface(const StepParams &P, int y, int z, 
     }
 }
 
+// ---- two nodes per thread (x and x + 32) for the main kernel -------------------------------
+// The address of each direction is formed once and serves both nodes through an immediate
+// offset of 32 elements, so a warp's accesses stay coalesced (32 consecutive nodes each).
+template <typename St, bool NB>
+__device__ __forceinline__ void load_interior2(const StepParams &P, int cell, bool two, float (&h0)[27],
+                                               float (&h1)[27]) {
+#pragma unroll
+    for (int d = 0; d < 27; ++d) {
+        const St *p = NB ? static_cast<const St *>(P.fp[opp(d)]) + (cell - (cy(d) * P.g.nx + cz(d) * P.g.nxy)) - cx(d)
+                         : static_cast<const St *>(P.fp[d]) + cell;
+        h0[d] = Store<St>::ld(p);
+        h1[d] = two ? Store<St>::ld(p + 32) : 0.0f;
+    }
+}
+
+template <typename St, bool NB>
+__device__ __forceinline__ void store_interior2(const StepParams &P, int cell, bool two, const float (&h0)[27],
+                                                const float (&h1)[27]) {
+#pragma unroll
+    for (int d = 0; d < 27; ++d) {
+        St *p = NB ? static_cast<St *>(P.fpo[d]) + (cell + (cy(d) * P.g.nx + cz(d) * P.g.nxy)) + cx(d)
+                   : static_cast<St *>(P.fpo[opp(d)]) + cell;
+        Store<St>::st(p, h0[d]);
+        if (two) Store<St>::st(p + 32, h1[d]);
+    }
+}
+
+template <typename St>
+__device__ __forceinline__ void load_yzface2(const StepParams &P, int y, int z, int cell, bool two, float (&h0)[27],
+                                             float (&h1)[27]) {
+    int off[9];
+    bool bb[9];
+    yz_rows<-1>(P.g, y, z, off, bb);
+#pragma unroll
+    for (int d = 0; d < 27; ++d) {
+        const St *p = bb[d / 3] ? static_cast<const St *>(P.fp[d]) + cell
+                                : static_cast<const St *>(P.fp[opp(d)]) + (cell + off[d / 3]) - cx(d);
+        h0[d] = Store<St>::ld(p);
+        h1[d] = two ? Store<St>::ld(p + 32) : 0.0f;
+    }
+}
+
+template <typename St>
+__device__ __forceinline__ void store_yzface2(const StepParams &P, int y, int z, int cell, bool two,
+                                              const float (&h0)[27], const float (&h1)[27]) {
+    int off[9];
+    bool bb[9];
+    yz_rows<+1>(P.g, y, z, off, bb);
+#pragma unroll
+    for (int d = 0; d < 27; ++d) {
+        St *p = bb[d / 3] ? static_cast<St *>(P.fpo[opp(d)]) + cell
+                          : static_cast<St *>(P.fpo[d]) + (cell + off[d / 3]) + cx(d);
+        Store<St>::st(p, h0[d]);
+        if (two) Store<St>::st(p + 32, h1[d]);
+    }
+}
+
 // ---- the edge strips: y/z faces per block, x faces per lane --------------------------------
 // The pull rules of load_general and the matching push rules, arranged for a block that covers one
 // strip of one (y, z) row: the y/z rows come from yz_rows (uniform), and only the lanes at
