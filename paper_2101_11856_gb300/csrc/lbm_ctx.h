@@ -180,6 +180,21 @@ inline lbm::StepParams make_params(const lbm_ctx *h, long long t) {
     P.r6 = (float)(1.0 - h->cfg.omega_hi[3]);
     P.q3 = (float)(1.0 - 0.5 * h->cfg.omega_hi[0]);
     P.q5 = (float)(1.0 - 0.5 * h->cfg.omega_hi[2]);
+    {
+        // coefficients of the scaled relaxation in collide_v (FP64 products, rounded once)
+        const double r0 = h->cfg.rho0, rs = 1.0 - ws, rb = 1.0 - h->cfg.omega_bulk;
+        const double r3 = 1.0 - h->cfg.omega_hi[0], r4 = 1.0 - h->cfg.omega_hi[1];
+        const double r5 = 1.0 - h->cfg.omega_hi[2], r6 = 1.0 - h->cfg.omega_hi[3];
+        const double q3 = 1.0 - 0.5 * h->cfg.omega_hi[0], q5 = 1.0 - 0.5 * h->cfg.omega_hi[2];
+        P.a2 = (float)(rs / 4); P.b2 = (float)(-(1 - rs) / 4 * r0);
+        P.tb6 = (float)(rb / 6); P.ts6 = (float)(rs / 6); P.r0h = (float)(r0 / 2);
+        P.a3 = (float)(r3 / 4); P.b3 = (float)((1 - r3) / 4 * r0); P.f3 = (float)(q3 / 3 / 4);
+        P.a3e = (float)(r3 / 8); P.b3e = (float)((1 - r3) / 8 * r0);
+        P.a4 = (float)(r4 / 4); P.b4r = (float)((1 - r4) / 4 / 9); P.b4u = (float)(-(1 - r4) / 4 * r0 / 3);
+        P.a4m = (float)(r4 / 8); P.b4m = (float)(-(1 - r4) / 8 * r0);
+        P.a5 = (float)(r5 / 8); P.b5 = (float)((1 - r5) / 8 * r0); P.f5 = (float)(q5 / 9 / 8);
+        P.a6 = (float)(r6 / 8); P.b6r = (float)((1 - r6) / 8 / 27); P.b6u = (float)(-(1 - r6) / 8 * r0);
+    }
     P.u_in = (float)h->cfg.u_in;
     P.noise = (float)h->cfg.inlet_noise;
     P.seed = h->cfg.seed;

@@ -72,6 +72,16 @@ struct StepParams {
     float rs, rb, r3, r4, r5, r6;   // 1 - omega of shear, bulk, orders 3..6
     float q3, q5;                // 1 - omega/2 of orders 3 and 5 (their force moments)
     float u_in, noise;           // inlet velocity and relative noise amplitude
+    // relaxation coefficients of the central-moment collision in the form
+    // sigma (rr h + (1 - rr) e + force), sigma = 2^-(number of nonzero indices): see collide_v
+    float a2, b2;                // shear off-diagonal: sigma 1/4, e = -rho0 u_a u_b
+    float tb6, ts6, r0h;         // trace / deviators: rb / 6, rs / 6; rho0 / 2
+    float a3, b3, f3;            // order 3 with force: sigma 1/4, e = rho0 u t; force q3 / 3
+    float a3e, b3e;              // kappa_111: sigma 1/8
+    float a4, b4r, b4u;          // kappa_220-type: sigma 1/4, e = rhop / 9 - rho0 / 3 (3 u2 v2 + u2 + v2)
+    float a4m, b4m;              // kappa_211-type: sigma 1/8, e = -rho0 t_a u_b u_c
+    float a5, b5, f5;            // order 5: sigma 1/8, e = rho0 u_c t_a t_b; force q5 / 9
+    float a6, b6r, b6u;          // kappa_222: sigma 1/8, e = rhop / 27 - rho0 (s1 / 9 + s2 / 3 + s3)
     unsigned long long seed;
     long long t;                 // index of the step being computed (1-based)
     const float *inlet_profile;  // [nyz] Fourier part of the inflow, or nullptr
@@ -156,9 +166,9 @@ template <typename V> __device__ __forceinline__ void raw3(V &a, V &b, V &c) {
 }
 // raw -> central moments about u
 template <typename V> __device__ __forceinline__ void shift3(V &m0, V &m1, V &m2, V u) {
-    const V t = vfma(u, m0, -2.0f * m1);
+    const V u2 = u * u, m2u = -2.0f * u;   // shared by the nine triplets of a sweep
+    m2 = vfma(u2, m0, vfma(m2u, m1, m2));
     m1 = vfma(-u, m0, m1);
-    m2 = vfma(u, t, m2);
 }
 // central moments about u -> populations
 template <typename V> __device__ __forceinline__ void inv3(V &m0, V &m1, V &m2, V u) {
@@ -169,6 +179,17 @@ template <typename V> __device__ __forceinline__ void inv3(V &m0, V &m1, V &m2, 
     m0 = vfma(0.5f, r2, -hr);
     m2 = vfma(0.5f, r2, hr);
     m1 = b;
+}
+
+// central moments about u -> populations, with the order-1 and order-2 moments given halved
+// (k0, k1 / 2, k2 / 2); hu = u / 2, tu = 2 u, u2h = u^2 / 2
+__device__ __forceinline__ void inv3h(float &m0, float &m1, float &m2, float hu, float tu, float u2h) {
+    const float r1h = fmaf(hu, m0, m1);                 // (k1 + u k0) / 2
+    const float R2 = fmaf(u2h, m0, fmaf(tu, m1, m2));   // (k2 + 2 u k1 + u^2 k0) / 2
+    const float k0 = m0;
+    m0 = R2 - r1h;
+    m2 = R2 + r1h;
+    m1 = fmaf(-2.0f, R2, k0);
 }
 
 // base index of the k-th triplet along the axis with stride S (1: x, 3: y, 9: z)
@@ -188,6 +209,11 @@ template <int S, typename V> __device__ __forceinline__ void sweep_inv(V (&h)[27
 #pragma unroll
     for (int k = 0; k < 9; ++k) inv3(h[tri_base<S>(k)], h[tri_base<S>(k) + S], h[tri_base<S>(k) + 2 * S], u);
 }
+template <int S> __device__ __forceinline__ void sweep_invh(float (&h)[27], float u, float u2) {
+    const float hu = 0.5f * u, tu = u + u, u2h = 0.5f * u2;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) inv3h(h[tri_base<S>(k)], h[tri_base<S>(k) + S], h[tri_base<S>(k) + 2 * S], hu, tu, u2h);
+}
 
 // ---- collision (Eqs. 4-5) ---------------------------------------------------------------
 // In: h = streamed deviations f*_i - w_i rho0 (tensor order), F = total force.
@@ -199,8 +225,11 @@ template <int S, typename V> __device__ __forceinline__ void sweep_inv(V (&h)[27
 // the diagonal second-order moments through their trace (omega_b) and two deviators
 // (omega_s).  The transform acts on the deviations h; the rest-weight part w rho0 has the
 // central moments rho0 t_p(u_x) t_q(u_y) t_r(u_z), t = (1, -u, 1/3 + u^2), so with
-// e = kappa_eq - rho0 t t t the update reads h' = e + (1 - omega)(h - e) + (1 - omega/2) R^F
-// in moment space, every term small; the e are expanded to avoid cancellation.
+// e = kappa_eq - rho0 t t t the update reads h' = rr h + (1 - rr) e + (1 - omega/2) R^F in
+// moment space (rr = 1 - omega), every term small; the e are expanded to avoid cancellation.
+// Each relaxed moment is stored multiplied by sigma = 2^-(number of nonzero indices), which the
+// inverse sweeps (inv3h) expect; the products of sigma with the rates come precomputed in the
+// launch parameters (make_params), so they cost no instructions here.
 template <typename V>
 __device__ __forceinline__ void collide_v(V (&h)[27], V Fx, V Fy, V Fz, const StepParams &P, V &rho, V &ux, V &uy,
                                           V &uz) {
@@ -217,67 +246,71 @@ __device__ __forceinline__ void collide_v(V (&h)[27], V Fx, V Fy, V Fz, const St
     sweep_shift<3>(h, uy);
     sweep_shift<9>(h, uz);
 
-    const float r0 = P.rho0;
     const V ux2 = ux * ux, uy2 = uy * uy, uz2 = uz * uz;
-    const float third = 1.0f / 3.0f, ninth = 1.0f / 9.0f;
+    const float third = 1.0f / 3.0f;
     const V tx = third + ux2, ty = third + uy2, tz = third + uz2;
+    const V uxy = ux * uy, uxz = ux * uz, uyz = uy * uz;
 
-    // order 1: conserved, kappa'_100 = F_x / 2  (stored as deviation moment rho0 u_x + F_x/2)
-    h[K(1, 0, 0)] = vfma(r0, ux, 0.5f * Fx);
-    h[K(0, 1, 0)] = vfma(r0, uy, 0.5f * Fy);
-    h[K(0, 0, 1)] = vfma(r0, uz, 0.5f * Fz);
+    // order 1: conserved, kappa'_100 = F_x / 2 (stored as deviation moment rho0 u_x + F_x/2), times 1/2
+    h[K(1, 0, 0)] = vfma(P.r0h, ux, 0.25f * Fx);
+    h[K(0, 1, 0)] = vfma(P.r0h, uy, 0.25f * Fy);
+    h[K(0, 0, 1)] = vfma(P.r0h, uz, 0.25f * Fz);
 
-#define RELAX(idx, e, r) { const V e_ = (e); h[idx] = vfma(vconst<V>(r), h[idx] - e_, e_); }
-#define RELAXF(idx, e, r, fr) { const V e_ = (e); h[idx] = vfma(vconst<V>(r), h[idx] - e_, e_ + (fr)); }
+    // sigma (rr h + (1 - rr) e + f) with A = sigma rr and B e_term = sigma (1 - rr) e
+#define RELAX(idx, A, Be) h[idx] = vfma(vconst<V>(A), h[idx], (Be))
     // order 2, off-diagonal (shear)
-    RELAX(K(1, 1, 0), -r0 * (ux * uy), P.rs);
-    RELAX(K(1, 0, 1), -r0 * (ux * uz), P.rs);
-    RELAX(K(0, 1, 1), -r0 * (uy * uz), P.rs);
-    // order 2, diagonal: trace (bulk) and two deviators (shear)
+    RELAX(K(1, 1, 0), P.a2, P.b2 * uxy);
+    RELAX(K(1, 0, 1), P.a2, P.b2 * uxz);
+    RELAX(K(0, 1, 1), P.a2, P.b2 * uyz);
+    // order 2, diagonal: trace (bulk) and two deviators (shear), times 1/2
     {
-        const V e200 = vfma(third, rhop, -r0 * ux2);
-        const V e020 = vfma(third, rhop, -r0 * uy2);
-        const V e002 = vfma(third, rhop, -r0 * uz2);
-        const V a = h[K(2, 0, 0)] - e200, b = h[K(0, 2, 0)] - e020, c = h[K(0, 0, 2)] - e002;
-        const V tr = P.rb * (a + b + c);
-        const V d1 = P.rs * (a - b);
-        const V d2 = P.rs * (a - c);
-        h[K(2, 0, 0)] = vfma(third, tr + d1 + d2, e200);
-        h[K(0, 2, 0)] = vfma(third, vfma(-2.0f, d1, tr + d2), e020);
-        h[K(0, 0, 2)] = vfma(third, vfma(-2.0f, d2, tr + d1), e002);
+        const V a = vfma(P.rho0, ux2, vfma(-third, rhop, h[K(2, 0, 0)]));   // kappa - e, e = rhop/3 - rho0 u^2
+        const V b = vfma(P.rho0, uy2, vfma(-third, rhop, h[K(0, 2, 0)]));
+        const V c = vfma(P.rho0, uz2, vfma(-third, rhop, h[K(0, 0, 2)]));
+        const V sixth_rhop = (0.5f * third) * rhop;
+        const V T = P.tb6 * (a + b + c);
+        const V D1 = P.ts6 * (a - b);
+        const V D2 = P.ts6 * (a - c);
+        const V TD1 = T + D1;
+        h[K(2, 0, 0)] = (TD1 + D2) + vfma(-P.r0h, ux2, sixth_rhop);
+        h[K(0, 2, 0)] = vfma(-2.0f, D1, T + D2) + vfma(-P.r0h, uy2, sixth_rhop);
+        h[K(0, 0, 2)] = vfma(-2.0f, D2, TD1) + vfma(-P.r0h, uz2, sixth_rhop);
     }
     // order 3 (force moments F/3 on 210, 201, 120, 021, 102, 012)
-    const float q3t = P.q3 * third, q5n = P.q5 * ninth;
-    RELAXF(K(2, 1, 0), r0 * (uy * tx), P.r3, q3t * Fy);
-    RELAXF(K(2, 0, 1), r0 * (uz * tx), P.r3, q3t * Fz);
-    RELAXF(K(1, 2, 0), r0 * (ux * ty), P.r3, q3t * Fx);
-    RELAXF(K(0, 2, 1), r0 * (uz * ty), P.r3, q3t * Fz);
-    RELAXF(K(1, 0, 2), r0 * (ux * tz), P.r3, q3t * Fx);
-    RELAXF(K(0, 1, 2), r0 * (uy * tz), P.r3, q3t * Fy);
-    RELAX(K(1, 1, 1), r0 * (ux * uy * uz), P.r3);
+    const V gx3 = P.f3 * Fx, gy3 = P.f3 * Fy, gz3 = P.f3 * Fz;
+    RELAX(K(2, 1, 0), P.a3, vfma(P.b3, uy * tx, gy3));
+    RELAX(K(2, 0, 1), P.a3, vfma(P.b3, uz * tx, gz3));
+    RELAX(K(1, 2, 0), P.a3, vfma(P.b3, ux * ty, gx3));
+    RELAX(K(0, 2, 1), P.a3, vfma(P.b3, uz * ty, gz3));
+    RELAX(K(1, 0, 2), P.a3, vfma(P.b3, ux * tz, gx3));
+    RELAX(K(0, 1, 2), P.a3, vfma(P.b3, uy * tz, gy3));
+    RELAX(K(1, 1, 1), P.a3e, P.b3e * (uxy * uz));
     // order 4
-    RELAX(K(2, 2, 0), vfma(ninth, rhop, -r0 * vfma(ux2, uy2, third * (ux2 + uy2))), P.r4);
-    RELAX(K(2, 0, 2), vfma(ninth, rhop, -r0 * vfma(ux2, uz2, third * (ux2 + uz2))), P.r4);
-    RELAX(K(0, 2, 2), vfma(ninth, rhop, -r0 * vfma(uy2, uz2, third * (uy2 + uz2))), P.r4);
-    RELAX(K(2, 1, 1), -r0 * (tx * (uy * uz)), P.r4);
-    RELAX(K(1, 2, 1), -r0 * (ty * (ux * uz)), P.r4);
-    RELAX(K(1, 1, 2), -r0 * (tz * (ux * uy)), P.r4);
+    {
+        const V x3 = 3.0f * ux2, y3 = 3.0f * uy2;
+        const V r4 = P.b4r * rhop;
+        RELAX(K(2, 2, 0), P.a4, vfma(P.b4u, vfma(x3, uy2, ux2 + uy2), r4));
+        RELAX(K(2, 0, 2), P.a4, vfma(P.b4u, vfma(x3, uz2, ux2 + uz2), r4));
+        RELAX(K(0, 2, 2), P.a4, vfma(P.b4u, vfma(y3, uz2, uy2 + uz2), r4));
+    }
+    RELAX(K(2, 1, 1), P.a4m, P.b4m * (tx * uyz));
+    RELAX(K(1, 2, 1), P.a4m, P.b4m * (ty * uxz));
+    RELAX(K(1, 1, 2), P.a4m, P.b4m * (tz * uxy));
     // order 5 (force moments F/9 on 221, 212, 122)
-    RELAXF(K(2, 2, 1), r0 * (uz * (tx * ty)), P.r5, q5n * Fz);
-    RELAXF(K(2, 1, 2), r0 * (uy * (tx * tz)), P.r5, q5n * Fy);
-    RELAXF(K(1, 2, 2), r0 * (ux * (ty * tz)), P.r5, q5n * Fx);
+    RELAX(K(2, 2, 1), P.a5, vfma(P.b5, uz * (tx * ty), P.f5 * Fz));
+    RELAX(K(2, 1, 2), P.a5, vfma(P.b5, uy * (tx * tz), P.f5 * Fy));
+    RELAX(K(1, 2, 2), P.a5, vfma(P.b5, ux * (ty * tz), P.f5 * Fx));
     // order 6
     {
         const V s1 = ux2 + uy2 + uz2;
-        const V s2 = ux2 * uy2 + ux2 * uz2 + uy2 * uz2;
+        const V s2 = vfma(ux2, uy2 + uz2, uy2 * uz2);
         const V s3 = ux2 * uy2 * uz2;
-        RELAX(K(2, 2, 2), vfma(1.0f / 27.0f, rhop, -r0 * vfma(ninth, s1, vfma(third, s2, s3))), P.r6);
+        RELAX(K(2, 2, 2), P.a6, vfma(P.b6u, vfma(1.0f / 9.0f, s1, vfma(third, s2, s3)), P.b6r * rhop));
     }
 #undef RELAX
-#undef RELAXF
-    sweep_inv<9>(h, uz);
-    sweep_inv<3>(h, uy);
-    sweep_inv<1>(h, ux);
+    sweep_invh<9>(h, uz, uz2);
+    sweep_invh<3>(h, uy, uy2);
+    sweep_invh<1>(h, ux, ux2);
 }
 
 __device__ __forceinline__ void collide(float (&h)[27], float Fx, float Fy, float Fz, const StepParams &P,

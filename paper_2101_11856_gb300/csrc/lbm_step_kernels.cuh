@@ -24,35 +24,54 @@ __device__ __forceinline__ void store_velocity(const StepParams &P, int cell, fl
 // ---- the fused step ---------------------------------------------------------------------
 // Pull the 27 streamed populations, add the body force and the band's immersed-boundary
 // force, collide in registers, store in place.  k_step_main updates the nodes
-// XEDGE <= x < nx - XEDGE, two per thread: one block row per (y, z), so a block's y/z face status is
+// XEDGE <= x < nx - XEDGE (two per thread for FP32): one block row per (y, z), so a block's y/z face status is
 // uniform (interior rows use constant offsets; face rows of odd steps use wrapped or bounced
 // rows; even steps address only the node's own slots).  k_step_edges updates the two edge
 // strips of each row with the general face rules (inlet, outlet, x wrap) in whole warps.
 // Every node is updated by exactly one of the two, and the two touch disjoint slots.
+// nodes per thread of the main kernel: two for FP32 storage (memory bound: the shared
+// addresses and the doubled bytes in flight pay), one for FP16 / BF16 (issue bound: the
+// lower register count keeps twice the warps resident)
+template <typename St> __host__ __device__ constexpr int main_nodes() { return sizeof(St) == 4 ? 2 : 1; }
+
 template <typename St, bool NB, bool BAND, int COLL, bool VOUT>
 __global__ void __launch_bounds__(STEP_BX) k_step_main(StepParams P) {
-    // a block covers 2 STEP_BX nodes of a row; warp w, lane l: nodes 64 w + l and 64 w + l + 32
-    const int x = blockIdx.x * (2 * STEP_BX) + (threadIdx.x >> 5) * 64 + (threadIdx.x & 31) + XEDGE;
-    const int xend = P.g.nx - XEDGE;
-    if (x >= xend) return;
-    const bool two = x + 32 < xend;
     const int y = blockIdx.y, z = blockIdx.z;
-    const int cell = x + P.g.nx * (y + P.g.ny * z);
     const bool inner = y >= 1 && y <= P.g.ny - 2 && z >= 1 && z <= P.g.nz - 2;   // uniform per block
-    float h0[27], h1[27];
-    if (!NB || inner) load_interior2<St, NB>(P, cell, two, h0, h1);
-    else load_yzface2<St>(P, y, z, cell, two, h0, h1);
+    const int xend = P.g.nx - XEDGE;
     float Fx, Fy, Fz, rho, ux, uy, uz;
-    band_force<BAND>(P, cell, Fx, Fy, Fz);
-    collide_model<COLL>(h0, Fx, Fy, Fz, P, rho, ux, uy, uz);
-    if (VOUT) store_velocity(P, cell, ux, uy, uz);
-    if (two) {
-        band_force<BAND>(P, cell + 32, Fx, Fy, Fz);
-        collide_model<COLL>(h1, Fx, Fy, Fz, P, rho, ux, uy, uz);
-        if (VOUT) store_velocity(P, cell + 32, ux, uy, uz);
+    if constexpr (main_nodes<St>() == 2) {
+        // a block covers 2 STEP_BX nodes of a row; warp w, lane l: nodes 64 w + l and 64 w + l + 32
+        const int x = blockIdx.x * (2 * STEP_BX) + (threadIdx.x >> 5) * 64 + (threadIdx.x & 31) + XEDGE;
+        if (x >= xend) return;
+        const bool two = x + 32 < xend;
+        const int cell = x + P.g.nx * (y + P.g.ny * z);
+        float h0[27], h1[27];
+        if (!NB || inner) load_interior2<St, NB>(P, cell, two, h0, h1);
+        else load_yzface2<St>(P, y, z, cell, two, h0, h1);
+        band_force<BAND>(P, cell, Fx, Fy, Fz);
+        collide_model<COLL>(h0, Fx, Fy, Fz, P, rho, ux, uy, uz);
+        if (VOUT) store_velocity(P, cell, ux, uy, uz);
+        if (two) {
+            band_force<BAND>(P, cell + 32, Fx, Fy, Fz);
+            collide_model<COLL>(h1, Fx, Fy, Fz, P, rho, ux, uy, uz);
+            if (VOUT) store_velocity(P, cell + 32, ux, uy, uz);
+        }
+        if (!NB || inner) store_interior2<St, NB>(P, cell, two, h0, h1);
+        else store_yzface2<St>(P, y, z, cell, two, h0, h1);
+    } else {
+        const int x = blockIdx.x * STEP_BX + threadIdx.x + XEDGE;
+        if (x >= xend) return;
+        const int cell = x + P.g.nx * (y + P.g.ny * z);
+        float h[27];
+        if (!NB || inner) load_interior<St, NB>(P, cell, h);
+        else load_yzface<St>(P, y, z, cell, h);
+        band_force<BAND>(P, cell, Fx, Fy, Fz);
+        collide_model<COLL>(h, Fx, Fy, Fz, P, rho, ux, uy, uz);
+        if (!NB || inner) store_interior<St, NB>(P, cell, h);
+        else store_yzface<St>(P, y, z, cell, h);
+        if (VOUT) store_velocity(P, cell, ux, uy, uz);
     }
-    if (!NB || inner) store_interior2<St, NB>(P, cell, two, h0, h1);
-    else store_yzface2<St>(P, y, z, cell, two, h0, h1);
 }
 
 // one warp per edge strip of one row, EDGE_ROWS rows (y) per block: blockIdx.y * EDGE_ROWS +
@@ -102,7 +121,7 @@ cudaError_t launch_step_tt(const StepParams &P, int part, cudaStream_t st) {
             k_step_rows<St, NB, BAND, COLL, VOUT><<<grid, block, 0, st>>>(P);
         }
     } else if (has_interior(g)) {
-        const dim3 grid(step_blocks(g.nx - 2 * XEDGE, 2 * STEP_BX), g.ny, g.nz);
+        const dim3 grid(step_blocks(g.nx - 2 * XEDGE, main_nodes<St>() * STEP_BX), g.ny, g.nz);
         k_step_main<St, NB, BAND, COLL, VOUT><<<grid, STEP_BX, 0, st>>>(P);
     }
     return cudaGetLastError();
