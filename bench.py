@@ -31,7 +31,7 @@ BYTES_PER_CELL = {"f32": 216, "f16": 108, "bf16": 108}   # 27 loads + 27 stores 
 PAPER_MLUPS = 1200 * 250 * 840 / 1.21 / 1e6                # Table 3, Fig. 1 scene: 1.21 s/step on 4x P40
 # DRAM bytes per cell of k_step_main (FP32) from one ncu capture of the current kernel
 # (profiles/k_step_main_box_city_480x100x336.md); None once the kernel changes
-TRAFFIC_PER_CELL = {"f32": 215.97}
+TRAFFIC_PER_CELL = {"f32": 215.8}
 
 
 def parse():
