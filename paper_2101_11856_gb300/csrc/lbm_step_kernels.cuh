@@ -41,8 +41,8 @@ __global__ void __launch_bounds__(STEP_BX) k_step_main(StepParams P) {
     const int xend = P.g.nx - XEDGE;
     float Fx, Fy, Fz, rho, ux, uy, uz;
     if constexpr (main_nodes<St>() == 2) {
-        // a block covers 2 STEP_BX nodes of a row; warp w, lane l: nodes 64 w + l and 64 w + l + 32
-        const int x = blockIdx.x * (2 * STEP_BX) + (threadIdx.x >> 5) * 64 + (threadIdx.x & 31) + XEDGE;
+        // a block covers 2 blockDim.x nodes of a row; warp w, lane l: nodes 64 w + l and 64 w + l + 32
+        const int x = blockIdx.x * (2 * blockDim.x) + (threadIdx.x >> 5) * 64 + (threadIdx.x & 31) + XEDGE;
         if (x >= xend) return;
         const bool two = x + 32 < xend;
         const int cell = x + P.g.nx * (y + P.g.ny * z);
@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(STEP_BX) k_step_main(StepParams P) {
         if (!NB || inner) store_interior2<St, NB>(P, cell, two, h0, h1);
         else store_yzface2<St>(P, y, z, cell, two, h0, h1);
     } else {
-        const int x = blockIdx.x * STEP_BX + threadIdx.x + XEDGE;
+        const int x = blockIdx.x * blockDim.x + threadIdx.x + XEDGE;
         if (x >= xend) return;
         const int cell = x + P.g.nx * (y + P.g.ny * z);
         float h[27];
@@ -121,8 +121,12 @@ cudaError_t launch_step_tt(const StepParams &P, int part, cudaStream_t st) {
             k_step_rows<St, NB, BAND, COLL, VOUT><<<grid, block, 0, st>>>(P);
         }
     } else if (has_interior(g)) {
-        const dim3 grid(step_blocks(g.nx - 2 * XEDGE, main_nodes<St>() * STEP_BX), g.ny, g.nz);
-        k_step_main<St, NB, BAND, COLL, VOUT><<<grid, STEP_BX, 0, st>>>(P);
+        // one warp per block when a row's main range fits in one warp's nodes (short rows would
+        // leave the second warp idle)
+        const int range = g.nx - 2 * XEDGE, per_warp = 32 * main_nodes<St>();
+        const int threads = range <= per_warp ? 32 : STEP_BX;
+        const dim3 grid(step_blocks(range, main_nodes<St>() * threads), g.ny, g.nz);
+        k_step_main<St, NB, BAND, COLL, VOUT><<<grid, threads, 0, st>>>(P);
     }
     return cudaGetLastError();
 }
