@@ -277,6 +277,11 @@ int lbm_tracer_dims(const lbm_ctx *h, int s, int dims[3]);
  * voxels), LBM_ENOMEM (workspace: 4 bytes per voxel, 8 with a host out). */
 int lbm_tracer_density(lbm_ctx *h, int s, float *out);
 
+/* Replace the 16 inflow-profile coefficients a_mn (layout of lbm_config.inflow_coef) of a
+ * context whose -x face is an inlet; takes effect from the next step (lbm_step, lbm_adjoint).
+ * Errors: LBM_EINVAL (no inlet, NULL or non-finite coef), LBM_ENOMEM. */
+int lbm_set_inflow(lbm_ctx *h, const double coef[16]);
+
 /* Number of band nodes (nodes within the 2x2x2 stencil of a sample) of the solid. */
 long long lbm_band_size(const lbm_ctx *h);
 

@@ -5,6 +5,6 @@ The compute path is the C-ABI CUDA library ``liblbm.so`` (sources in ``csrc/``, 
 ``include/lbm.h``); ``lbm`` is its thin ctypes binding.  Build with ``build.build()``.
 """
 from . import lbm
-from .lbm import Solver, LBMError
+from .lbm import Solver, LBMError, LBMSolve, lbm_solve
 
-__all__ = ["lbm", "Solver", "LBMError"]
+__all__ = ["lbm", "Solver", "LBMError", "LBMSolve", "lbm_solve"]

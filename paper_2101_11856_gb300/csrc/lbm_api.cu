@@ -66,6 +66,29 @@ template <typename T> int upload(lbm_ctx *h, T **dst, const std::vector<T> &src)
     return LBM_OK;
 }
 
+// the Fourier part of the inflow profile on the inlet nodes, from h->cfg.inflow_coef (freed
+// when every coefficient is zero or there is no inlet)
+int upload_inflow(lbm_ctx *h) {
+    const lbm_config &c = h->cfg;
+    bool any_coef = false;
+    for (int k = 0; k < 16; ++k) any_coef |= c.inflow_coef[k] != 0.0;
+    if (h->f) cudaStreamSynchronize(h->stream);
+    dev_free(h->inlet_profile);
+    if (!any_coef || c.face_type[0] != LBM_FACE_INLET) return LBM_OK;
+    const int ny = h->ny, nz = h->nz;
+    std::vector<float> prof((size_t)ny * nz);
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y) {
+            double v = 0.0;
+            for (int m = 1; m <= 4; ++m)
+                for (int n = 1; n <= 4; ++n)
+                    v += c.inflow_coef[(m - 1) * 4 + (n - 1)] * std::sin(m * M_PI * (y + 0.5) / ny) *
+                         std::sin(n * M_PI * (z + 0.5) / nz);
+            prof[y + (size_t)ny * z] = (float)v;
+        }
+    return upload(h, &h->inlet_profile, prof);
+}
+
 int require_state(lbm_ctx *h) {
     if (!h) return fail(nullptr, LBM_EINVAL, "null context");
     if (!h->has_state) return fail(h, LBM_ESTATE, "lbm_set_state (or lbm_load) has not been called");
@@ -151,21 +174,7 @@ int lbm_create(lbm_ctx **out, int nx, int ny, int nz, double nu, const double fo
             return bail(LBM_ENOMEM);
         }
     }
-    bool any_coef = false;
-    for (int k = 0; k < 16; ++k) any_coef |= c.inflow_coef[k] != 0.0;
-    if (any_coef && c.face_type[0] == LBM_FACE_INLET) {
-        std::vector<float> prof((size_t)ny * nz);
-        for (int z = 0; z < nz; ++z)
-            for (int y = 0; y < ny; ++y) {
-                double v = 0.0;
-                for (int m = 1; m <= 4; ++m)
-                    for (int n = 1; n <= 4; ++n)
-                        v += c.inflow_coef[(m - 1) * 4 + (n - 1)] * std::sin(m * M_PI * (y + 0.5) / ny) *
-                             std::sin(n * M_PI * (z + 0.5) / nz);
-                prof[y + (size_t)ny * z] = (float)v;
-            }
-        if (upload(h, &h->inlet_profile, prof) != LBM_OK) return bail(LBM_ENOMEM);
-    }
+    if (upload_inflow(h) != LBM_OK) return bail(LBM_ENOMEM);
     if (dev_alloc(h, &h->red, 8) != LBM_OK || dev_alloc(h, &h->flag, 1) != LBM_OK) return bail(LBM_ENOMEM);
     *out = h;
     return LBM_OK;
@@ -461,6 +470,19 @@ int lbm_velocity(int i, int c[3]) {
 }
 
 long long lbm_time(const lbm_ctx *h) { return h ? h->t : -1; }
+
+int lbm_set_inflow(lbm_ctx *h, const double coef[16]) {
+    if (!h) return fail(nullptr, LBM_EINVAL, "null context");
+    if (!coef) return fail(h, LBM_EINVAL, "coef is NULL");
+    if (h->cfg.face_type[0] != LBM_FACE_INLET) return fail(h, LBM_EINVAL, "the -x face is not an inlet");
+    for (int k = 0; k < 16; ++k)
+        if (!std::isfinite(coef[k])) return fail(h, LBM_EINVAL, "non-finite inflow coefficient");
+    for (int k = 0; k < 16; ++k) h->cfg.inflow_coef[k] = coef[k];
+    int rc = upload_inflow(h);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
 
 long long lbm_band_size(const lbm_ctx *h) {
     if (!h) return -1;

@@ -70,6 +70,7 @@ _SIGS = {
     "lbm_profile": (C.c_int, [C.c_void_p, C.c_int]),
     "lbm_kernel_times": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
     "lbm_band_size": (C.c_longlong, [C.c_void_p]),
+    "lbm_set_inflow": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     "lbm_set_motion": (C.c_int, [C.c_void_p, C.POINTER(lbm_motion)]),
     "lbm_solid_samples": (C.c_int, [C.c_void_p, C.c_void_p]),
     "lbm_solid_torque": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
@@ -225,6 +226,11 @@ def lbm_kernel_times(h):
 
 def lbm_band_size(h):
     return library().lbm_band_size(h)
+
+
+def lbm_set_inflow(h, coef):
+    c = (C.c_double * 16)(*[float(v) for v in np.asarray(coef, dtype=np.float64).ravel()])
+    _check(library().lbm_set_inflow(h, c), h)
 
 
 def lbm_set_motion(h, motion=None):
@@ -405,6 +411,59 @@ class Solver:
     def adjoint(self, n, K=20, w_drag=1.0, w_ke=0.0, ke_x0=0, ke_x1=0, count=0):
         return lbm_adjoint(self.h, n, K, w_drag, w_ke, ke_x0, ke_x1, count)
 
+    def set_inflow(self, coef):
+        lbm_set_inflow(self.h, coef)
+
     @property
     def time(self):
         return lbm_time(self.h)
+
+
+# ---- autograd ------------------------------------------------------------------------
+
+def _autograd_function():
+    import torch
+
+    class LBMSolve(torch.autograd.Function):
+        """L(a, X) of n solver steps as a differentiable function of the 16 inflow coefficients a
+        and the sample positions X (count, 3).  forward sets a, the samples and the initial
+        state (rho0, u0), then runs lbm_adjoint (n steps with checkpoints every K, loss and
+        both gradients in one pass); backward returns grad_L times the stored gradients.
+        The solver must have an inlet on -x and is left at the state after the n steps."""
+
+        @staticmethod
+        def forward(ctx, coef, X, solver, rho0, u0, n, K, w_drag, w_ke, ke_x0, ke_x1, area):
+            solver.set_inflow(coef.detach().double().cpu().numpy())
+            Xf = X.detach().to(torch.float32).contiguous()
+            solver.set_solids(Xf, area)
+            solver.set_state(rho0, u0)
+            L, dcoef, dpos = solver.adjoint(n, K, w_drag, w_ke, ke_x0, ke_x1, Xf.shape[0])
+            ctx.save_for_backward(torch.as_tensor(dcoef, dtype=coef.dtype, device=coef.device),
+                                  torch.as_tensor(dpos, dtype=X.dtype, device=X.device))
+            return torch.tensor(L, dtype=torch.float64, device=coef.device)
+
+        @staticmethod
+        def backward(ctx, grad_L):
+            dcoef, dpos = ctx.saved_tensors
+            g = grad_L.to(torch.float64)
+            return ((g * dcoef.double()).to(dcoef.dtype), (g * dpos.double()).to(dpos.dtype),
+                    None, None, None, None, None, None, None, None, None, None)
+
+    return LBMSolve
+
+
+_LBMSolve = None
+
+
+def LBMSolve():
+    """The torch.autograd.Function class (created on first use, so importing this module does
+    not import torch)."""
+    global _LBMSolve
+    if _LBMSolve is None:
+        _LBMSolve = _autograd_function()
+    return _LBMSolve
+
+
+def lbm_solve(coef, X, solver, rho0, u0, n, K=20, w_drag=1.0, w_ke=0.0, ke_x0=0, ke_x1=0, area=None):
+    """Differentiable loss of n steps (see LBMSolve): coef (16,) and X (count, 3) torch tensors."""
+    return LBMSolve().apply(coef, X, solver, rho0, u0, n, K, w_drag, w_ke, ke_x0, ke_x1, area)
