@@ -101,3 +101,39 @@ def test_adjoint_advances_state_like_forward_steps():
     b.step(7)
     assert np.array_equal(a.populations(), b.populations())
     assert np.allclose(a.reductions()[2], b.reductions()[2], rtol=0, atol=0)
+
+
+@pytest.mark.parametrize("K", [4, 2])
+def test_long_rows_main_and_edge_kernels(K):
+    """nx >= 65: the backward step runs the main kernel (32 <= x < nx - 32) and the two edge
+    strips, the layout of the 128^3 benchmark, against the oracle; the sphere lies in the main
+    range, the kinetic-energy slab next to the inlet (so that the inflow coefficients reach the
+    loss within the 6 steps)."""
+    nx, ny, nz = 70, 6, 5
+    faces = ("inlet", "outlet", "noslip", "noslip", "periodic", "periodic")
+    X, A = scenes.fibonacci_sphere((37.4, 2.6, 2.3), 1.6, 30)
+    rho, u = scenes.uniform_flow(nx, ny, nz, (0.04, 0, 0))
+    coef = np.random.default_rng(3).uniform(-0.004, 0.004, 16)
+    loss = Loss(1.0, 1.5, 1, 5)
+    s, (Lg, dcg, dxg), (Lo, dco, dxo) = run_both(nx, ny, nz, 0.04, 6, K, loss, faces, rho, u, X, A, coef=coef,
+                                                 u_in=0.04, noise=0.01,
+                                                 rates=dict(omega_bulk=1.2, omega_hi=(1.1, 0.95, 1.3, 1.05)))
+    print(f"nx=70 K={K}: L {Lg:.6e} vs {Lo:.6e}; rel dtheta {rel_l2(dcg, dco.numpy()):.2e}; "
+          f"rel dX {rel_l2(dxg, dxo.numpy()):.2e}")
+    assert abs(Lg - Lo) <= 1e-5 * abs(Lo)
+    assert np.abs(dco.numpy()).max() > 0 and np.abs(dxo.numpy()).max() > 0
+    assert rel_l2(dcg, dco.numpy()) <= 1e-3
+    assert rel_l2(dxg, dxo.numpy()) <= 1e-3
+
+
+def test_long_rows_periodic_box():
+    nx, ny, nz = 72, 6, 6
+    rho, u = scenes.taylor_green(nx, ny, nz, 0.04)
+    X, A = scenes.fibonacci_sphere((33.3, 3.1, 2.8), 1.8, 30)
+    ub = np.tile([0.01, 0.0, -0.004], (30, 1))
+    loss = Loss(1.0, 0.7, 30, 42)
+    s, (Lg, dcg, dxg), (Lo, dco, dxo) = run_both(nx, ny, nz, 0.03, 5, 3, loss, ("periodic",) * 6, rho, u, X, A, ub,
+                                                 forcing=(1e-5, 0, -1e-5))
+    print(f"nx=72 periodic: L {Lg:.6e} vs {Lo:.6e}; rel dX {rel_l2(dxg, dxo.numpy()):.2e}")
+    assert abs(Lg - Lo) <= 1e-5 * abs(Lo)
+    assert rel_l2(dxg, dxo.numpy()) <= 1e-3
