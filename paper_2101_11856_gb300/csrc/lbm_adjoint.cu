@@ -399,7 +399,10 @@ __global__ void __launch_bounds__(STEP_BX) k_adj_main(StepParams P, AdjParams A)
 }
 
 // push of mu from an edge-strip node: interior rows use constant row offsets, face rows the
-// wrapped / bounced rows; the x-face lane applies the x rule of its face
+// wrapped / bounced rows.  Every lane pushes in the same instruction stream: a direction whose
+// source lies across the x face of the lane's side is redirected by address selection (x wrap,
+// the node's own slot for no-slip and inlet, no write for the outlet ghost, whose use goes to
+// the duplicate buffer for k_adj_outlet); the face type of a side is uniform.
 template <bool INNER, int SIDE>
 __device__ __forceinline__ void adj_push_edge(const StepParams &P, const AdjParams &A, int x, int y, int z, int cell,
                                               const float (&lam)[27]) {
@@ -408,31 +411,31 @@ __device__ __forceinline__ void adj_push_edge(const StepParams &P, const AdjPara
     bool bb[9];
     row_offsets<-1, INNER>(P.g, y, z, off, bb);
     const bool xlo = SIDE != 1 && x == 0, xhi = SIDE != 0 && x == P.g.nx - 1;
-    const bool outlet_node = xhi && P.g.face[1] == FACE_OUTLET;
-    double sth = 0.0;
+    const int flo = P.g.face[0], fhi = P.g.face[1];
+    const bool outlet_node = xhi && fhi == FACE_OUTLET;
+    float sth = 0.0f;   // this node's inflow sensitivity (accumulated over steps in FP64)
 #pragma unroll
     for (int d = 0; d < 27; ++d) {
         const int j = d / 3;
         const float mu = lam[d];
-        bool ghost = false;
-        if (bb[j]) {
+        if (bb[j]) {                         // uniform per warp: the row crosses a no-slip y/z face
             A.lam_prev[opp(d) * N + cell] = mu;
-        } else if (cx(d) == 0 || !(cx(d) == 1 ? xlo : xhi)) {
-            A.lam_prev[d * N + cell + off[j] - cx(d)] = mu;
-        } else {
-            const int ft = P.g.face[cx(d) == 1 ? 0 : 1];
-            if (ft == FACE_PERIODIC) {
-                A.lam_prev[d * N + cell + off[j] + cx(d) * (P.g.nx - 1)] = mu;
-            } else if (ft == FACE_OUTLET) {
-                ghost = true;
-            } else {
-                A.lam_prev[opp(d) * N + cell] = mu;
-                if (ft == FACE_INLET) sth += (double)mu * (6.0 * wgt(d) * P.rho0 * cx(d));
-            }
+            if (outlet_node && cx(d) == -1) A.blam[(long long)j * P.g.nyz + y + P.g.ny * z] = 0.0f;
+            continue;
         }
+        bool xc = false;
+        int ft = FACE_PERIODIC;
+        if (cx(d) == 1) { xc = xlo; ft = flo; }
+        if (cx(d) == -1) { xc = xhi; ft = fhi; }
+        const bool own = xc && (ft == FACE_NOSLIP || ft == FACE_INLET);
+        const bool ghost = xc && ft == FACE_OUTLET;
+        const long long idx = own ? (long long)opp(d) * N + cell
+                                  : (long long)d * N + cell + off[j] + (xc ? cx(d) * (P.g.nx - 1) : -cx(d));
+        if (!ghost) A.lam_prev[idx] = mu;
+        if (cx(d) == 1 && xc && ft == FACE_INLET) sth = fmaf(mu, 6.0f * wgt(d) * P.rho0, sth);
         if (outlet_node && cx(d) == -1) A.blam[(long long)j * P.g.nyz + y + P.g.ny * z] = ghost ? mu : 0.0f;
     }
-    if (xlo && P.g.face[0] == FACE_INLET) A.s_inlet[y + P.g.ny * z] += sth;
+    if (xlo && flo == FACE_INLET) A.s_inlet[y + P.g.ny * z] += (double)sth;
 }
 
 // Backward step of the edge strips (one warp per strip and row, EDGE_ROWS rows per block; the
