@@ -170,17 +170,6 @@ template <typename V> __device__ __forceinline__ void shift3(V &m0, V &m1, V &m2
     m2 = vfma(u2, m0, vfma(m2u, m1, m2));
     m1 = vfma(-u, m0, m1);
 }
-// central moments about u -> populations
-template <typename V> __device__ __forceinline__ void inv3(V &m0, V &m1, V &m2, V u) {
-    const V r1 = vfma(u, m0, m1);
-    const V r2 = vfma(u, m1 + r1, m2);
-    const V hr = 0.5f * r1;
-    const V b = m0 - r2;
-    m0 = vfma(0.5f, r2, -hr);
-    m2 = vfma(0.5f, r2, hr);
-    m1 = b;
-}
-
 // central moments about u -> populations, with the order-1 and order-2 moments given halved
 // (k0, k1 / 2, k2 / 2); hu = u / 2, tu = 2 u, u2h = u^2 / 2
 __device__ __forceinline__ void inv3h(float &m0, float &m1, float &m2, float hu, float tu, float u2h) {
@@ -204,10 +193,6 @@ template <int S, typename V> __device__ __forceinline__ void sweep_raw(V (&h)[27
 template <int S, typename V> __device__ __forceinline__ void sweep_shift(V (&h)[27], V u) {
 #pragma unroll
     for (int k = 0; k < 9; ++k) shift3(h[tri_base<S>(k)], h[tri_base<S>(k) + S], h[tri_base<S>(k) + 2 * S], u);
-}
-template <int S, typename V> __device__ __forceinline__ void sweep_inv(V (&h)[27], V u) {
-#pragma unroll
-    for (int k = 0; k < 9; ++k) inv3(h[tri_base<S>(k)], h[tri_base<S>(k) + S], h[tri_base<S>(k) + 2 * S], u);
 }
 template <int S> __device__ __forceinline__ void sweep_invh(float (&h)[27], float u, float u2) {
     const float hu = 0.5f * u, tu = u + u, u2h = 0.5f * u2;
