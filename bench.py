@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-moving", action="store_true", help="skip the rotating-torus run")
     ap.add_argument("--tracers", type=int, default=4_000_000, help="smoke tracers of the tracer run")
     ap.add_argument("--adjoint-only", action="store_true", help="time only the adjoint workload")
+    ap.add_argument("--adjoint-steps", type=int, default=200, help="steps of the adjoint workload")
+    ap.add_argument("--adjoint-k", type=int, default=20, help="checkpoint interval of the adjoint workload")
     return ap.parse_args()
 
 
@@ -169,10 +171,11 @@ def run_reference(args):
 def adjoint_cost(torch, args):
     """Adjoint workload: 128^3 channel, IB sphere r = 12.6 at (40, 64, 64) with 2,000 samples,
     200 steps, loss = mean drag + kinetic energy of the slab 96 <= x < 128, checkpoints every
-    20 steps.  Reports the adjoint (forward + backward) time against 200 forward steps."""
+    20 steps (--adjoint-steps / --adjoint-k change the last two, for small profiling runs).
+    Reports the adjoint (forward + backward) time against the same number of forward steps."""
     from paper_2101_11856_gb300 import Solver
     n = max(8, int(round(128 * args.scale))) if args.scale < 1.0 else 128
-    steps, K = 200, 20
+    steps, K = args.adjoint_steps, args.adjoint_k
     X, A = scenes.fibonacci_sphere((40.0 * n / 128, n / 2, n / 2), 12.6 * n / 128, 2000)
     rho, u = scenes.uniform_flow(n, n, n, (0.05, 0, 0))
     faces = ("inlet", "outlet", "periodic", "periodic", "periodic", "periodic")
