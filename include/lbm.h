@@ -44,6 +44,11 @@ extern "C" {
 #define LBM_FACE_NOSLIP   1  /* half-way bounce-back (the paper's Algorithm 1)             */
 #define LBM_FACE_INLET    2  /* -x only: moving-wall bounce-back at u_in(y, z, t)          */
 #define LBM_FACE_OUTLET   3  /* +x only: zero-gradient ghost layer                         */
+#define LBM_FACE_FREESLIP 4  /* y and z faces only: half-way specular reflection (the
+                                population from the tangential neighbour, its normal
+                                component reversed); no-slip and the inlet win at edges,
+                                the outlet ghost is read at the mirrored source; not
+                                covered by lbm_adjoint (LBM_EINVAL)                        */
 
 typedef struct lbm_ctx lbm_ctx;
 

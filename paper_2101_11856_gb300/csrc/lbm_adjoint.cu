@@ -387,9 +387,9 @@ __global__ void __launch_bounds__(STEP_BX) k_adj_main(StepParams P, AdjParams A)
         for (int d = 0; d < 27; ++d)
             A.lam_prev[d * N + cell - (cx(d) + cy(d) * P.g.nx + cz(d) * P.g.nxy)] = lam[d];
     } else {
-        int off[9];
+        int off[9], mir[9];
         bool bb[9];
-        yz_rows<-1>(P.g, y, z, off, bb);
+        yz_rows<-1>(P.g, y, z, off, bb, mir);   // free-slip faces are rejected by lbm_adjoint
 #pragma unroll
         for (int d = 0; d < 27; ++d) {
             if (bb[d / 3]) A.lam_prev[opp(d) * N + cell] = lam[d];
@@ -407,9 +407,9 @@ template <bool INNER, int SIDE>
 __device__ __forceinline__ void adj_push_edge(const StepParams &P, const AdjParams &A, int x, int y, int z, int cell,
                                               const float (&lam)[27]) {
     const long long N = P.g.ncell;
-    int off[9];
+    int off[9], mir[9];
     bool bb[9];
-    row_offsets<-1, INNER>(P.g, y, z, off, bb);
+    row_offsets<-1, INNER>(P.g, y, z, off, bb, mir);   // free-slip faces are rejected by lbm_adjoint
     const bool xlo = SIDE != 1 && x == 0, xhi = SIDE != 0 && x == P.g.nx - 1;
     const int flo = P.g.face[0], fhi = P.g.face[1];
     const bool outlet_node = xhi && fhi == FACE_OUTLET;
@@ -576,6 +576,8 @@ extern "C" int lbm_adjoint(lbm_ctx *h, int n, int K, const lbm_loss *loss, doubl
     if (n < 1 || !loss) return fail(h, LBM_EINVAL, "n must be >= 1 and loss given");
     if (h->cfg.collision != LBM_COLL_ACM) return fail(h, LBM_EINVAL, "the adjoint exists for the ACM-MRT collision only");
     if (h->band_count_dev) return fail(h, LBM_EINVAL, "the adjoint exists for static solids only (lbm_set_motion was called)");
+    for (int k = 2; k < 6; ++k)
+        if (h->cfg.face_type[k] == LBM_FACE_FREESLIP) return fail(h, LBM_EINVAL, "the adjoint does not cover free-slip faces");
     if (loss->ke_x0 < 0 || loss->ke_x1 > h->nx || loss->ke_x0 > loss->ke_x1) return fail(h, LBM_EINVAL, "bad slab");
     K = std::max(1, std::min(K, n));
     const long long N = h->N, S = h->S, nb = h->nband;

@@ -127,13 +127,14 @@ int lbm_create(lbm_ctx **out, int nx, int ny, int nz, double nu, const double fo
     if (c.storage < 0 || c.storage > 2) return fail(nullptr, LBM_EINVAL, "unknown storage type");
     if (c.collision < LBM_COLL_ACM || c.collision > LBM_COLL_RAW) return fail(nullptr, LBM_EINVAL, "unknown collision model");
     for (int k = 0; k < 6; ++k)
-        if (c.face_type[k] < 0 || c.face_type[k] > 3) return fail(nullptr, LBM_EINVAL, "unknown face type");
+        if (c.face_type[k] < 0 || c.face_type[k] > 4) return fail(nullptr, LBM_EINVAL, "unknown face type");
     for (int a = 0; a < 3; ++a)
         if ((c.face_type[2 * a] == LBM_FACE_PERIODIC) != (c.face_type[2 * a + 1] == LBM_FACE_PERIODIC))
             return fail(nullptr, LBM_EINVAL, "periodic faces must come in pairs");
     for (int k = 0; k < 6; ++k) {
         if (c.face_type[k] == LBM_FACE_INLET && k != 0) return fail(nullptr, LBM_EINVAL, "the inlet must be the -x face");
         if (c.face_type[k] == LBM_FACE_OUTLET && k != 1) return fail(nullptr, LBM_EINVAL, "the outlet must be the +x face");
+        if (c.face_type[k] == LBM_FACE_FREESLIP && k < 2) return fail(nullptr, LBM_EINVAL, "free-slip faces are y or z faces");
     }
     if (!(c.rho0 > 0.0)) return fail(nullptr, LBM_EINVAL, "rho0 must be positive");
 

@@ -24,12 +24,19 @@ __host__ __device__ constexpr float wgt(int d) { return w1(cx(d)) * w1(cy(d)) * 
 // index of central moment kappa_pqr in the in-place moment tensor
 __host__ __device__ constexpr int K(int p, int q, int r) { return p + 3 * q + 9 * r; }
 
-enum FaceType { FACE_PERIODIC = 0, FACE_NOSLIP = 1, FACE_INLET = 2, FACE_OUTLET = 3 };
+enum FaceType { FACE_PERIODIC = 0, FACE_NOSLIP = 1, FACE_INLET = 2, FACE_OUTLET = 3, FACE_FREESLIP = 4 };
 // bits of a crossing classification
-enum { CROSS_NOSLIP = 1, CROSS_INLET = 2, CROSS_OUTLET = 4 };
+enum { CROSS_NOSLIP = 1, CROSS_INLET = 2, CROSS_OUTLET = 4, CROSS_FREESLIP = 8 };
 
 __host__ __device__ constexpr int face_bit(int t) {
-    return t == FACE_NOSLIP ? CROSS_NOSLIP : t == FACE_INLET ? CROSS_INLET : t == FACE_OUTLET ? CROSS_OUTLET : 0;
+    return t == FACE_NOSLIP ? CROSS_NOSLIP : t == FACE_INLET ? CROSS_INLET : t == FACE_OUTLET ? CROSS_OUTLET
+         : t == FACE_FREESLIP ? CROSS_FREESLIP : 0;
+}
+
+// direction d with its y (bit 0 of mir) and / or z (bit 1) component reversed: the specular
+// image at a free-slip face
+__host__ __device__ constexpr int mirror_dir(int d, int mir) {
+    return d + ((mir & 1) ? -6 * cy(d) : 0) + ((mir & 2) ? -18 * cz(d) : 0);
 }
 
 // ---- population storage: deviations h_i = f_i - w_i rho0 ---------------------------
@@ -118,9 +125,11 @@ __device__ __forceinline__ float inlet_velocity(const StepParams &P, int y, int 
 // ---- neighbour classification with the domain faces ----------------------------------
 
 struct Nbr {
-    int idx;    // flat index of the (wrapped) node, valid when kind == 0 or for lateral wraps
-    int y, z;   // wrapped lateral coordinates
+    int idx;    // flat index of the (wrapped) node, valid when kind == 0 or for lateral wraps;
+                // across a free-slip face the coordinate of that axis is the node's own
+    int y, z;   // wrapped (or free-slip mirrored) lateral coordinates
     int kind;   // CROSS_* bits of the non-periodic faces crossed
+    int mir;    // free-slip axes crossed: bit 0 y, bit 1 z
 };
 
 // node x + S c_D (S = -1: pull source, S = +1: push target); D is a constant after unrolling
@@ -132,19 +141,27 @@ __device__ __forceinline__ Nbr neighbour(const Geometry &g, int D, int x, int y,
         if (sx < 0) { if (g.periodic[0]) sx += g.nx; else kind |= face_bit(g.face[0]); }
         else if (sx >= g.nx) { if (g.periodic[0]) sx -= g.nx; else kind |= face_bit(g.face[1]); }
     }
+    int mir = 0;
     if (cy(D) != 0) {
-        if (sy < 0) { if (g.periodic[1]) sy += g.ny; else kind |= face_bit(g.face[2]); }
-        else if (sy >= g.ny) { if (g.periodic[1]) sy -= g.ny; else kind |= face_bit(g.face[3]); }
+        const int fy = sy < 0 ? g.face[2] : g.face[3];
+        if (sy < 0 || sy >= g.ny) {
+            if (g.periodic[1]) sy += sy < 0 ? g.ny : -g.ny;
+            else { kind |= face_bit(fy); if (fy == FACE_FREESLIP) { mir |= 1; sy = y; } }
+        }
     }
     if (cz(D) != 0) {
-        if (sz < 0) { if (g.periodic[2]) sz += g.nz; else kind |= face_bit(g.face[4]); }
-        else if (sz >= g.nz) { if (g.periodic[2]) sz -= g.nz; else kind |= face_bit(g.face[5]); }
+        const int fz = sz < 0 ? g.face[4] : g.face[5];
+        if (sz < 0 || sz >= g.nz) {
+            if (g.periodic[2]) sz += sz < 0 ? g.nz : -g.nz;
+            else { kind |= face_bit(fz); if (fz == FACE_FREESLIP) { mir |= 2; sz = z; } }
+        }
     }
     Nbr n;
     n.idx = sx + g.nx * (sy + g.ny * sz);
     n.y = sy;
     n.z = sz;
     n.kind = kind;
+    n.mir = mir;
     return n;
 }
 

@@ -54,8 +54,12 @@ __device__ __forceinline__ void load_post(const StepParams &P, int x, int y, int
 #pragma unroll
     for (int d = 0; d < 27; ++d) {
         if (AFTER_NB) {
+            // pushed to x + c_d; across free-slip faces only, to the tangential neighbour's slot
+            // of the mirrored direction; across any other face, to the node's own slot
             const Nbr n = neighbour<+1>(P.g, d, x, y, z);
-            h[d] = n.kind == 0 ? Store<St>::ld(A + d * pl + n.idx) : Store<St>::ld(A + opp(d) * pl + cell);
+            if (n.kind == 0) h[d] = Store<St>::ld(A + d * pl + n.idx);
+            else if (n.kind == CROSS_FREESLIP) h[d] = Store<St>::ld(A + mirror_dir(d, n.mir) * pl + n.idx);
+            else h[d] = Store<St>::ld(A + opp(d) * pl + cell);
         } else {
             h[d] = Store<St>::ld(A + opp(d) * pl + cell);
         }

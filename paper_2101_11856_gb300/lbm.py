@@ -18,7 +18,7 @@ _lib = None
 
 LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ETIMEOUT, LBM_ESTATE = 0, -1, -2, -3, -4, -5, -6
 STORAGE = {"f32": 0, "f16": 1, "bf16": 2}
-FACE = {"periodic": 0, "noslip": 1, "inlet": 2, "outlet": 3}
+FACE = {"periodic": 0, "noslip": 1, "inlet": 2, "outlet": 3, "freeslip": 4}
 COLLISION = {"acm": 0, "bgk": 1, "raw": 2}
 KERNEL_KINDS = ("step", "band", "interp", "spread", "boundary", "other", "tracer", "motion")
 
