@@ -213,11 +213,11 @@ def scene_rotating_torus(nx=400, ny=200, nz=400, R=40.0, r=12.0, spacing=0.68, o
 
 def scene_box_city(nx=1200, ny=250, nz=840, n_boxes=200, side_range=(8, 24), u_in=0.08, nu=1e-4,
                    spacing=0.5, seed=SEED, noise=0.01, with_state=True):
-    """Buildings scene: inlet at x = 0, outlet at x = nx-1, no-slip ground (y = 0) and top
-    (y = ny-1), z periodic; ``n_boxes`` procedural boxes sampled at ``spacing``."""
+    """Buildings scene: inlet at x = 0, outlet at x = nx-1, no-slip ground (y = 0), free-slip
+    top (y = ny-1), z periodic; ``n_boxes`` procedural boxes sampled at ``spacing``."""
     X, A = box_city(nx, ny, nz, n_boxes, side_range, (20, 120), spacing, seed)
     d = dict(name=f"box_city_{nx}x{ny}x{nz}", nx=nx, ny=ny, nz=nz, nu=nu,
-             faces=("inlet", "outlet", "noslip", "noslip", "periodic", "periodic"),
+             faces=("inlet", "outlet", "noslip", "freeslip", "periodic", "periodic"),
              samples=X, area=A, u_in=u_in, noise=noise)
     if with_state:
         d["rho"], d["u"] = uniform_flow(nx, ny, nz, (u_in, 0.0, 0.0))

@@ -137,3 +137,34 @@ def test_long_rows_periodic_box():
     print(f"nx=72 periodic: L {Lg:.6e} vs {Lo:.6e}; rel dX {rel_l2(dxg, dxo.numpy()):.2e}")
     assert abs(Lg - Lo) <= 1e-5 * abs(Lo)
     assert rel_l2(dxg, dxo.numpy()) <= 1e-3
+
+
+def test_c5_fullsize_directional_derivatives():
+    """The adjoint workload at full size (128^3 channel, 2,000-sample sphere, 200 steps, K = 20,
+    loss = mean drag + kinetic energy of 96 <= x < 128, gradients at a = 0): the loss's
+    central differences along the adjoint's own gradient directions equal the gradient
+    norms.  Inflow coefficients: step 1e-3 (the loss is smooth in a), bar 1e-4; positions:
+    step 1e-2 cells (the trilinear weights have kinks at cell faces, and the FP32 loss of ~660
+    has ~1e-4 noise), bar 3 %."""
+    from paper_2101_11856_gb300 import Solver
+    n = 128
+    X, A = scenes.fibonacci_sphere((40.0, 64, 64), 12.6, 2000)
+    rho, u = scenes.uniform_flow(n, n, n, (0.05, 0, 0))
+    s = Solver(n, n, n, 0.01, faces=("inlet", "outlet", "periodic", "periodic", "periodic", "periodic"),
+               u_in=0.05, noise=0.01, seed=2101)
+
+    def run(coef, Xs):
+        s.set_inflow(coef)
+        s.set_solids(Xs.astype(np.float32), A)
+        s.set_state(rho, u)
+        return s.adjoint(200, 20, 1.0, 1.0, 96, 128, 2000)
+
+    a0 = np.zeros(16)
+    L, dc, dx = run(a0, X)
+    e = dc / np.linalg.norm(dc)
+    fd_c = (run(a0 + 1e-3 * e, X)[0] - run(a0 - 1e-3 * e, X)[0]) / 2e-3
+    ex = dx / np.linalg.norm(dx)
+    fd_x = (run(a0, X + 1e-2 * ex)[0] - run(a0, X - 1e-2 * ex)[0]) / 2e-2
+    print(f"C5: L {L:.4f}; |dL/da| {np.linalg.norm(dc):.6e} vs {fd_c:.6e}; |dL/dX| {np.linalg.norm(dx):.5e} vs {fd_x:.5e}")
+    assert abs(fd_c - np.linalg.norm(dc)) <= 1e-4 * np.linalg.norm(dc)
+    assert abs(fd_x - np.linalg.norm(dx)) <= 3e-2 * np.linalg.norm(dx)
