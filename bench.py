@@ -144,6 +144,16 @@ def oracle_sample(d, steps, block=None):
 REFERENCE_BLOCK = (500, 96, 0, 96, 4)     # one reference-arm step: 36,864 cells near the buildings
 
 
+def max_over_ranks(x, dist, device):
+    """The largest value of x over the ranks (x itself without a process group)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -365,11 +375,7 @@ def main():
     with Clocks(local) as clk:
         ms, kt = timed_steps(s, args.steps, torch)
     barrier()
-    ms_max = ms
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
+    ms_max = max_over_ranks(ms, dist, "cuda" if torch.cuda.is_available() else "cpu")
     ms_step = ms_max / args.steps
     mlups = world * N / (ms_step * 1e-3) / 1e6
     xedge = 32                            # edge strip of the face kernel (XEDGE in lbm_internal.h)
