@@ -408,9 +408,10 @@ def main():
             lbm.lbm_synchronize(s.h, 600.0)
         dt = time.perf_counter() - t0
         e2e = {"value": world * N * batch * rounds / dt / 1e6, "unit": "MLUPS",
-               "h2d_bytes_per_step": 16 * N, "d2h_bytes_per_step": 16 * N,
-               "steps_per_batch": batch,
-               "what": "per batch: lbm_set_state from pinned host rho,u + 100 steps + lbm_macroscopic to pinned host"}
+               "h2d_bytes_per_step": 16 * N / batch, "d2h_bytes_per_step": 16 * N / batch,
+               "steps_per_batch": batch, "bytes_per_batch_each_way": 16 * N,
+               "what": "per batch: lbm_set_state from pinned host rho,u (16 N bytes) + 100 steps + "
+                       "lbm_macroscopic to pinned host (16 N bytes); per-step bytes = batch bytes / 100"}
         del h_rho, h_u, o_rho, o_u
     s.close()
     del s

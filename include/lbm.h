@@ -98,7 +98,9 @@ int lbm_destroy(lbm_ctx *h);
 
 /* Initialise the populations to the equilibrium of the given fields, f_i = f_eq_i(rho, u)
  * (product-form discrete Maxwellian), and reset the step counter to 0.
- * rho: N floats; u: 3N floats (SoA).  Host or device pointers. */
+ * rho: N floats; u: 3N floats (SoA).  Host or device pointers; host fields go through a
+ * device staging buffer of 16 N bytes that the context keeps for later host transfers
+ * (lbm_set_state, lbm_macroscopic), and the call returns after they were read. */
 int lbm_set_state(lbm_ctx *h, const float *rho, const float *u);
 
 /* Install the immersed solid (Sec. 3.1): count samples at positions samples[3*s+a]
@@ -115,14 +117,16 @@ int lbm_set_solids(lbm_ctx *h, const float *samples, long long count,
  * with forcing, domain faces), asynchronously on the context's stream.  Each step is one
  * fused stream+collide kernel over the nodes 32 <= x < nx-32, one over the two 32-node
  * edge strips of every row (the inlet/outlet/x-periodic rules), and three small
- * immersed-boundary kernels when a solid is installed.
+ * immersed-boundary kernels when a solid is installed (plus the re-pose of a moving solid
+ * and the tracer advection when those are set).
  * Errors: LBM_ESTATE before lbm_set_state, LBM_ECUDA. */
 int lbm_step(lbm_ctx *h, int n);
 
 /* Density and Guo-shifted velocity u = (sum c f + F/2)/rho used by the most recent
  * collision (Eq. 2); before any step, the fields given to lbm_set_state.
  * rho: N floats, u: 3N floats (SoA); either may be NULL.  Host or device pointers;
- * with host pointers the call returns after the copy completed. */
+ * with host pointers the call returns after the copy completed (through the context's
+ * staging buffer, see lbm_set_state). */
 int lbm_macroscopic(lbm_ctx *h, float *rho, float *u);
 
 /* FP64 global diagnostics of the most recent step: total mass sum rho, total momentum

@@ -186,6 +186,7 @@ int lbm_destroy(lbm_ctx *h) {
     if (h->f) cudaStreamSynchronize(h->stream);
     free_solid(h);
     free_tracers(h);
+    dev_free(h->stage);
     dev_free(h->f);
     dev_free(h->outlet);
     dev_free(h->inlet_profile);
@@ -207,25 +208,21 @@ int lbm_set_state(lbm_ctx *h, const float *rho, const float *u) {
     if (!h) return fail(nullptr, LBM_EINVAL, "null context");
     if (!rho || !u) return fail(h, LBM_EINVAL, "rho and u are required");
     const float *drho = rho, *du = u;
-    float *tmp = nullptr;
     const bool dev = is_device_ptr(rho) && is_device_ptr(u);
     if (!dev) {
-        int rc = dev_alloc(h, &tmp, (size_t)4 * h->N);
+        int rc = ensure_stage(h, (size_t)4 * h->N);
         if (rc) return rc;
-        CK(cudaMemcpyAsync(tmp, rho, (size_t)h->N * sizeof(float), cudaMemcpyDefault, h->stream));
-        CK(cudaMemcpyAsync(tmp + h->N, u, (size_t)3 * h->N * sizeof(float), cudaMemcpyDefault, h->stream));
-        drho = tmp;
-        du = tmp + h->N;
+        CK(cudaMemcpyAsync(h->stage, rho, (size_t)h->N * sizeof(float), cudaMemcpyDefault, h->stream));
+        CK(cudaMemcpyAsync(h->stage + h->N, u, (size_t)3 * h->N * sizeof(float), cudaMemcpyDefault, h->stream));
+        drho = h->stage;
+        du = h->stage + h->N;
     }
     StepParams P = make_params(h, 0);
     {
         Timed tm(h, LBM_KERNEL_OTHER);
         CK(launch_init(h->storage, P, drho, du, h->stream));
     }
-    if (tmp) {
-        CK(cudaStreamSynchronize(h->stream));
-        dev_free(tmp);
-    }
+    if (!dev) CK(cudaStreamSynchronize(h->stream));   // the caller may reuse its host buffers
     h->t = 0;
     h->has_state = true;
     return LBM_OK;
@@ -373,12 +370,11 @@ int lbm_macroscopic(lbm_ctx *h, float *rho, float *u) {
     if (rc) return rc;
     if (!rho && !u) return LBM_OK;
     const bool dr = !rho || is_device_ptr(rho), du = !u || is_device_ptr(u);
-    float *tmp = nullptr;
     float *drho = rho, *duu = u;
     if (!dr || !du) {
-        if ((rc = dev_alloc(h, &tmp, (size_t)4 * h->N))) return rc;
-        if (!dr) drho = tmp;
-        if (!du) duu = tmp + h->N;
+        if ((rc = ensure_stage(h, (size_t)4 * h->N))) return rc;
+        if (!dr) drho = h->stage;
+        if (!du) duu = h->stage + h->N;
     }
     StepParams P = make_params(h, h->t);
     {
@@ -387,10 +383,7 @@ int lbm_macroscopic(lbm_ctx *h, float *rho, float *u) {
     }
     if (!dr) CK(cudaMemcpyAsync(rho, drho, (size_t)h->N * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
     if (!du) CK(cudaMemcpyAsync(u, duu, (size_t)3 * h->N * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
-    if (tmp) {
-        CK(cudaStreamSynchronize(h->stream));
-        dev_free(tmp);
-    }
+    if (!dr || !du) CK(cudaStreamSynchronize(h->stream));
     return LBM_OK;
 }
 

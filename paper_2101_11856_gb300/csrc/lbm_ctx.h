@@ -67,6 +67,10 @@ struct lbm_ctx {
     void *tracer_ws = nullptr;
     size_t tracer_ws_bytes = 0;
 
+    // device staging of host-pointer fields (lbm_set_state / lbm_macroscopic), kept between calls
+    float *stage = nullptr;
+    size_t stage_cap = 0;           // floats
+
     // scratch of the reductions
     double *partial = nullptr;
     size_t partial_cap = 0;         // doubles
@@ -232,6 +236,16 @@ int advect_tracers(lbm_ctx *h, long long t);
 // rebuild the band; refresh the host copy of the samples' caller order
 int motion_before_step(lbm_ctx *h, long long t);
 int sync_order(lbm_ctx *h);
+
+inline int ensure_stage(lbm_ctx *h, size_t floats) {
+    if (floats <= h->stage_cap) return LBM_OK;
+    dev_free(h->stage);
+    h->stage_cap = 0;
+    int rc = dev_alloc(h, &h->stage, floats);
+    if (rc) return rc;
+    h->stage_cap = floats;
+    return LBM_OK;
+}
 
 inline int ensure_partial(lbm_ctx *h, size_t doubles) {
     if (doubles <= h->partial_cap) return LBM_OK;
