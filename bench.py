@@ -285,7 +285,7 @@ def moving_run(torch, lbm, Solver, args, peak, world):
     s.close()
     torch.cuda.empty_cache()
     k = kt["step"][0] / max(kt["step"][1], 1)
-    n_int = (nx - 64) * ny * nz
+    n_int = main_cells(nx, ny, nz, sc["faces"])
     ach = 216 * n_int / (k * 1e-3) / 1e9
     if not np.all(np.isfinite(torque)):
         raise RuntimeError("non-finite torque in the rotating-torus run")
@@ -294,6 +294,19 @@ def moving_run(torch, lbm, Solver, args, peak, world):
             "kernel_ms_per_step": {kk: round(v[0] / steps, 4) for kk, v in kt.items() if v[1]},
             "step_kernel_roofline": {"achieved": ach, "frac": ach / peak},
             "torque": list(map(float, torque))}
+
+
+def main_cells(nx, ny, nz, faces):
+    """Nodes one launch of the main step kernel updates: the main range 32 <= x < nx - 32 (32 =
+    the edge strip of the face kernel) of every row, or, on a grid with a free-slip face, of the
+    rows off the y/z faces (the face rows run with the boundary kernels)."""
+    xedge = 32
+    if nx < 2 * xedge + 1:
+        return 0
+    rows = ny * nz
+    if "freeslip" in faces:
+        rows = max(ny - 2, 0) * max(nz - 2, 0)
+    return (nx - 2 * xedge) * rows
 
 
 def timed_steps(solver, steps, torch):
@@ -378,8 +391,7 @@ def main():
     ms_max = max_over_ranks(ms, dist, "cuda" if torch.cuda.is_available() else "cpu")
     ms_step = ms_max / args.steps
     mlups = world * N / (ms_step * 1e-3) / 1e6
-    xedge = 32                            # edge strip of the face kernel (XEDGE in lbm_internal.h)
-    n_int = max(nx - 2 * xedge, 0) * ny * nz if nx >= 2 * xedge + 1 else 0   # cells of k_step_main
+    n_int = main_cells(nx, ny, nz, d["faces"])   # cells of one k_step_main launch
     step_ms, step_n = kt["step"]
     k_ms = step_ms / max(step_n, 1)
     achieved = BYTES_PER_CELL["f32"] * n_int / (k_ms * 1e-3) / 1e9
@@ -461,7 +473,7 @@ def main():
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": TRAFFIC_PER_CELL["f32"] * n_int if TRAFFIC_PER_CELL.get("f32") else None,
-                         "kernel": "k_step_main (fused stream+collide, 32 <= x < nx-32)",
+                         "kernel": "k_step_main (fused stream+collide, 32 <= x < nx-32 of the rows off the y/z faces)",
                          "cells_per_launch": n_int, "bytes_per_cell": 216,
                          "peak_kind": peak_kind},
             "kernel_ms": breakdown,

@@ -17,8 +17,9 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "liblbm.so")
-SOURCES = ["lbm_adjoint.cu", "lbm_step_acm.cu", "lbm_step_bgk.cu", "lbm_step_raw.cu", "lbm_kernels.cu", "lbm_api.cu",
-           "lbm_tracers.cu", "lbm_motion.cu", "lbm_sort.cu", "lbm_static.cu"]
+SOURCES = ["lbm_adjoint.cu", "lbm_step_acm.cu", "lbm_step_bgk.cu", "lbm_step_raw.cu", "lbm_step_acm_fs.cu",
+           "lbm_step_bgk_fs.cu", "lbm_step_raw_fs.cu", "lbm_kernels.cu", "lbm_api.cu", "lbm_tracers.cu",
+           "lbm_motion.cu", "lbm_sort.cu", "lbm_static.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

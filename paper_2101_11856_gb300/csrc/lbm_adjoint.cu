@@ -379,7 +379,7 @@ __global__ void __launch_bounds__(STEP_BX) k_adj_main(StepParams P, AdjParams A)
     const bool inner = y >= 1 && y <= P.g.ny - 2 && z >= 1 && z <= P.g.nz - 2;   // uniform per block
     float fs[27], lam[27];
     if (!NB || inner) load_interior<St, NB>(P, cell, fs);
-    else load_yzface<St>(P, y, z, cell, fs);
+    else load_yzface<St, false>(P, y, z, cell, fs);
     node_vjp<BAND>(P, A, x, cell, fs, lam);
     const long long N = P.g.ncell;
     if (inner) {
@@ -389,7 +389,7 @@ __global__ void __launch_bounds__(STEP_BX) k_adj_main(StepParams P, AdjParams A)
     } else {
         int off[9], mir[9];
         bool bb[9];
-        yz_rows<-1>(P.g, y, z, off, bb, mir);   // free-slip faces are rejected by lbm_adjoint
+        yz_rows<-1, false>(P.g, y, z, off, bb, mir);   // free-slip faces are rejected by lbm_adjoint
 #pragma unroll
         for (int d = 0; d < 27; ++d) {
             if (bb[d / 3]) A.lam_prev[opp(d) * N + cell] = lam[d];
@@ -409,7 +409,7 @@ __device__ __forceinline__ void adj_push_edge(const StepParams &P, const AdjPara
     const long long N = P.g.ncell;
     int off[9], mir[9];
     bool bb[9];
-    row_offsets<-1, INNER>(P.g, y, z, off, bb, mir);   // free-slip faces are rejected by lbm_adjoint
+    row_offsets<-1, INNER, false>(P.g, y, z, off, bb, mir);   // free-slip faces are rejected by lbm_adjoint
     const bool xlo = SIDE != 1 && x == 0, xhi = SIDE != 0 && x == P.g.nx - 1;
     const int flo = P.g.face[0], fhi = P.g.face[1];
     const bool outlet_node = xhi && fhi == FACE_OUTLET;
@@ -448,7 +448,7 @@ __device__ __forceinline__ void adj_edge_node(const StepParams &P, const AdjPara
     if (x >= P.g.nx) return;
     const int cell = x + P.g.nx * (y + P.g.ny * z);
     float fs[27], lam[27];
-    load_edge<St, NB, SIDE>(P, x, y, z, cell, fs);
+    load_edge<St, NB, SIDE, false>(P, x, y, z, cell, fs);
     node_vjp<BAND>(P, A, x, cell, fs, lam);
     if (y >= 1 && y <= P.g.ny - 2 && z >= 1 && z <= P.g.nz - 2) adj_push_edge<true, SIDE>(P, A, x, y, z, cell, lam);
     else adj_push_edge<false, SIDE>(P, A, x, y, z, cell, lam);

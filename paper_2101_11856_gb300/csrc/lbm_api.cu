@@ -33,9 +33,12 @@ int step_with(lbm_ctx *h, const StepParams &P) {
         { Timed tm(h, LBM_KERNEL_INTERP); CK(launch_ib_interp(h->S, h->nband, h->X, h->area, h->ub, h->corner_band, h->band_rho, h->band_u, h->g, h->stream)); }
         { Timed tm(h, LBM_KERNEL_SPREAD); CK(launch_ib_spread(h->S, h->nband, h->band_count_dev, h->X, h->g, h->base_nbr, h->cstart, h->ccount, h->bandF, h->stream)); }
     }
-    { Timed tm(h, LBM_KERNEL_BOUNDARY); CK(launch_step(h->storage, P, band, STEP_BOUNDARY, h->cfg.collision, h->stream)); }
+    {
+        Timed tm(h, LBM_KERNEL_BOUNDARY, step_launches(P, STEP_BOUNDARY));
+        CK(launch_step(h->storage, P, band, STEP_BOUNDARY, h->cfg.collision, h->stream));
+    }
     if (has_interior(P.g)) {
-        Timed tm(h, LBM_KERNEL_STEP);
+        Timed tm(h, LBM_KERNEL_STEP, step_launches(P, STEP_INTERIOR));
         CK(launch_step(h->storage, P, band, STEP_INTERIOR, h->cfg.collision, h->stream));
     }
     return LBM_OK;

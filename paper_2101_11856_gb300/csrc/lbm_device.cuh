@@ -98,6 +98,8 @@ struct StepParams {
     long long nband;             // band nodes, or the stride of the band arrays when band_count is set
     const int *band_count;       // device count of band nodes (moving solids), or nullptr
     float *u_out;                // [3][ncell] Guo-shifted velocity of the step, or nullptr
+    int inner_rows;              // 1: the step kernels skip the rows on a y/z face (run by the
+                                 // free-slip kernels of the same step)
 };
 
 // ---- inlet noise: counter-based SplitMix64 (Steele, Lea, Flood 2014) ------------------

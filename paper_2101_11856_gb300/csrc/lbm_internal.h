@@ -17,10 +17,28 @@ enum CollisionModel { COLL_ACM = 0, COLL_BGK = 1, COLL_RAW = 2 };
 constexpr int XEDGE = 32;
 constexpr int STEP_BX = 64;   // threads per block of the main step kernels (along x)
 cudaError_t launch_step(int storage, const StepParams &P, bool band, int part, int collision, cudaStream_t st);
-template <int COLL>
+template <int COLL, bool FS>
 cudaError_t launch_step_coll(int storage, const StepParams &P, bool band, int part, cudaStream_t st);
 long long boundary_count(const Geometry &g);
 __host__ __device__ inline bool has_interior(const Geometry &g) { return g.nx >= 2 * XEDGE + 1; }
+// kernels one launch_step call makes (a grid with a free-slip face runs its face rows in the
+// boundary part: edge strips of the other rows, then edge strips and main range of the face rows)
+int step_launches(const StepParams &P, int part);
+// the rows (y, z) on a y or z face: z = 0 and z = nz-1 (every y), then y = 0 and y = ny-1 of each
+// z in between, in this order
+__host__ __device__ inline long long face_rows(const Geometry &g) {
+    const long long ny = g.ny, nz = g.nz;
+    return ny * (nz < 2 ? nz : 2) + (nz > 2 ? nz - 2 : 0) * (ny < 2 ? ny : 2);
+}
+__host__ __device__ inline void face_row(const Geometry &g, long long r, int &y, int &z) {
+    if (r < g.ny) { y = (int)r; z = 0; return; }
+    r -= g.ny;
+    if (r < g.ny) { y = (int)r; z = g.nz - 1; return; }   // (nz >= 2 here)
+    r -= g.ny;
+    const int w = g.ny > 1 ? 2 : 1;
+    z = 1 + (int)(r / w);
+    y = (r % w) ? g.ny - 1 : 0;
+}
 __host__ __device__ inline int edge_per_row(const Geometry &g) { return has_interior(g) ? 2 * XEDGE : g.nx; }
 cudaError_t launch_init(int storage, const StepParams &P, const float *rho, const float *u, cudaStream_t st);
 long long macro_blocks(const StepParams &P);

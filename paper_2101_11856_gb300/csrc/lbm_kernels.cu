@@ -276,12 +276,44 @@ static cudaError_t dispatch_storage(int storage, F &&fn) {
     }
 }
 
-cudaError_t launch_step(int storage, const StepParams &P, bool band, int part, int collision, cudaStream_t st) {
+// The free-slip variants (FS) serve the grids with a free-slip face.  They run over the rows on a
+// y/z face only, in the boundary part (edge strips and main range of those rows), and the kernels
+// without FS over the other rows (inner_rows): the mirror logic is compiled out of the kernel
+// that updates nearly every node, which keeps its register count.  Grids without a main range
+// run the FS rows kernel on every row.
+namespace {
+bool has_freeslip(const Geometry &g) {
+    bool fs = false;
+    for (int k = 2; k < 6; ++k) fs = fs || g.face[k] == FACE_FREESLIP;
+    return fs;
+}
+
+template <bool FS>
+cudaError_t launch_step_fs(int storage, const StepParams &P, bool band, int part, int collision, cudaStream_t st) {
     switch (collision) {
-        case COLL_BGK: return launch_step_coll<COLL_BGK>(storage, P, band, part, st);
-        case COLL_RAW: return launch_step_coll<COLL_RAW>(storage, P, band, part, st);
-        default: return launch_step_coll<COLL_ACM>(storage, P, band, part, st);
+        case COLL_BGK: return launch_step_coll<COLL_BGK, FS>(storage, P, band, part, st);
+        case COLL_RAW: return launch_step_coll<COLL_RAW, FS>(storage, P, band, part, st);
+        default: return launch_step_coll<COLL_ACM, FS>(storage, P, band, part, st);
     }
+}
+}  // namespace
+
+int step_launches(const StepParams &P, int part) {
+    if (part == STEP_INTERIOR) return has_interior(P.g) ? 1 : 0;
+    return has_freeslip(P.g) && has_interior(P.g) ? 3 : 1;
+}
+
+cudaError_t launch_step(int storage, const StepParams &P, bool band, int part, int collision, cudaStream_t st) {
+    if (!has_freeslip(P.g)) return launch_step_fs<false>(storage, P, band, part, collision, st);
+    StepParams Pi = P;
+    Pi.inner_rows = 1;
+    if (part == STEP_INTERIOR)
+        return has_interior(P.g) ? launch_step_fs<false>(storage, Pi, band, part, collision, st) : cudaSuccess;
+    if (has_interior(P.g)) {
+        const cudaError_t e = launch_step_fs<false>(storage, Pi, band, part, collision, st);
+        if (e != cudaSuccess) return e;
+    }
+    return launch_step_fs<true>(storage, P, band, part, collision, st);
 }
 
 cudaError_t launch_init(int storage, const StepParams &P, const float *rho, const float *u, cudaStream_t st) {

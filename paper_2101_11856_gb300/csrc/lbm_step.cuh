@@ -111,8 +111,9 @@ __device__ __forceinline__ void band_force(const StepParams &P, int cell, float 
 // periodic wrap), or mark it as crossing a no-slip face (bounce-back to the node's own slot),
 // or as crossing free-slip faces: mir bit 0 (y) / bit 1 (z), the row offset of that axis is 0
 // and the population is the specular image (mirror_dir).  No-slip wins over free-slip.
-// Row j of direction d is j = d / 3 = (c_y + 1) + 3 (c_z + 1).
-template <int S>
+// Row j of direction d is j = d / 3 = (c_y + 1) + 3 (c_z + 1).  FS: the grid has a free-slip face
+// (without it the mirror flags are the constant 0 and every mirrored direction folds to d).
+template <int S, bool FS>
 __device__ __forceinline__ void yz_rows(const Geometry &g, int y, int z, int (&off)[9], bool (&bb)[9], int (&mir)[9]) {
     int oy[3], oz[3];
     bool by[3], bz[3], my[3], mz[3];
@@ -120,16 +121,22 @@ __device__ __forceinline__ void yz_rows(const Geometry &g, int y, int z, int (&o
     for (int c = -1; c <= 1; ++c) {
         int yy = y + S * c, zz = z + S * c;
         by[c + 1] = bz[c + 1] = my[c + 1] = mz[c + 1] = false;
-        if (yy < 0 || yy >= g.ny) {
-            const int f = yy < 0 ? g.face[2] : g.face[3];
-            if (g.periodic[1]) yy += yy < 0 ? g.ny : -g.ny;
-            else if (f == FACE_FREESLIP) { my[c + 1] = true; yy = y; }
+        if (yy < 0) {
+            if (g.periodic[1]) yy += g.ny;
+            else if (FS && g.face[2] == FACE_FREESLIP) { my[c + 1] = true; yy = y; }
+            else by[c + 1] = true;
+        } else if (yy >= g.ny) {
+            if (g.periodic[1]) yy -= g.ny;
+            else if (FS && g.face[3] == FACE_FREESLIP) { my[c + 1] = true; yy = y; }
             else by[c + 1] = true;
         }
-        if (zz < 0 || zz >= g.nz) {
-            const int f = zz < 0 ? g.face[4] : g.face[5];
-            if (g.periodic[2]) zz += zz < 0 ? g.nz : -g.nz;
-            else if (f == FACE_FREESLIP) { mz[c + 1] = true; zz = z; }
+        if (zz < 0) {
+            if (g.periodic[2]) zz += g.nz;
+            else if (FS && g.face[4] == FACE_FREESLIP) { mz[c + 1] = true; zz = z; }
+            else bz[c + 1] = true;
+        } else if (zz >= g.nz) {
+            if (g.periodic[2]) zz -= g.nz;
+            else if (FS && g.face[5] == FACE_FREESLIP) { mz[c + 1] = true; zz = z; }
             else bz[c + 1] = true;
         }
         oy[c + 1] = (yy - y) * g.nx;
@@ -139,39 +146,42 @@ __device__ __forceinline__ void yz_rows(const Geometry &g, int y, int z, int (&o
     for (int j = 0; j < 9; ++j) {
         off[j] = oy[j % 3] + oz[j / 3];
         bb[j] = by[j % 3] || bz[j / 3];
-        mir[j] = (my[j % 3] ? 1 : 0) | (mz[j / 3] ? 2 : 0);
+        mir[j] = FS ? (my[j % 3] ? 1 : 0) | (mz[j / 3] ? 2 : 0) : 0;
     }
 }
 
 // direction D of a row with free-slip mirror flags m (warp-uniform): its specular image for
-// the mirrored axes in which D has a nonzero component (constant D after unrolling)
+// the mirrored axes in which D has a nonzero component (constant D after unrolling); D itself
+// without a free-slip face (spelled out: the flags 0 alone do not fold the table index)
+template <bool FS>
 __device__ __forceinline__ int mdir(int D, int m) {
+    if (!FS) return D;
     const int my = cy(D) != 0 ? (m & 1) : 0, mz = cz(D) != 0 ? (m & 2) : 0;
     return mirror_dir(D, my | mz);
 }
 
 // odd-step loads/stores of a node with 1 <= x <= nx-2 on a y or z face
-template <typename St>
+template <typename St, bool FS>
 __device__ __forceinline__ void load_yzface(const StepParams &P, int y, int z, int cell, float (&h)[27]) {
     int off[9], mir[9];
     bool bb[9];
-    yz_rows<-1>(P.g, y, z, off, bb, mir);
+    yz_rows<-1, FS>(P.g, y, z, off, bb, mir);
 #pragma unroll
     for (int d = 0; d < 27; ++d) {
         if (bb[d / 3]) h[d] = Store<St>::ld(static_cast<const St *>(P.fp[d]) + cell);
-        else h[d] = Store<St>::ld(static_cast<const St *>(P.fp[opp(mdir(d, mir[d / 3]))]) + (cell + off[d / 3]) - cx(d));
+        else h[d] = Store<St>::ld(static_cast<const St *>(P.fp[opp(mdir<FS>(d, mir[d / 3]))]) + (cell + off[d / 3]) - cx(d));
     }
 }
 
-template <typename St>
+template <typename St, bool FS>
 __device__ __forceinline__ void store_yzface(const StepParams &P, int y, int z, int cell, const float (&h)[27]) {
     int off[9], mir[9];
     bool bb[9];
-    yz_rows<+1>(P.g, y, z, off, bb, mir);
+    yz_rows<+1, FS>(P.g, y, z, off, bb, mir);
 #pragma unroll
     for (int d = 0; d < 27; ++d) {
         if (bb[d / 3]) Store<St>::st(static_cast<St *>(P.fpo[opp(d)]) + cell, h[d]);
-        else Store<St>::st(static_cast<St *>(P.fpo[mdir(d, mir[d / 3])]) + (cell + off[d / 3]) + cx(d), h[d]);
+        else Store<St>::st(static_cast<St *>(P.fpo[mdir<FS>(d, mir[d / 3])]) + (cell + off[d / 3]) + cx(d), h[d]);
     }
 }
 
@@ -202,31 +212,31 @@ __device__ __forceinline__ void store_interior2(const StepParams &P, int cell, b
     }
 }
 
-template <typename St>
+template <typename St, bool FS>
 __device__ __forceinline__ void load_yzface2(const StepParams &P, int y, int z, int cell, bool two, float (&h0)[27],
                                              float (&h1)[27]) {
     int off[9], mir[9];
     bool bb[9];
-    yz_rows<-1>(P.g, y, z, off, bb, mir);
+    yz_rows<-1, FS>(P.g, y, z, off, bb, mir);
 #pragma unroll
     for (int d = 0; d < 27; ++d) {
         const St *p = bb[d / 3] ? static_cast<const St *>(P.fp[d]) + cell
-                                : static_cast<const St *>(P.fp[opp(mdir(d, mir[d / 3]))]) + (cell + off[d / 3]) - cx(d);
+                                : static_cast<const St *>(P.fp[opp(mdir<FS>(d, mir[d / 3]))]) + (cell + off[d / 3]) - cx(d);
         h0[d] = Store<St>::ld(p);
         h1[d] = two ? Store<St>::ld(p + 32) : 0.0f;
     }
 }
 
-template <typename St>
+template <typename St, bool FS>
 __device__ __forceinline__ void store_yzface2(const StepParams &P, int y, int z, int cell, bool two,
                                               const float (&h0)[27], const float (&h1)[27]) {
     int off[9], mir[9];
     bool bb[9];
-    yz_rows<+1>(P.g, y, z, off, bb, mir);
+    yz_rows<+1, FS>(P.g, y, z, off, bb, mir);
 #pragma unroll
     for (int d = 0; d < 27; ++d) {
         St *p = bb[d / 3] ? static_cast<St *>(P.fpo[opp(d)]) + cell
-                          : static_cast<St *>(P.fpo[mdir(d, mir[d / 3])]) + (cell + off[d / 3]) + cx(d);
+                          : static_cast<St *>(P.fpo[mdir<FS>(d, mir[d / 3])]) + (cell + off[d / 3]) + cx(d);
         Store<St>::st(p, h0[d]);
         if (two) Store<St>::st(p + 32, h1[d]);
     }
@@ -239,7 +249,7 @@ __device__ __forceinline__ void store_yzface2(const StepParams &P, int y, int z,
 // (push) lies across that face.  Priority at edges: no-slip > inlet > outlet.
 // Row offsets of the 9 (c_y, c_z) neighbour rows, pull (S = -1) or push (S = +1): constant
 // offsets for a row away from the y/z faces (INNER), else yz_rows (wrap / no-slip flags).
-template <int S, bool INNER>
+template <int S, bool INNER, bool FS>
 __device__ __forceinline__ void row_offsets(const Geometry &g, int y, int z, int (&off)[9], bool (&bb)[9],
                                             int (&mir)[9]) {
     if (INNER) {
@@ -250,17 +260,17 @@ __device__ __forceinline__ void row_offsets(const Geometry &g, int y, int z, int
             mir[j] = 0;
         }
     } else {
-        yz_rows<S>(g, y, z, off, bb, mir);
+        yz_rows<S, FS>(g, y, z, off, bb, mir);
     }
 }
 
 // SIDE: 0 = left strip (only x = 0 can be a face lane), 1 = right strip (only x = nx-1),
 // 2 = a whole short row (both)
-template <typename St, bool NB, bool INNER, int SIDE>
+template <typename St, bool NB, bool INNER, int SIDE, bool FS>
 __device__ __forceinline__ void load_edge_t(const StepParams &P, int x, int y, int z, int cell, float (&h)[27]) {
     int off[9], mir[9];
     bool bb[9];
-    row_offsets<-1, INNER>(P.g, y, z, off, bb, mir);
+    row_offsets<-1, INNER, FS>(P.g, y, z, off, bb, mir);
     const bool xlo = SIDE != 1 && x == 0, xhi = SIDE != 0 && x == P.g.nx - 1;
     // every lane pulls as an interior node; the lanes at x = 0 / nx-1 read their own slot for
     // the directions whose source lies across the x face, and are fixed up below
@@ -274,7 +284,7 @@ __device__ __forceinline__ void load_edge_t(const StepParams &P, int x, int y, i
         bool own = bb[j];
         if (cx(d) == 1) own = own || xlo;
         if (cx(d) == -1) own = own || xhi;
-        const St *base = static_cast<const St *>(own ? P.fp[d] : P.fp[opp(mdir(d, mir[j]))]);
+        const St *base = static_cast<const St *>(own ? P.fp[d] : P.fp[opp(mdir<FS>(d, mir[j]))]);
         h[d] = Store<St>::ld(base + (own ? cell : cell + off[j] - cx(d)));
     }
     // x-face rules of the face lanes (one per warp), once per side
@@ -285,7 +295,7 @@ __device__ __forceinline__ void load_edge_t(const StepParams &P, int x, int y, i
         for (int d = 2; d < 27; d += 3) {   // c_x = +1: sources across the -x face
             if (bb[d / 3]) continue;         // no-slip wins at edges
             if (ft == FACE_PERIODIC && NB)
-                h[d] = Store<St>::ld(static_cast<const St *>(P.fp[opp(mdir(d, mir[d / 3]))]) +
+                h[d] = Store<St>::ld(static_cast<const St *>(P.fp[opp(mdir<FS>(d, mir[d / 3]))]) +
                                      (cell + off[d / 3] + (P.g.nx - 1)));
             else if (ft == FACE_INLET)
                 h[d] += 6.0f * wgt(d) * P.rho0 * uw;
@@ -298,12 +308,12 @@ __device__ __forceinline__ void load_edge_t(const StepParams &P, int x, int y, i
         for (int d = 0; d < 27; d += 3) {   // c_x = -1: sources across the +x face
             if (bb[d / 3]) continue;
             if (ft == FACE_PERIODIC && NB) {
-                h[d] = Store<St>::ld(static_cast<const St *>(P.fp[opp(mdir(d, mir[d / 3]))]) +
+                h[d] = Store<St>::ld(static_cast<const St *>(P.fp[opp(mdir<FS>(d, mir[d / 3]))]) +
                                      (cell + off[d / 3] - (P.g.nx - 1)));
             } else if (ft == FACE_OUTLET) {
                 // outlet ghost: post-collision f_d of (nx-1, y - c_dy, z - c_dz) of the previous
                 // step; across a free-slip face the source keeps y (z) and the direction mirrors
-                const int m = mir[d / 3], dd = mdir(d, m);
+                const int m = mir[d / 3], dd = mdir<FS>(d, m);
                 int ys = y - cy(d), zs = z - cz(d);
                 ys += ys < 0 ? P.g.ny : (ys >= P.g.ny ? -P.g.ny : 0);
                 zs += zs < 0 ? P.g.nz : (zs >= P.g.nz ? -P.g.nz : 0);
@@ -315,13 +325,13 @@ __device__ __forceinline__ void load_edge_t(const StepParams &P, int x, int y, i
     }
 }
 
-template <typename St, bool NB, bool INNER, int SIDE>
+template <typename St, bool NB, bool INNER, int SIDE, bool FS>
 __device__ __forceinline__ void store_edge_t(const StepParams &P, int x, int y, int z, int cell, const float (&h)[27]) {
     const bool xlo = SIDE != 1 && x == 0, xhi = SIDE != 0 && x == P.g.nx - 1, per = P.g.periodic[0];
     if (NB) {
         int off[9], mir[9];
         bool bb[9];
-        row_offsets<+1, INNER>(P.g, y, z, off, bb, mir);
+        row_offsets<+1, INNER, FS>(P.g, y, z, off, bb, mir);
 #pragma unroll
         for (int d = 0; d < 27; ++d) {
             const int j = d / 3;
@@ -331,7 +341,7 @@ __device__ __forceinline__ void store_edge_t(const StepParams &P, int x, int y, 
             // target across a no-slip face (or a non-periodic x face): the node's own slot
             const bool own = bb[j] || (xc && !per);
             const int idx = own ? cell : cell + off[j] + (xc ? -cx(d) * (P.g.nx - 1) : cx(d));
-            St *base = static_cast<St *>(own ? P.fpo[opp(d)] : P.fpo[mdir(d, mir[j])]);
+            St *base = static_cast<St *>(own ? P.fpo[opp(d)] : P.fpo[mdir<FS>(d, mir[j])]);
             Store<St>::st(base + idx, h[d]);
         }
     } else {
@@ -347,16 +357,17 @@ __device__ __forceinline__ void store_edge_t(const StepParams &P, int x, int y, 
 }
 
 // edge-strip node of a warp row: INNER when the row is away from the y/z faces (warp-uniform)
-template <typename St, bool NB, int SIDE>
+template <typename St, bool NB, int SIDE, bool FS>
 __device__ __forceinline__ void load_edge(const StepParams &P, int x, int y, int z, int cell, float (&h)[27]) {
-    if (y >= 1 && y <= P.g.ny - 2 && z >= 1 && z <= P.g.nz - 2) load_edge_t<St, NB, true, SIDE>(P, x, y, z, cell, h);
-    else load_edge_t<St, NB, false, SIDE>(P, x, y, z, cell, h);
+    // (the FS kernels see face rows, or every row of a grid without a main range: yz_rows serves both)
+    if (!FS && y >= 1 && y <= P.g.ny - 2 && z >= 1 && z <= P.g.nz - 2) load_edge_t<St, NB, true, SIDE, FS>(P, x, y, z, cell, h);
+    else load_edge_t<St, NB, false, SIDE, FS>(P, x, y, z, cell, h);
 }
 
-template <typename St, bool NB, int SIDE>
+template <typename St, bool NB, int SIDE, bool FS>
 __device__ __forceinline__ void store_edge(const StepParams &P, int x, int y, int z, int cell, const float (&h)[27]) {
-    if (y >= 1 && y <= P.g.ny - 2 && z >= 1 && z <= P.g.nz - 2) store_edge_t<St, NB, true, SIDE>(P, x, y, z, cell, h);
-    else store_edge_t<St, NB, false, SIDE>(P, x, y, z, cell, h);
+    if (!FS && y >= 1 && y <= P.g.ny - 2 && z >= 1 && z <= P.g.nz - 2) store_edge_t<St, NB, true, SIDE, FS>(P, x, y, z, cell, h);
+    else store_edge_t<St, NB, false, SIDE, FS>(P, x, y, z, cell, h);
 }
 
 // x of an edge-strip thread: SIDE 0 / 1 = left / right strip of a row with a main range,

@@ -2,5 +2,5 @@
 #include "lbm_step_kernels.cuh"
 
 namespace lbm {
-template cudaError_t launch_step_coll<COLL_BGK>(int storage, const StepParams &P, bool band, int part, cudaStream_t st);
+template cudaError_t launch_step_coll<COLL_BGK, false>(int storage, const StepParams &P, bool band, int part, cudaStream_t st);
 }  // namespace lbm

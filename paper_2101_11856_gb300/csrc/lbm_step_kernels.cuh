@@ -1,7 +1,8 @@
 // The fused step kernels (main range and edge strips) and their launchers, templated on the
-// storage type, the AA parity, the immersed-boundary force and the collision model.  Each
-// collision model is instantiated in its own translation unit (lbm_step_acm.cu,
-// lbm_step_bgk.cu, lbm_step_raw.cu) so that they compile in parallel.
+// storage type, the AA parity, the immersed-boundary force, the collision model and the
+// presence of a free-slip face.  Each collision model is instantiated in its own translation
+// units (lbm_step_acm.cu and lbm_step_acm_fs.cu, likewise bgk and raw) so that they compile in
+// parallel.
 #pragma once
 
 #include "lbm_models.cuh"
@@ -10,6 +11,11 @@
 namespace lbm {
 
 inline unsigned step_blocks(long long n, int threads) { return (unsigned)((n + threads - 1) / threads); }
+// grid of gx x n blocks with n folded into (y, z) (y at most 65535)
+inline dim3 face_grid(unsigned gx, long long n) {
+    const long long gy = n < 65535 ? (n > 0 ? n : 1) : 65535;
+    return dim3(gx, (unsigned)gy, (unsigned)((n + gy - 1) / gy > 0 ? (n + gy - 1) / gy : 1));
+}
 
 // the velocity field output of a step (for the smoke tracers; kernels with VOUT only)
 __device__ __forceinline__ void store_velocity(const StepParams &P, int cell, float ux, float uy, float uz) {
@@ -34,10 +40,25 @@ __device__ __forceinline__ void store_velocity(const StepParams &P, int cell, fl
 // lower register count keeps twice the warps resident)
 template <typename St> __host__ __device__ constexpr int main_nodes() { return sizeof(St) == 4 ? 2 : 1; }
 
-template <typename St, bool NB, bool BAND, int COLL, bool VOUT>
+// Without FS a block row is (blockIdx.y, blockIdx.z) = (y, z); the FS kernels (a grid with a
+// free-slip face) run over the face rows only (face_row of blockIdx.y + gridDim.y blockIdx.z),
+// while the kernels without FS skip those rows (inner_rows): the mirror logic costs registers,
+// which would otherwise slow every row.
+template <typename St, bool NB, bool BAND, int COLL, bool VOUT, bool FS>
 __global__ void __launch_bounds__(STEP_BX) k_step_main(StepParams P) {
-    const int y = blockIdx.y, z = blockIdx.z;
-    const bool inner = y >= 1 && y <= P.g.ny - 2 && z >= 1 && z <= P.g.nz - 2;   // uniform per block
+    int y, z;
+    bool inner;   // uniform per block
+    if constexpr (FS) {
+        const long long r = blockIdx.y + (long long)gridDim.y * blockIdx.z;
+        if (r >= face_rows(P.g)) return;
+        face_row(P.g, r, y, z);
+        inner = false;
+    } else {
+        y = blockIdx.y;
+        z = blockIdx.z;
+        inner = y >= 1 && y <= P.g.ny - 2 && z >= 1 && z <= P.g.nz - 2;
+        if (P.inner_rows && !inner) return;
+    }
     const int xend = P.g.nx - XEDGE;
     float Fx, Fy, Fz, rho, ux, uy, uz;
     if constexpr (main_nodes<St>() == 2) {
@@ -48,7 +69,7 @@ __global__ void __launch_bounds__(STEP_BX) k_step_main(StepParams P) {
         const int cell = x + P.g.nx * (y + P.g.ny * z);
         float h0[27], h1[27];
         if (!NB || inner) load_interior2<St, NB>(P, cell, two, h0, h1);
-        else load_yzface2<St>(P, y, z, cell, two, h0, h1);
+        else load_yzface2<St, FS>(P, y, z, cell, two, h0, h1);
         band_force<BAND>(P, cell, Fx, Fy, Fz);
         collide_model<COLL>(h0, Fx, Fy, Fz, P, rho, ux, uy, uz);
         if (VOUT) store_velocity(P, cell, ux, uy, uz);
@@ -58,18 +79,18 @@ __global__ void __launch_bounds__(STEP_BX) k_step_main(StepParams P) {
             if (VOUT) store_velocity(P, cell + 32, ux, uy, uz);
         }
         if (!NB || inner) store_interior2<St, NB>(P, cell, two, h0, h1);
-        else store_yzface2<St>(P, y, z, cell, two, h0, h1);
+        else store_yzface2<St, FS>(P, y, z, cell, two, h0, h1);
     } else {
         const int x = blockIdx.x * blockDim.x + threadIdx.x + XEDGE;
         if (x >= xend) return;
         const int cell = x + P.g.nx * (y + P.g.ny * z);
         float h[27];
         if (!NB || inner) load_interior<St, NB>(P, cell, h);
-        else load_yzface<St>(P, y, z, cell, h);
+        else load_yzface<St, FS>(P, y, z, cell, h);
         band_force<BAND>(P, cell, Fx, Fy, Fz);
         collide_model<COLL>(h, Fx, Fy, Fz, P, rho, ux, uy, uz);
         if (!NB || inner) store_interior<St, NB>(P, cell, h);
-        else store_yzface<St>(P, y, z, cell, h);
+        else store_yzface<St, FS>(P, y, z, cell, h);
         if (VOUT) store_velocity(P, cell, ux, uy, uz);
     }
 }
@@ -78,80 +99,96 @@ __global__ void __launch_bounds__(STEP_BX) k_step_main(StepParams P) {
 // threadIdx.y = y, blockIdx.z = z.  With a main range, blockIdx.x picks the left (0) or right
 // (1) strip (one launch for both: measured faster than a launch per side); short rows run the
 // SIDE = 2 kernel over consecutive warps.
-template <typename St, bool NB, bool BAND, int SIDE, int COLL, bool VOUT>
+template <typename St, bool NB, bool BAND, int SIDE, int COLL, bool VOUT, bool FS>
 __device__ __forceinline__ void edge_node(const StepParams &P, int y, int z) {
     const int x = edge_x<SIDE>(P.g);
     if (x >= P.g.nx) return;
     const int cell = x + P.g.nx * (y + P.g.ny * z);
     float h[27];
-    load_edge<St, NB, SIDE>(P, x, y, z, cell, h);
+    load_edge<St, NB, SIDE, FS>(P, x, y, z, cell, h);
     float Fx, Fy, Fz;
     band_force<BAND>(P, cell, Fx, Fy, Fz);
     float rho, ux, uy, uz;
     collide_model<COLL>(h, Fx, Fy, Fz, P, rho, ux, uy, uz);
-    store_edge<St, NB, SIDE>(P, x, y, z, cell, h);
+    store_edge<St, NB, SIDE, FS>(P, x, y, z, cell, h);
     if (VOUT) store_velocity(P, cell, ux, uy, uz);
 }
 
-template <typename St, bool NB, bool BAND, int COLL, bool VOUT>
+template <typename St, bool NB, bool BAND, int COLL, bool VOUT, bool FS>
 __global__ void __launch_bounds__(XEDGE * EDGE_ROWS) k_step_edges(StepParams P) {
-    const int y = blockIdx.y * EDGE_ROWS + threadIdx.y, z = blockIdx.z;
-    if (y >= P.g.ny) return;
-    if (blockIdx.x == 0) edge_node<St, NB, BAND, 0, COLL, VOUT>(P, y, z);
-    else edge_node<St, NB, BAND, 1, COLL, VOUT>(P, y, z);
+    int y, z;
+    if constexpr (FS) {   // face rows only (as k_step_main)
+        const long long r = (blockIdx.y + (long long)gridDim.y * blockIdx.z) * EDGE_ROWS + threadIdx.y;
+        if (r >= face_rows(P.g)) return;
+        face_row(P.g, r, y, z);
+    } else {
+        y = blockIdx.y * EDGE_ROWS + threadIdx.y;
+        z = blockIdx.z;
+        if (y >= P.g.ny) return;
+        if (P.inner_rows && !(y >= 1 && y <= P.g.ny - 2 && z >= 1 && z <= P.g.nz - 2)) return;
+    }
+    if (blockIdx.x == 0) edge_node<St, NB, BAND, 0, COLL, VOUT, FS>(P, y, z);
+    else edge_node<St, NB, BAND, 1, COLL, VOUT, FS>(P, y, z);
 }
 
-template <typename St, bool NB, bool BAND, int COLL, bool VOUT>
+template <typename St, bool NB, bool BAND, int COLL, bool VOUT, bool FS>
 __global__ void __launch_bounds__(XEDGE * EDGE_ROWS) k_step_rows(StepParams P) {
     const int y = blockIdx.y * EDGE_ROWS + threadIdx.y, z = blockIdx.z;
     if (y >= P.g.ny) return;
-    edge_node<St, NB, BAND, 2, COLL, VOUT>(P, y, z);
+    edge_node<St, NB, BAND, 2, COLL, VOUT, FS>(P, y, z);
 }
 
-template <typename St, bool NB, bool BAND, int COLL, bool VOUT>
+// FS (face rows of a grid with a free-slip face): the boundary part launches the edge strips and
+// the main range of those rows; there is no FS interior part
+template <typename St, bool NB, bool BAND, int COLL, bool VOUT, bool FS>
 cudaError_t launch_step_tt(const StepParams &P, int part, cudaStream_t st) {
     const Geometry &g = P.g;
+    // one warp per block when a row's main range fits in one warp's nodes (short rows would
+    // leave the second warp idle)
+    const int range = g.nx - 2 * XEDGE, per_warp = 32 * main_nodes<St>();
+    const int threads = range <= per_warp ? 32 : STEP_BX;
+    const unsigned xb = step_blocks(range, main_nodes<St>() * threads);
     if (part == STEP_BOUNDARY) {
         const dim3 block(XEDGE, EDGE_ROWS);
         if (has_interior(g)) {
-            const dim3 grid(2, step_blocks(g.ny, EDGE_ROWS), g.nz);
-            k_step_edges<St, NB, BAND, COLL, VOUT><<<grid, block, 0, st>>>(P);
+            const dim3 grid = FS ? face_grid(2, (face_rows(g) + EDGE_ROWS - 1) / EDGE_ROWS)
+                                 : dim3(2, step_blocks(g.ny, EDGE_ROWS), g.nz);
+            k_step_edges<St, NB, BAND, COLL, VOUT, FS><<<grid, block, 0, st>>>(P);
+            if (FS) k_step_main<St, NB, BAND, COLL, VOUT, FS><<<face_grid(xb, face_rows(g)), threads, 0, st>>>(P);
         } else {
             const dim3 grid(step_blocks(g.nx, XEDGE), step_blocks(g.ny, EDGE_ROWS), g.nz);
-            k_step_rows<St, NB, BAND, COLL, VOUT><<<grid, block, 0, st>>>(P);
+            k_step_rows<St, NB, BAND, COLL, VOUT, FS><<<grid, block, 0, st>>>(P);
         }
     } else if (has_interior(g)) {
-        // one warp per block when a row's main range fits in one warp's nodes (short rows would
-        // leave the second warp idle)
-        const int range = g.nx - 2 * XEDGE, per_warp = 32 * main_nodes<St>();
-        const int threads = range <= per_warp ? 32 : STEP_BX;
-        const dim3 grid(step_blocks(range, main_nodes<St>() * threads), g.ny, g.nz);
-        k_step_main<St, NB, BAND, COLL, VOUT><<<grid, threads, 0, st>>>(P);
+        if constexpr (FS) return cudaErrorInvalidValue;
+        else k_step_main<St, NB, BAND, COLL, VOUT, FS><<<dim3(xb, g.ny, g.nz), threads, 0, st>>>(P);
     }
     return cudaGetLastError();
 }
 
-template <typename St, int COLL, bool VOUT>
+template <typename St, int COLL, bool VOUT, bool FS>
 cudaError_t launch_step_v(const StepParams &P, bool band, int part, cudaStream_t st) {
     const bool nb = (P.t & 1) != 0;
-    if (nb) return band ? launch_step_tt<St, true, true, COLL, VOUT>(P, part, st)
-                        : launch_step_tt<St, true, false, COLL, VOUT>(P, part, st);
-    return band ? launch_step_tt<St, false, true, COLL, VOUT>(P, part, st)
-                : launch_step_tt<St, false, false, COLL, VOUT>(P, part, st);
+    if (nb) return band ? launch_step_tt<St, true, true, COLL, VOUT, FS>(P, part, st)
+                        : launch_step_tt<St, true, false, COLL, VOUT, FS>(P, part, st);
+    return band ? launch_step_tt<St, false, true, COLL, VOUT, FS>(P, part, st)
+                : launch_step_tt<St, false, false, COLL, VOUT, FS>(P, part, st);
 }
 
-template <typename St, int COLL>
+template <typename St, int COLL, bool FS>
 cudaError_t launch_step_t(const StepParams &P, bool band, int part, cudaStream_t st) {
-    return P.u_out ? launch_step_v<St, COLL, true>(P, band, part, st) : launch_step_v<St, COLL, false>(P, band, part, st);
+    return P.u_out ? launch_step_v<St, COLL, true, FS>(P, band, part, st)
+                   : launch_step_v<St, COLL, false, FS>(P, band, part, st);
 }
 
-// one part of one step for the collision model COLL; instantiated in lbm_step_<model>.cu
-template <int COLL>
+// one part of one step for the collision model COLL, on a grid with (FS) or without a free-slip
+// face; instantiated in lbm_step_<model>.cu and lbm_step_<model>_fs.cu
+template <int COLL, bool FS>
 cudaError_t launch_step_coll(int storage, const StepParams &P, bool band, int part, cudaStream_t st) {
     switch (storage) {
-        case 0: return launch_step_t<float, COLL>(P, band, part, st);
-        case 1: return launch_step_t<__half, COLL>(P, band, part, st);
-        default: return launch_step_t<__nv_bfloat16, COLL>(P, band, part, st);
+        case 0: return launch_step_t<float, COLL, FS>(P, band, part, st);
+        case 1: return launch_step_t<__half, COLL, FS>(P, band, part, st);
+        default: return launch_step_t<__nv_bfloat16, COLL, FS>(P, band, part, st);
     }
 }
 
