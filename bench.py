@@ -411,19 +411,25 @@ def main():
         o_rho = torch.empty(N, pin_memory=True)
         o_u = torch.empty(3, N, pin_memory=True)
         rounds = 2
+        phase = np.zeros(3)     # set_state (H2D + init), steps, macroscopic (+ D2H), seconds
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(rounds):
-            lbm.lbm_set_state(s.h, h_rho, h_u)
+            ta = time.perf_counter()
+            lbm.lbm_set_state(s.h, h_rho, h_u)          # returns after the copy from the host buffers
+            tb = time.perf_counter()
             s.step(batch)
-            lbm.lbm_macroscopic(s.h, o_rho, o_u)
             lbm.lbm_synchronize(s.h, 600.0)
+            tc = time.perf_counter()
+            lbm.lbm_macroscopic(s.h, o_rho, o_u)        # returns after the copy to the host buffers
+            phase += (tb - ta, tc - tb, time.perf_counter() - tc)
         dt = time.perf_counter() - t0
         e2e = {"value": world * N * batch * rounds / dt / 1e6, "unit": "MLUPS",
                "h2d_bytes_per_step": 16 * N / batch, "d2h_bytes_per_step": 16 * N / batch,
                "steps_per_batch": batch, "bytes_per_batch_each_way": 16 * N,
                "what": "per batch: lbm_set_state from pinned host rho,u (16 N bytes) + 100 steps + "
-                       "lbm_macroscopic to pinned host (16 N bytes); per-step bytes = batch bytes / 100"}
+                       "lbm_macroscopic to pinned host (16 N bytes); per-step bytes = batch bytes / 100",
+               "ms_per_batch": {k: round(1e3 * v / rounds, 2) for k, v in zip(("set_state", "steps", "macroscopic"), phase)}}
         del h_rho, h_u, o_rho, o_u
     s.close()
     del s
