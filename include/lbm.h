@@ -129,6 +129,24 @@ int lbm_step(lbm_ctx *h, int n);
  * staging buffer, see lbm_set_state). */
 int lbm_macroscopic(lbm_ctx *h, float *rho, float *u);
 
+/* lbm_set_state and lbm_macroscopic with the host copies queued instead of waited for, so
+ * that they overlap the steps queued around them (the step's inputs uploaded while the
+ * previous batch of steps runs, its outputs read back while the next one runs).
+ * lbm_set_state_async queues the copy of host rho (N floats) and u (3N floats) on the
+ * context's host-to-device copy stream into one of two device staging buffers (16 N bytes
+ * each, taken in turn; a buffer is reused once the initialisation that read it is done),
+ * then the initialisation f_i = f_eq_i(rho, u) on the context's stream behind the copy; the
+ * step counter is 0 for the steps queued after it.  lbm_macroscopic_async queues the density
+ * and Guo-shifted velocity of the current state (as lbm_macroscopic) into a device staging
+ * buffer (16 N bytes) on the context's stream and their copy to host rho / u (either may be
+ * NULL) on the device-to-host copy stream behind it.  The staging buffers and both copy
+ * streams are made on first use and kept by the context.  The host buffers must stay valid
+ * and unchanged (inputs) or unread (outputs) until lbm_synchronize returns; only page-locked
+ * host memory lets the copies overlap.  Device pointers behave as in the blocking calls.
+ * Errors: as lbm_set_state / lbm_macroscopic; LBM_ENOMEM for the staging buffers. */
+int lbm_set_state_async(lbm_ctx *h, const float *rho, const float *u);
+int lbm_macroscopic_async(lbm_ctx *h, float *rho, float *u);
+
 /* FP64 global diagnostics of the most recent step: total mass sum rho, total momentum
  * sum rho u, and the drag on the solid -sum_s g_s (Algorithm 2, total force).
  * Any pointer may be NULL.  Host pointers; the call waits for the stream. */
@@ -152,8 +170,9 @@ long long lbm_time(const lbm_ctx *h);
 /* Scan the most recent macroscopic state for non-finite values: LBM_OK or LBM_EUNSTABLE. */
 int lbm_check(lbm_ctx *h);
 
-/* Wait for the context's stream with a wall-clock limit in seconds (<= 0: no limit),
- * polling with cudaEventQuery: LBM_OK, LBM_ETIMEOUT or LBM_ECUDA. */
+/* Wait for the context's stream and the copy streams of the asynchronous host transfers
+ * with a wall-clock limit in seconds (<= 0: no limit), polling with cudaEventQuery:
+ * LBM_OK, LBM_ETIMEOUT or LBM_ECUDA. */
 int lbm_synchronize(lbm_ctx *h, double timeout_s);
 
 /* Loss of the adjoint problem: L = w_drag * (1/n) sum_{t=1..n} D_x(t)

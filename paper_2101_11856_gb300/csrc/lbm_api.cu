@@ -187,6 +187,7 @@ int lbm_create(lbm_ctx **out, int nx, int ny, int nz, double nu, const double fo
 int lbm_destroy(lbm_ctx *h) {
     if (!h) return LBM_OK;
     if (h->f) cudaStreamSynchronize(h->stream);
+    free_async(h);
     free_solid(h);
     free_tracers(h);
     dev_free(h->stage);
@@ -226,6 +227,40 @@ int lbm_set_state(lbm_ctx *h, const float *rho, const float *u) {
         CK(launch_init(h->storage, P, drho, du, h->stream));
     }
     if (!dev) CK(cudaStreamSynchronize(h->stream));   // the caller may reuse its host buffers
+    h->t = 0;
+    h->has_state = true;
+    return LBM_OK;
+}
+
+int lbm_set_state_async(lbm_ctx *h, const float *rho, const float *u) {
+    if (!h) return fail(nullptr, LBM_EINVAL, "null context");
+    if (!rho || !u) return fail(h, LBM_EINVAL, "rho and u are required");
+    const float *drho = rho, *du = u;
+    const bool dev = is_device_ptr(rho) && is_device_ptr(u);
+    const int k = h->stage_in_next;
+    if (!dev) {
+        int rc = ensure_async(h);
+        if (rc) return rc;
+        if (!h->stage_in[k] && (rc = dev_alloc(h, &h->stage_in[k], (size_t)4 * h->N))) return rc;
+        // the copy waits until the initialisation that last read this buffer is done, and the
+        // initialisation below waits for the copy
+        CK(cudaStreamWaitEvent(h->h2d, h->in_free[k], 0));
+        CK(cudaMemcpyAsync(h->stage_in[k], rho, (size_t)h->N * sizeof(float), cudaMemcpyDefault, h->h2d));
+        CK(cudaMemcpyAsync(h->stage_in[k] + h->N, u, (size_t)3 * h->N * sizeof(float), cudaMemcpyDefault, h->h2d));
+        CK(cudaEventRecord(h->in_ready[k], h->h2d));
+        CK(cudaStreamWaitEvent(h->stream, h->in_ready[k], 0));
+        drho = h->stage_in[k];
+        du = h->stage_in[k] + h->N;
+    }
+    StepParams P = make_params(h, 0);
+    {
+        Timed tm(h, LBM_KERNEL_OTHER);
+        CK(launch_init(h->storage, P, drho, du, h->stream));
+    }
+    if (!dev) {
+        CK(cudaEventRecord(h->in_free[k], h->stream));
+        h->stage_in_next = k ^ 1;
+    }
     h->t = 0;
     h->has_state = true;
     return LBM_OK;
@@ -390,6 +425,36 @@ int lbm_macroscopic(lbm_ctx *h, float *rho, float *u) {
     return LBM_OK;
 }
 
+int lbm_macroscopic_async(lbm_ctx *h, float *rho, float *u) {
+    int rc = require_state(h);
+    if (rc) return rc;
+    if (!rho && !u) return LBM_OK;
+    const bool dr = !rho || is_device_ptr(rho), du = !u || is_device_ptr(u);
+    float *drho = rho, *duu = u;
+    const bool host = !dr || !du;
+    if (host) {
+        if ((rc = ensure_async(h))) return rc;
+        if (!h->stage_out && (rc = dev_alloc(h, &h->stage_out, (size_t)4 * h->N))) return rc;
+        // the moments wait until the previous copy out of the staging buffer is done
+        CK(cudaStreamWaitEvent(h->stream, h->out_free, 0));
+        if (!dr) drho = h->stage_out;
+        if (!du) duu = h->stage_out + h->N;
+    }
+    StepParams P = make_params(h, h->t);
+    {
+        Timed tm(h, LBM_KERNEL_OTHER);
+        CK(launch_macro(h->storage, P, h->S > 0, h->t > 0, drho, duu, nullptr, nullptr, nullptr, h->stream));
+    }
+    if (host) {
+        CK(cudaEventRecord(h->out_ready, h->stream));
+        CK(cudaStreamWaitEvent(h->d2h, h->out_ready, 0));
+        if (!dr) CK(cudaMemcpyAsync(rho, drho, (size_t)h->N * sizeof(float), cudaMemcpyDefault, h->d2h));
+        if (!du) CK(cudaMemcpyAsync(u, duu, (size_t)3 * h->N * sizeof(float), cudaMemcpyDefault, h->d2h));
+        CK(cudaEventRecord(h->out_free, h->d2h));
+    }
+    return LBM_OK;
+}
+
 int lbm_reductions(lbm_ctx *h, double *mass, double mom[3], double drag[3]) {
     int rc = require_state(h);
     if (rc) return rc;
@@ -511,25 +576,41 @@ int lbm_check(lbm_ctx *h) {
 
 int lbm_synchronize(lbm_ctx *h, double timeout_s) {
     if (!h) return fail(nullptr, LBM_EINVAL, "null context");
-    cudaEvent_t e;
-    CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-    CK(cudaEventRecord(e, h->stream));
+    // the context's stream and, once made, the copy streams of the asynchronous transfers
+    cudaStream_t streams[3] = {h->stream, h->h2d, h->d2h};
+    const int ns = h->h2d ? 3 : 1;
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    auto destroy = [&]() {
+        for (auto &e : ev)
+            if (e) cudaEventDestroy(e);
+    };
+    for (int i = 0; i < ns; ++i) {
+        cudaError_t c = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
+        if (c == cudaSuccess) c = cudaEventRecord(ev[i], streams[i]);
+        if (c != cudaSuccess) {
+            destroy();
+            return fail(h, LBM_ECUDA, std::string("event record failed: ") + cudaGetErrorString(c));
+        }
+    }
     const auto t0 = std::chrono::steady_clock::now();
-    for (;;) {
-        cudaError_t q = cudaEventQuery(e);
-        if (q == cudaSuccess) break;
+    for (int i = 0; i < ns;) {
+        cudaError_t q = cudaEventQuery(ev[i]);
+        if (q == cudaSuccess) {
+            ++i;
+            continue;
+        }
         if (q != cudaErrorNotReady) {
-            cudaEventDestroy(e);
+            destroy();
             return fail(h, LBM_ECUDA, std::string("stream failed: ") + cudaGetErrorString(q));
         }
         const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         if (timeout_s > 0 && el > timeout_s) {
-            cudaEventDestroy(e);
+            destroy();
             return fail(h, LBM_ETIMEOUT, "stream did not finish within the time limit");
         }
         std::this_thread::sleep_for(std::chrono::microseconds(50));
     }
-    cudaEventDestroy(e);
+    destroy();
     return LBM_OK;
 }
 

@@ -87,6 +87,18 @@ struct lbm_ctx {
     // device workspace of lbm_adjoint (pointer, bytes), reused by later calls
     std::vector<std::pair<void *, size_t>> adj_ws;
 
+    // asynchronous host transfers (lbm_set_state_async, lbm_macroscopic_async), made on first
+    // use: a host-to-device and a device-to-host copy stream, two input staging buffers taken
+    // in turn (rho | u, 4 N floats each) and one output staging buffer; in_ready[k] = copy into
+    // buffer k done, in_free[k] = the initialisation that read it done, out_ready = moments
+    // written, out_free = copy out done
+    cudaStream_t h2d = nullptr, d2h = nullptr;
+    float *stage_in[2] = {nullptr, nullptr};
+    int stage_in_next = 0;
+    cudaEvent_t in_ready[2] = {nullptr, nullptr}, in_free[2] = {nullptr, nullptr};
+    float *stage_out = nullptr;
+    cudaEvent_t out_ready = nullptr, out_free = nullptr;
+
     std::string err;
 };
 
@@ -245,6 +257,37 @@ inline int ensure_stage(lbm_ctx *h, size_t floats) {
     if (rc) return rc;
     h->stage_cap = floats;
     return LBM_OK;
+}
+
+// the copy streams and events of the asynchronous host transfers
+inline int ensure_async(lbm_ctx *h) {
+    if (h->h2d) return LBM_OK;
+    CK(cudaStreamCreateWithFlags(&h->h2d, cudaStreamNonBlocking));
+    CK(cudaStreamCreateWithFlags(&h->d2h, cudaStreamNonBlocking));
+    for (int k = 0; k < 2; ++k) {
+        CK(cudaEventCreateWithFlags(&h->in_ready[k], cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&h->in_free[k], cudaEventDisableTiming));
+    }
+    CK(cudaEventCreateWithFlags(&h->out_ready, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&h->out_free, cudaEventDisableTiming));
+    return LBM_OK;
+}
+
+inline void free_async(lbm_ctx *h) {
+    if (!h->h2d) return;
+    cudaStreamSynchronize(h->h2d);
+    cudaStreamSynchronize(h->d2h);
+    for (int k = 0; k < 2; ++k) {
+        dev_free(h->stage_in[k]);
+        cudaEventDestroy(h->in_ready[k]);
+        cudaEventDestroy(h->in_free[k]);
+    }
+    dev_free(h->stage_out);
+    cudaEventDestroy(h->out_ready);
+    cudaEventDestroy(h->out_free);
+    cudaStreamDestroy(h->h2d);
+    cudaStreamDestroy(h->d2h);
+    h->h2d = h->d2h = nullptr;
 }
 
 inline int ensure_partial(lbm_ctx *h, size_t doubles) {

@@ -58,6 +58,8 @@ _SIGS = {
     "lbm_set_solids": (C.c_int, [C.c_void_p, C.c_void_p, C.c_longlong, C.c_void_p, C.c_void_p]),
     "lbm_step": (C.c_int, [C.c_void_p, C.c_int]),
     "lbm_macroscopic": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "lbm_set_state_async": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "lbm_macroscopic_async": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "lbm_reductions": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "lbm_ib_forces": (C.c_int, [C.c_void_p, C.c_void_p]),
     "lbm_populations": (C.c_int, [C.c_void_p, C.c_void_p]),
@@ -122,6 +124,22 @@ def _ptr(a):
     return C.c_void_p(arr.ctypes.data), arr
 
 
+def _ptr_nocopy(a):
+    """Pointer of a float32 array that the library may read or write after the call returns
+    (asynchronous transfers): a C-contiguous float32 numpy array or torch tensor, passed as is;
+    anything that would need a converted temporary is refused."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        import torch
+        if a.dtype != torch.float32 or not a.is_contiguous():
+            raise ValueError("asynchronous transfers need a contiguous float32 tensor")
+        return C.c_void_p(a.data_ptr())
+    if not isinstance(a, np.ndarray) or a.dtype != np.float32 or not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("asynchronous transfers need a C-contiguous float32 numpy array")
+    return C.c_void_p(a.ctypes.data)
+
+
 # ---- the C functions under their own names -------------------------------------------
 
 def lbm_config_default() -> lbm_config:
@@ -163,6 +181,16 @@ def lbm_macroscopic(h, rho, u):
     pr, kr = _ptr(rho) if rho is not None else (None, None)
     pu, ku = _ptr(u) if u is not None else (None, None)
     _check(library().lbm_macroscopic(h, pr, pu), h)
+
+
+def lbm_set_state_async(h, rho, u):
+    """The caller keeps rho and u alive and unchanged until lbm_synchronize returns."""
+    _check(library().lbm_set_state_async(h, _ptr_nocopy(rho), _ptr_nocopy(u)), h)
+
+
+def lbm_macroscopic_async(h, rho, u):
+    """rho and u (either may be None) are filled when lbm_synchronize returns."""
+    _check(library().lbm_macroscopic_async(h, _ptr_nocopy(rho), _ptr_nocopy(u)), h)
 
 
 def lbm_reductions(h):
@@ -365,6 +393,17 @@ class Solver:
         u = np.empty((3,) + self.shape, np.float32)
         lbm_macroscopic(self.h, rho, u)
         return rho, u
+
+    def set_state_async(self, rho, u):
+        """Queue the upload and initialisation (keep rho, u unchanged until synchronize)."""
+        lbm_set_state_async(self.h, rho, u)
+
+    def macroscopic_async(self, rho, u):
+        """Queue the moments and their copy into rho, u (filled at synchronize)."""
+        lbm_macroscopic_async(self.h, rho, u)
+
+    def synchronize(self, timeout_s=0.0):
+        lbm_synchronize(self.h, timeout_s)
 
     def reductions(self):
         return lbm_reductions(self.h)

@@ -78,3 +78,21 @@ def test_create_rejects_bad_arguments_without_touching_the_gpu(lib):
         with pytest.raises(lbm.LBMError) as e:
             lbm.lbm_create(4, 4, 4, 0.1, cfg=bad)
         assert e.value.code == lbm.LBM_EINVAL
+
+
+def test_async_binding_refuses_converted_temporaries():
+    """The asynchronous transfers read or write the caller's buffer after the call returns, so
+    the binding passes float32 C-contiguous buffers as they are and refuses anything that would
+    need a temporary copy (which could be freed before the transfer runs)."""
+    import numpy as np
+    import torch
+    from paper_2101_11856_gb300.lbm import _ptr_nocopy
+    a = np.zeros((4, 5), np.float32)
+    assert _ptr_nocopy(a).value == a.ctypes.data
+    t = torch.zeros(6)
+    assert _ptr_nocopy(t).value == t.data_ptr()
+    assert _ptr_nocopy(None) is None
+    for bad in (np.zeros(4), np.zeros((4, 6), np.float32)[:, ::2], torch.zeros(4, dtype=torch.float64),
+                torch.zeros(4, 6)[:, ::2], [1.0, 2.0]):
+        with pytest.raises(ValueError):
+            _ptr_nocopy(bad)
