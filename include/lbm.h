@@ -118,7 +118,9 @@ int lbm_set_solids(lbm_ctx *h, const float *samples, long long count,
  * fused stream+collide kernel over the nodes 32 <= x < nx-32, one over the two 32-node
  * edge strips of every row (the inlet/outlet/x-periodic rules), and three small
  * immersed-boundary kernels when a solid is installed (plus the re-pose of a moving solid
- * and the tracer advection when those are set).
+ * and the tracer advection when those are set).  On a grid with a free-slip face the rows
+ * on a y or z face run in two more kernels (strips and main range) that carry the mirror
+ * rule, and the first two skip them.
  * Errors: LBM_ESTATE before lbm_set_state, LBM_ECUDA. */
 int lbm_step(lbm_ctx *h, int n);
 
