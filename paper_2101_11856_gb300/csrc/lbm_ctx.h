@@ -259,17 +259,29 @@ inline int ensure_stage(lbm_ctx *h, size_t floats) {
     return LBM_OK;
 }
 
-// the copy streams and events of the asynchronous host transfers
+// the copy streams and events of the asynchronous host transfers, all or none
 inline int ensure_async(lbm_ctx *h) {
     if (h->h2d) return LBM_OK;
-    CK(cudaStreamCreateWithFlags(&h->h2d, cudaStreamNonBlocking));
-    CK(cudaStreamCreateWithFlags(&h->d2h, cudaStreamNonBlocking));
-    for (int k = 0; k < 2; ++k) {
-        CK(cudaEventCreateWithFlags(&h->in_ready[k], cudaEventDisableTiming));
-        CK(cudaEventCreateWithFlags(&h->in_free[k], cudaEventDisableTiming));
+    cudaStream_t st[2] = {nullptr, nullptr};
+    cudaEvent_t ev[6] = {};
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaStreamCreateWithFlags(&st[i], cudaStreamNonBlocking);
+    for (int i = 0; i < 6 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        for (auto x : ev)
+            if (x) cudaEventDestroy(x);
+        for (auto x : st)
+            if (x) cudaStreamDestroy(x);
+        return fail(h, LBM_ECUDA, std::string("copy streams: ") + cudaGetErrorString(e));
     }
-    CK(cudaEventCreateWithFlags(&h->out_ready, cudaEventDisableTiming));
-    CK(cudaEventCreateWithFlags(&h->out_free, cudaEventDisableTiming));
+    h->h2d = st[0];
+    h->d2h = st[1];
+    h->in_ready[0] = ev[0];
+    h->in_ready[1] = ev[1];
+    h->in_free[0] = ev[2];
+    h->in_free[1] = ev[3];
+    h->out_ready = ev[4];
+    h->out_free = ev[5];
     return LBM_OK;
 }
 
