@@ -54,3 +54,17 @@ def test_reference_arm_under_torchrun_two_ranks():
     assert len(lines) == 1
     rec = json.loads(lines[0])
     assert rec["impl"] == "reference" and rec["value"] > 0 and rec["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_main_kernel_cells():
+    """The roofline's cells per main-kernel launch: the main range 32 <= x < nx - 32 of every
+    row, or of the rows off the y/z faces on a grid with a free-slip face (those rows run with
+    the boundary kernels); no main range below nx = 65."""
+    sys.path.insert(0, ROOT)
+    import bench
+    city = ("inlet", "outlet", "noslip", "freeslip", "periodic", "periodic")
+    closed = ("inlet", "outlet", "noslip", "noslip", "periodic", "periodic")
+    assert bench.main_cells(1200, 250, 840, city) == 1136 * 248 * 838 == 236088064
+    assert bench.main_cells(1200, 250, 840, closed) == 1136 * 250 * 840
+    assert bench.main_cells(65, 2, 7, city) == 0            # every row on a face
+    assert bench.main_cells(64, 9, 9, closed) == 0          # no main range
