@@ -12,6 +12,10 @@ Per step t (1-based), starting from the post-collision populations f(t-1):
    nodes (Eq. 8), and the drag on the solid is -sum_s g_s;
 4. collision with the total force F = F_body + F_IB (Eqs. 4-5; ``collision``).
 
+``ib_lag`` (a reading for the fused variant of the step, not the paper's order): step 3 takes
+rho* and u_IB from the streamed populations of the previous step instead of this one's (this
+one's for the first step after set_state or set_solids); everything else is unchanged.
+
 The macroscopic fields reported for step t are rho* and the Guo-shifted velocity
 (j + F/2)/rho* used by that collision; before the first step they are the initial fields.
 The initial populations are the equilibrium of the initial fields, taken as the
@@ -48,6 +52,7 @@ class Problem:
     omega_bulk: float = 1.0
     omega_hi: tuple = (1.0, 1.0, 1.0, 1.0)
     collision: str = "factorised"          # or "matrix" (same operator), "bgk", "raw" (comparison models)
+    ib_lag: bool = False                   # step-lagged immersed boundary (see the module docstring)
     rates: dict = field(init=False)
 
     def __post_init__(self):
@@ -91,28 +96,31 @@ def collide(p: Problem, fstar, F):
     return col.collide_factorised(fstar, F, p.rates)
 
 
-def step(p: Problem, f: torch.Tensor, t: int, coef=None, solids=None):
+def step(p: Problem, f: torch.Tensor, t: int, coef=None, solids=None, ib_moments=None):
     """Advance post-collision f(t-1) to f(t).  ``solids`` = (X (S,3), area (S,), u_b (3,S)).
+    ``ib_moments`` = (rho*, u_IB) the immersed boundary interpolates instead of this step's
+    (the step-lagged variant), or None.
 
-    Returns (f(t), diagnostics dict with rho, u, F, g, drag).
+    Returns (f(t), diagnostics dict with rho, u, F, g, drag and this step's rho*, u_IB).
     """
     wall = inlet_velocity(p, t, coef) if "inlet" in p.faces else None
     fstar = stream(f, p.faces, wall, p.rho0)
     rho, j = col.density_momentum(fstar)
     F = torch.tensor(p.forcing, dtype=DTYPE).view(3, 1, 1, 1).expand(3, *p.shape)
+    u_ib = col.guo_velocity(rho, j, F)
     g = None
     drag = torch.zeros(3, dtype=DTYPE)
     if solids is not None:
         X, area, u_b = solids
-        u_ib = col.guo_velocity(rho, j, F)
-        rho_s = ib.interpolate(rho, X)
-        u_s = ib.interpolate(u_ib, X)
+        rho_i, u_i = (rho, u_ib) if ib_moments is None else ib_moments
+        rho_s = ib.interpolate(rho_i, X)
+        u_s = ib.interpolate(u_i, X)
         g = ib.penalty_force(rho_s, u_s, u_b, area)
         F = F + ib.spread_scatter(g, X, p.shape)
         drag = -g.sum(1)
     fnew = collide(p, fstar, F)
     u = col.guo_velocity(rho, j, F)
-    return fnew, dict(rho=rho, u=u, F=F, g=g, drag=drag)
+    return fnew, dict(rho=rho, u=u, F=F, g=g, drag=drag, u_ib=u_ib)
 
 
 class OracleSolver:
@@ -127,6 +135,7 @@ class OracleSolver:
         self.t = 0
         self.f = None
         self.diag = None
+        self.ib_moments = None                # (rho*, u_IB) of the last step's streamed populations
 
     def set_state(self, rho, u):
         rho = torch.as_tensor(np.asarray(rho), dtype=DTYPE)
@@ -134,6 +143,7 @@ class OracleSolver:
         self.f = col.equilibrium(rho, u)
         self.t = 0
         self.diag = dict(rho=rho.clone(), u=u.clone(), drag=torch.zeros(3, dtype=DTYPE), g=None)
+        self.ib_moments = None
 
     def set_solids(self, X, area=None, u_b=None):
         X = torch.as_tensor(np.asarray(X), dtype=DTYPE)
@@ -142,6 +152,7 @@ class OracleSolver:
         u_b = torch.zeros(3, S, dtype=DTYPE) if u_b is None else torch.as_tensor(np.asarray(u_b), dtype=DTYPE).T
         self.solids = (X, area, u_b)
         self.motion = None
+        self.ib_moments = None
 
     def set_motion(self, motion):
         """Prescribed rigid motion (c0, V, axis, w) of the current samples (``motion``)."""
@@ -161,7 +172,9 @@ class OracleSolver:
             self.t += 1
             if self.motion is not None:
                 self._pose(self.t - 1)        # Algorithm 2 (c): the update after the previous IB stage
-            self.f, self.diag = step(self.p, self.f, self.t, self.coef, self.solids)
+            lagged = self.ib_moments if self.p.ib_lag else None
+            self.f, self.diag = step(self.p, self.f, self.t, self.coef, self.solids, lagged)
+            self.ib_moments = (self.diag["rho"], self.diag["u_ib"])
 
     def torque(self, center):
         """Torque on the solid about ``center`` from the last step's samples and forces."""
