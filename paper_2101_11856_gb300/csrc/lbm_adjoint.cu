@@ -522,6 +522,23 @@ template <typename F> cudaError_t with_storage(int storage, F &&fn) {
 // the adjoint's device workspace, kept by the context between calls: the k-th request of a
 // call reuses the k-th buffer when it is large enough (calls with the same sizes allocate
 // nothing after the first)
+// the context's IB arrays (band moments, penalty forces, spread forces) pointed at other storage
+// for a while: the recompute of a segment keeps each step's values, which the backward step then
+// reads instead of computing them again; the context's own arrays come back on every exit
+struct IBArrays {
+    lbm_ctx *h;
+    float *rho, *u, *g, *F;
+    explicit IBArrays(lbm_ctx *h_) : h(h_), rho(h_->band_rho), u(h_->band_u), g(h_->g), F(h_->bandF) {}
+    void point(float *r, float *uu, float *gg, float *ff) {
+        h->band_rho = r;
+        h->band_u = uu;
+        h->g = gg;
+        h->bandF = ff;
+    }
+    void restore() { point(rho, u, g, F); }
+    ~IBArrays() { restore(); }
+};
+
 struct AdjBuffers {
     lbm_ctx *h;
     size_t next = 0;
@@ -600,6 +617,18 @@ extern "C" int lbm_adjoint(lbm_ctx *h, int n, int K, const lbm_loss *loss, doubl
     if (S > 0 && ((rc = B.get(h, &dX, (size_t)3 * S)) || (rc = B.get(h, &dF_band, (size_t)3 * nb)) ||
                   (rc = B.get(h, &adj_band, (size_t)4 * nb)) || (rc = B.get(h, &adj_samp, (size_t)4 * S))))
         return rc;
+    // IB values of the recomputed steps of a segment (all but its last step): slot j holds those
+    // of the step from state t0 + j
+    float *k_rho = nullptr, *k_u = nullptr, *k_g = nullptr, *k_F = nullptr;
+    const size_t nslot = (size_t)(K - 1);
+    if (S > 0 && nslot > 0 &&
+        ((rc = B.get(h, &k_rho, nslot * nb)) || (rc = B.get(h, &k_u, nslot * 3 * nb)) ||
+         (rc = B.get(h, &k_g, nslot * 3 * S)) || (rc = B.get(h, &k_F, nslot * 3 * nb))))
+        return rc;
+    IBArrays ib(h);
+    auto point_slot = [&](long long j) {
+        ib.point(k_rho + j * nb, k_u + j * 3 * nb, k_g + j * 3 * S, k_F + j * 3 * nb);
+    };
     const int fblk = force_sum_blocks();
     StepParams P0 = make_params(h, h->t);
     const long long mblk = macro_blocks(P0);
@@ -647,11 +676,16 @@ extern "C" int lbm_adjoint(lbm_ctx *h, int n, int K, const lbm_loss *loss, doubl
         // recompute the segment's states out of place: seg[k] = f_{t0 + k}
         CK(cudaMemcpyAsync(seg[0], ckpt[sgi], state_bytes, cudaMemcpyDeviceToDevice, st));
         for (int k = 0; k + 1 < len; ++k) {
+            if (S > 0) point_slot(k);
             StepParams Pf = make_params(h, t0 + k + 1);
             point_states(Pf, h, seg[k], seg[k + 1]);
             if ((rc = step_with(h, Pf))) return rc;
         }
         for (long long t = t0 + len; t > t0; --t) {
+            const long long j = t - 1 - t0;
+            const bool kept = S > 0 && j + 1 < len;   // the recompute left this step's IB values
+            if (kept) point_slot(j);
+            else ib.restore();
             StepParams P = make_params(h, t);
             point_states(P, h, seg[t - 1 - t0], seg[t - 1 - t0]);
             AdjParams A{};
@@ -666,9 +700,11 @@ extern "C" int lbm_adjoint(lbm_ctx *h, int n, int K, const lbm_loss *loss, doubl
             A.ke_x1 = loss->ke_x1;
             const bool nbp = (t & 1) != 0;
             if (S > 0) {
-                CK(launch_band_moments(h->storage, P, h->band_cell, h->band_rho, h->band_u, st));
-                CK(launch_ib_interp(S, nb, h->X, h->area, h->ub, h->corner_band, h->band_rho, h->band_u, h->g, st));
-                CK(launch_ib_spread(S, nb, nullptr, h->X, h->g, h->base_nbr, h->cstart, h->ccount, h->bandF, st));
+                if (!kept) {
+                    CK(launch_band_moments(h->storage, P, h->band_cell, h->band_rho, h->band_u, st));
+                    CK(launch_ib_interp(S, nb, h->X, h->area, h->ub, h->corner_band, h->band_rho, h->band_u, h->g, st));
+                    CK(launch_ib_spread(S, nb, nullptr, h->X, h->g, h->base_nbr, h->cstart, h->ccount, h->bandF, st));
+                }
                 CK(with_storage(h->storage, [&](auto tag) {
                     using St = decltype(tag);
                     if (nbp) k_adj_band_force<St, true><<<nblocks(nb, 128), 128, 0, st>>>(P, A, h->band_cell);
@@ -692,6 +728,7 @@ extern "C" int lbm_adjoint(lbm_ctx *h, int n, int K, const lbm_loss *loss, doubl
             std::swap(lam_cur, lam_prev);
         }
     }
+    ib.restore();
     // the forward pass left the state at t_start + n; restore its IB diagnostics
     if (S > 0) {
         CK(cudaMemcpyAsync(h->g, g_last, 3 * S * sizeof(float), cudaMemcpyDeviceToDevice, st));
