@@ -539,6 +539,27 @@ struct IBArrays {
     ~IBArrays() { restore(); }
 };
 
+// one forward step as lbm_step takes it (moving solids excluded by lbm_adjoint), reading the
+// state buffer src and writing the state buffer dst, or the context's own state for dst = NULL
+int adj_forward_step(lbm_ctx *h, void *src, void *dst) {
+    const long long t = h->t + 1;
+    int rc;
+    StepParams P = make_params(h, t);
+    if (h->ntracer) P.u_out = h->tracer_u;
+    if (dst) {
+        point_states(P, h, src, dst);
+    } else {
+        const size_t pb = (size_t)h->plane * h->esize;
+        P.f = src;
+        for (int d = 0; d < 27; ++d) P.fp[d] = static_cast<char *>(src) + d * pb;
+        P.outlet = h->outlet ? static_cast<char *>(src) + 27 * pb : nullptr;
+    }
+    if ((rc = step_with(h, P))) return rc;
+    if ((rc = advect_tracers(h, t))) return rc;
+    h->t = t;
+    return LBM_OK;
+}
+
 struct AdjBuffers {
     lbm_ctx *h;
     size_t next = 0;
@@ -606,7 +627,8 @@ extern "C" int lbm_adjoint(lbm_ctx *h, int n, int K, const lbm_loss *loss, doubl
     AdjBuffers B(h);
     int rc;
     std::vector<char *> ckpt(nck), seg(K);
-    for (int i = 0; i < nck; ++i) if ((rc = B.get(h, &ckpt[i], state_bytes))) return rc;
+    // checkpoints of the segments but the last, whose states the forward pass keeps itself
+    for (int i = 0; i + 1 < nck; ++i) if ((rc = B.get(h, &ckpt[i], state_bytes))) return rc;
     for (int i = 0; i < K; ++i) if ((rc = B.get(h, &seg[i], state_bytes))) return rc;
     float *lamA, *lamB, *blam = nullptr, *dF_band = nullptr, *adj_band = nullptr, *adj_samp = nullptr;
     double *s_inlet, *dX = nullptr, *acc;
@@ -639,14 +661,28 @@ extern "C" int lbm_adjoint(lbm_ctx *h, int n, int K, const lbm_loss *loss, doubl
     if (dX) CK(cudaMemsetAsync(dX, 0, 3 * S * sizeof(double), st));
     CK(cudaMemsetAsync(lamA, 0, (size_t)27 * N * sizeof(float), st));
 
-    // forward pass: checkpoints, drag accumulation, final kinetic energy
+    // forward pass: checkpoints, drag accumulation, final kinetic energy.  The last segment runs
+    // out of place through the segment buffers and keeps its IB values, as its recompute would
+    // (the backward pass then starts without one); its last step writes the context's state.
     const long long t_start = h->t;
+    const int last0 = (nck - 1) * K, last_len = n - last0;
     for (int i = 0; i < n; ++i) {
-        if (i % K == 0) {
-            CK(cudaMemcpyAsync(ckpt[i / K], h->f, pop_bytes, cudaMemcpyDeviceToDevice, st));
-            if (out_bytes) CK(cudaMemcpyAsync(ckpt[i / K] + pop_bytes, h->outlet, out_bytes, cudaMemcpyDeviceToDevice, st));
+        char *keep = i < last0 ? (i % K == 0 ? ckpt[i / K] : nullptr) : (i == last0 ? seg[0] : nullptr);
+        if (keep) {
+            CK(cudaMemcpyAsync(keep, h->f, pop_bytes, cudaMemcpyDeviceToDevice, st));
+            if (out_bytes) CK(cudaMemcpyAsync(keep + pop_bytes, h->outlet, out_bytes, cudaMemcpyDeviceToDevice, st));
         }
-        if ((rc = lbm_step(h, 1))) return rc;
+        if (i < last0) {
+            if ((rc = lbm_step(h, 1))) return rc;
+        } else {
+            const int k = i - last0;
+            const bool inner = k + 1 < last_len;
+            if (S > 0) {
+                if (inner) point_slot(k);
+                else ib.restore();
+            }
+            if ((rc = adj_forward_step(h, seg[k], inner ? seg[k + 1] : nullptr))) return rc;
+        }
         if (S > 0) {
             CK(launch_sum_forces(S, h->g, h->partial, st));
             k_finalize_add<<<1, 256, 0, st>>>(h->partial, fblk, 3, acc);
@@ -673,13 +709,16 @@ extern "C" int lbm_adjoint(lbm_ctx *h, int n, int K, const lbm_loss *loss, doubl
     for (int sgi = nck - 1; sgi >= 0; --sgi) {
         const long long t0 = t_start + (long long)sgi * K;
         const int len = (int)std::min<long long>(K, t_start + n - t0);
-        // recompute the segment's states out of place: seg[k] = f_{t0 + k}
-        CK(cudaMemcpyAsync(seg[0], ckpt[sgi], state_bytes, cudaMemcpyDeviceToDevice, st));
-        for (int k = 0; k + 1 < len; ++k) {
-            if (S > 0) point_slot(k);
-            StepParams Pf = make_params(h, t0 + k + 1);
-            point_states(Pf, h, seg[k], seg[k + 1]);
-            if ((rc = step_with(h, Pf))) return rc;
+        // recompute the segment's states out of place: seg[k] = f_{t0 + k} (the last segment's
+        // are there from the forward pass)
+        if (sgi + 1 < nck) {
+            CK(cudaMemcpyAsync(seg[0], ckpt[sgi], state_bytes, cudaMemcpyDeviceToDevice, st));
+            for (int k = 0; k + 1 < len; ++k) {
+                if (S > 0) point_slot(k);
+                StepParams Pf = make_params(h, t0 + k + 1);
+                point_states(Pf, h, seg[k], seg[k + 1]);
+                if ((rc = step_with(h, Pf))) return rc;
+            }
         }
         for (long long t = t0 + len; t > t0; --t) {
             const long long j = t - 1 - t0;
