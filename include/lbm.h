@@ -203,11 +203,17 @@ typedef struct lbm_loss {
 int lbm_adjoint(lbm_ctx *h, int n, int K, const lbm_loss *loss, double *dL_dinflow, double *dL_dpos, double *L);
 
 /* Checkpoint: serialise the state (header + populations in canonical layout in the
- * storage type + outlet ghost plane + step counter) into buf.  With buf = NULL only
- * *bytes is set to the required size.  Host pointer. */
+ * storage type + outlet ghost plane + step counter) into buf.  The header records the dims,
+ * the storage type and a 64-bit hash of the configuration the state evolves under (nu, body
+ * force, face types, collision model and rates, rho0, inlet velocity, noise amplitude and
+ * seed, inflow coefficients).  With buf = NULL only *bytes is set to the required size.
+ * Host pointer. */
 int lbm_save(lbm_ctx *h, void *buf, size_t *bytes);
 
-/* Restore a checkpoint written by lbm_save for the same dims and storage. */
+/* Restore a checkpoint written by lbm_save into a context with the same dims, storage and
+ * configuration hash; anything else is LBM_EINVAL and leaves the context unchanged.  Only the
+ * populations, the outlet ghost plane and the step counter are restored: the solid, its
+ * motion and the tracers are the context's own and are not part of a checkpoint. */
 int lbm_load(lbm_ctx *h, const void *buf, size_t bytes);
 
 /* Per-kernel device timing (CUDA events on the context's stream around every launch).
@@ -315,6 +321,14 @@ int lbm_set_inflow(lbm_ctx *h, const double coef[16]);
 /* Number of band nodes (nodes within the 2x2x2 stencil of a sample) of the solid. */
 long long lbm_band_size(const lbm_ctx *h);
 
+/* Number of solid samples S of the last lbm_set_solids (0 without a solid; -1 for NULL h):
+ * the length of the per-sample outputs of lbm_ib_forces, lbm_solid_samples and the position
+ * gradient of lbm_adjoint (3 S values each). */
+long long lbm_solid_count(const lbm_ctx *h);
+
+/* Grid size of the context: dims = {nx, ny, nz}.  LBM_EINVAL for NULL arguments. */
+int lbm_dims(const lbm_ctx *h, int dims[3]);
+
 /* Allocation-free FP64 sum of per-sample forces: out[a] = sum_s g[3*s + a] (the paper has
  * no counterpart; this is a service for callers that cannot call cudaMalloc at the point
  * where they need the sum, e.g. code running while allocation is forbidden or a memory
@@ -322,10 +336,13 @@ long long lbm_band_size(const lbm_ctx *h);
  * out: device pointer to 3 doubles, written on cuda_stream (NULL = legacy stream).
  * No cudaMalloc, cudaFree or allocating library call is made: the partial sums live in a
  * fixed 48 KiB __device__ array that every GPU loading the library holds until exit.
- * The first call on a device looks up that array's address (cudaGetSymbolAddress); make
- * that first call before any stream capture.  All calls on a device share the array, so
+ * The first call on a device looks up that array's address (cudaGetSymbolAddress) and keeps
+ * it; make that first call before any stream capture, and do not reset the device
+ * (cudaDeviceReset) after it in the same process.  All calls on a device share the array, so
  * calls that overlap on the GPU race; serialise them.  count may be 0 (out = 0);
- * count > LBM_STATIC_MAX_SAMPLES, a NULL out, or a NULL g with count > 0 give LBM_EINVAL. */
+ * count > LBM_STATIC_MAX_SAMPLES, a NULL out, or a NULL g with count > 0 give LBM_EINVAL.
+ * A CUDA error already pending on the calling thread gives LBM_ECUDA without a launch and is
+ * left pending; LBM_ECUDA is otherwise a failure of this call's own launches. */
 #define LBM_STATIC_MAX_SAMPLES (2048LL * 256LL * 64LL)
 int lbm_sum_forces_static(const float *g, long long count, double *out, void *cuda_stream);
 

@@ -1,7 +1,9 @@
 """Build liblbm.so (the C-ABI CUDA library) in-tree for sm_103a with nvcc.
 
-The library is plain CUDA C++ (no PyTorch in its interface); the two translation units
-are compiled in parallel and linked with the static CUDA runtime.
+The library is plain CUDA C++ (no PyTorch in its interface); its translation units (SOURCES:
+the step kernels of each collision model with and without free-slip faces, the immersed
+boundary and diagnostics, the C ABI, the adjoint, tracers, moving solids, the radix sort and the
+allocation-free force sum) are compiled in parallel and linked with the static CUDA runtime.
 """
 from __future__ import annotations
 

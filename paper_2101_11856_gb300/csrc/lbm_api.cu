@@ -546,6 +546,16 @@ int lbm_set_inflow(lbm_ctx *h, const double coef[16]) {
     return LBM_OK;
 }
 
+long long lbm_solid_count(const lbm_ctx *h) { return h ? h->S : -1; }
+
+int lbm_dims(const lbm_ctx *h, int dims[3]) {
+    if (!h || !dims) return LBM_EINVAL;
+    dims[0] = h->nx;
+    dims[1] = h->ny;
+    dims[2] = h->nz;
+    return LBM_OK;
+}
+
 long long lbm_band_size(const lbm_ctx *h) {
     if (!h) return -1;
     if (!h->band_count_dev) return h->nband;
@@ -614,8 +624,36 @@ int lbm_synchronize(lbm_ctx *h, double timeout_s) {
     return LBM_OK;
 }
 
-// checkpoint layout: header (8 int64) | populations (27 planes of N elements) | outlet plane
-static const long long kMagic = 0x4c424d4741413031LL;   // "LBMGAA01"
+// checkpoint layout: header (8 int64) | populations (27 planes of N elements) | outlet plane;
+// header = magic, nx, ny, nz, storage, t, outlet bytes, configuration hash
+static const long long kMagic = 0x4c424d4741413032LL;   // "LBMGAA02"
+
+// FNV-1a (64 bit) over the configuration that a restored state is only valid under: nu, the
+// body force, the face types, the collision model and its rates, rho0 and the inlet
+// parameters (velocity, noise amplitude and seed, inflow coefficients)
+static long long config_hash(const lbm_ctx *h) {
+    unsigned long long x = 0xcbf29ce484222325ull;
+    auto mix = [&x](const void *p, size_t n) {
+        const unsigned char *b = static_cast<const unsigned char *>(p);
+        for (size_t i = 0; i < n; ++i) {
+            x ^= b[i];
+            x *= 0x100000001b3ull;
+        }
+    };
+    const lbm_config &c = h->cfg;
+    mix(&h->nu, sizeof(double));
+    mix(h->forcing, sizeof(h->forcing));
+    mix(c.face_type, sizeof(c.face_type));
+    mix(&c.collision, sizeof(int));
+    mix(&c.rho0, sizeof(double));
+    mix(&c.omega_bulk, sizeof(double));
+    mix(c.omega_hi, sizeof(c.omega_hi));
+    mix(&c.u_in, sizeof(double));
+    mix(&c.inlet_noise, sizeof(double));
+    mix(&c.seed, sizeof(c.seed));
+    mix(c.inflow_coef, sizeof(c.inflow_coef));
+    return (long long)x;
+}
 
 int lbm_save(lbm_ctx *h, void *buf, size_t *bytes) {
     int rc = require_state(h);
@@ -629,7 +667,7 @@ int lbm_save(lbm_ctx *h, void *buf, size_t *bytes) {
         return LBM_OK;
     }
     if (*bytes < need) return fail(h, LBM_EINVAL, "buffer too small");
-    long long hdr[8] = {kMagic, h->nx, h->ny, h->nz, h->storage, h->t, (long long)outl, 0};
+    long long hdr[8] = {kMagic, h->nx, h->ny, h->nz, h->storage, h->t, (long long)outl, config_hash(h)};
     char *p = static_cast<char *>(buf);
     std::memcpy(p, hdr, sizeof(hdr));
     p += sizeof(hdr);
@@ -652,6 +690,9 @@ int lbm_load(lbm_ctx *h, const void *buf, size_t bytes) {
     if (hdr[0] != kMagic || hdr[1] != h->nx || hdr[2] != h->ny || hdr[3] != h->nz || hdr[4] != h->storage ||
         hdr[6] != (long long)outl || bytes < sizeof(hdr) + pop + outl)
         return fail(h, LBM_EINVAL, "checkpoint does not match this context");
+    if (hdr[7] != config_hash(h))
+        return fail(h, LBM_EINVAL, "checkpoint was written under another configuration (nu, force, faces, collision, "
+                                   "rates, rho0 or inlet parameters)");
     const char *p = static_cast<const char *>(buf) + sizeof(hdr);
     for (int d = 0; d < 27; ++d)
         CK(cudaMemcpyAsync(static_cast<char *>(h->f) + (size_t)d * h->plane * h->esize, p + (size_t)d * h->N * h->esize,

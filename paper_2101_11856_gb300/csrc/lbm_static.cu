@@ -12,7 +12,9 @@
 // its 48 KiB until the process exits.  All calls on a device share it and it keeps the
 // last call's contents; every slot a call reads is written by that same call first, so
 // nothing has to start at zero.  Calls whose work overlaps on the GPU (different streams,
-// no ordering between them) race on the array and must be serialised by the caller.
+// no ordering between them) race on the array and must be serialised by the caller.  The
+// array's device address is looked up once per device and cached, so a cudaDeviceReset after
+// the first call in the same process is not supported (the cached address would be stale).
 #include <mutex>
 
 #include "lbm.h"
@@ -72,6 +74,9 @@ __global__ void __launch_bounds__(kStaticThreads) k_sum_forces_aos(long long S, 
 extern "C" int lbm_sum_forces_static(const float *g, long long count, double *out, void *cuda_stream) {
     if (count < 0 || count > LBM_STATIC_MAX_SAMPLES || !out || (count > 0 && !g)) return LBM_EINVAL;
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    // an error left pending by earlier work on this thread is not this call's: report it
+    // without launching and leave it pending, so the launch checks below see only this call
+    if (cudaPeekAtLastError() != cudaSuccess) return LBM_ECUDA;
     double *partial = nullptr;
     if (static_partial(&partial) != cudaSuccess) return LBM_ECUDA;
     long long blocks = (count + kStaticThreads - 1) / kStaticThreads;

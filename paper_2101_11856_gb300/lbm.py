@@ -72,6 +72,8 @@ _SIGS = {
     "lbm_profile": (C.c_int, [C.c_void_p, C.c_int]),
     "lbm_kernel_times": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
     "lbm_band_size": (C.c_longlong, [C.c_void_p]),
+    "lbm_solid_count": (C.c_longlong, [C.c_void_p]),
+    "lbm_dims": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
     "lbm_set_inflow": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     "lbm_set_motion": (C.c_int, [C.c_void_p, C.POINTER(lbm_motion)]),
     "lbm_solid_samples": (C.c_int, [C.c_void_p, C.c_void_p]),
@@ -122,6 +124,25 @@ def _ptr(a):
         return C.c_void_p(t.data_ptr()), t
     arr = np.ascontiguousarray(a, dtype=np.float32)
     return C.c_void_p(arr.ctypes.data), arr
+
+
+def _ptr_out(a, n, what):
+    """Pointer of an output buffer the library fills with n float32 values: a C-contiguous
+    float32 numpy array or torch tensor of at least n elements, passed as is.  Anything else
+    is refused: the library would fill a converted temporary and the caller's array would keep
+    stale data, or write past a short buffer."""
+    if hasattr(a, "data_ptr"):
+        import torch
+        if a.dtype != torch.float32 or not a.is_contiguous():
+            raise ValueError(f"{what}: the output must be a contiguous float32 tensor")
+        if a.numel() < n:
+            raise ValueError(f"{what}: the output holds {a.numel()} values, {n} are written")
+        return C.c_void_p(a.data_ptr())
+    if not isinstance(a, np.ndarray) or a.dtype != np.float32 or not a.flags["C_CONTIGUOUS"] or not a.flags["WRITEABLE"]:
+        raise ValueError(f"{what}: the output must be a writeable C-contiguous float32 numpy array")
+    if a.size < n:
+        raise ValueError(f"{what}: the output holds {a.size} values, {n} are written")
+    return C.c_void_p(a.ctypes.data)
 
 
 def _ptr_nocopy(a):
@@ -178,8 +199,10 @@ def lbm_step(h, n=1):
 
 
 def lbm_macroscopic(h, rho, u):
-    pr, kr = _ptr(rho) if rho is not None else (None, None)
-    pu, ku = _ptr(u) if u is not None else (None, None)
+    """Fill rho (N) and u (3 N) (either may be None) with the fields of the last collision."""
+    N = _cells(h)
+    pr = _ptr_out(rho, N, "lbm_macroscopic rho") if rho is not None else None
+    pu = _ptr_out(u, 3 * N, "lbm_macroscopic u") if u is not None else None
     _check(library().lbm_macroscopic(h, pr, pu), h)
 
 
@@ -202,13 +225,13 @@ def lbm_reductions(h):
 
 
 def lbm_ib_forces(h, out):
-    p, k = _ptr(out)
-    _check(library().lbm_ib_forces(h, p), h)
+    """Fill out (S, 3) with the penalty forces of the last step, S = lbm_solid_count(h)."""
+    _check(library().lbm_ib_forces(h, _ptr_out(out, 3 * lbm_solid_count(h), "lbm_ib_forces")), h)
 
 
 def lbm_populations(h, out):
-    p, k = _ptr(out)
-    _check(library().lbm_populations(h, p), h)
+    """Fill out (27, N) with the post-collision populations of the current time."""
+    _check(library().lbm_populations(h, _ptr_out(out, 27 * _cells(h), "lbm_populations")), h)
 
 
 def lbm_velocity(i):
@@ -256,6 +279,21 @@ def lbm_band_size(h):
     return library().lbm_band_size(h)
 
 
+def lbm_solid_count(h):
+    return library().lbm_solid_count(h)
+
+
+def lbm_dims(h):
+    d = (C.c_int * 3)()
+    _check(library().lbm_dims(h, d), h)
+    return tuple(d[:])
+
+
+def _cells(h):
+    nx, ny, nz = lbm_dims(h)
+    return nx * ny * nz
+
+
 def lbm_set_inflow(h, coef):
     c = (C.c_double * 16)(*[float(v) for v in np.asarray(coef, dtype=np.float64).ravel()])
     _check(library().lbm_set_inflow(h, c), h)
@@ -271,8 +309,7 @@ def lbm_set_motion(h, motion=None):
 
 
 def lbm_solid_samples(h, out):
-    p, k = _ptr(out)
-    _check(library().lbm_solid_samples(h, p), h)
+    _check(library().lbm_solid_samples(h, _ptr_out(out, 3 * lbm_solid_count(h), "lbm_solid_samples")), h)
 
 
 def lbm_solid_torque(h, center=None):
@@ -298,8 +335,7 @@ def lbm_tracer_count(h):
 
 
 def lbm_tracers(h, out):
-    p, k = _ptr(out)
-    _check(library().lbm_tracers(h, p), h)
+    _check(library().lbm_tracers(h, _ptr_out(out, 3 * lbm_tracer_count(h), "lbm_tracers")), h)
 
 
 def lbm_tracer_dims(h, s):
@@ -309,30 +345,50 @@ def lbm_tracer_dims(h, s):
 
 
 def lbm_tracer_density(h, s, out):
-    p, k = _ptr(out)
-    _check(library().lbm_tracer_density(h, int(s), p), h)
+    gx, gy, gz = lbm_tracer_dims(h, s)
+    _check(library().lbm_tracer_density(h, int(s), _ptr_out(out, gx * gy * gz, "lbm_tracer_density")), h)
 
 
-def lbm_adjoint(h, n, K, w_drag=1.0, w_ke=0.0, ke_x0=0, ke_x1=0, count=0):
-    """Run n steps with the adjoint; returns (L, dL/d inflow coefficients (16,), dL/dX (count, 3))."""
+def lbm_adjoint(h, n, K, w_drag=1.0, w_ke=0.0, ke_x0=0, ke_x1=0, count=None):
+    """Run n steps with the adjoint; returns (L, dL/d inflow coefficients (16,), dL/dX (S, 3)),
+    S = lbm_solid_count(h).  ``count``, when given, must equal S (a check of the caller's
+    sample count; the library writes 3 S position gradients)."""
+    S = lbm_solid_count(h)
+    if count is not None and int(count) != S:
+        raise ValueError(f"lbm_adjoint: count {count} differs from the context's {S} samples")
     loss = lbm_loss(w_drag, w_ke, ke_x0, ke_x1)
     dinf = (C.c_double * 16)()
-    dpos = (C.c_double * max(3 * count, 1))()
+    dpos = (C.c_double * (3 * S))() if S > 0 else None
     L = C.c_double()
     _check(library().lbm_adjoint(h, int(n), int(K), C.byref(loss), dinf, dpos, C.byref(L)), h)
-    return L.value, np.array(dinf[:]), np.array(dpos[: 3 * count]).reshape(count, 3)
+    grad_X = np.array(dpos[:]).reshape(S, 3) if S > 0 else np.zeros((0, 3))
+    return L.value, np.array(dinf[:]), grad_X
 
 
 def lbm_sum_forces_static(g, out, stream=None):
-    """Allocation-free FP64 sum of per-sample forces: g (S, 3) float32 CUDA tensor, out (3,)
-    float64 CUDA tensor; launched on ``stream`` (default: torch's current stream)."""
+    """Allocation-free FP64 sum of per-sample forces: g (S, 3) contiguous float32 CUDA tensor,
+    out contiguous float64 CUDA tensor of at least 3 values, both on the current device;
+    launched on ``stream`` (default: torch's current stream)."""
     import torch
+    if not (isinstance(g, torch.Tensor) and isinstance(out, torch.Tensor)):
+        raise ValueError("lbm_sum_forces_static: g and out must be torch tensors")
+    if g.dtype != torch.float32 or not g.is_contiguous() or g.dim() != 2 or g.shape[1] != 3:
+        raise ValueError(f"lbm_sum_forces_static: g must be a contiguous float32 (S, 3) tensor, got "
+                         f"{tuple(g.shape)} {g.dtype}")
+    if out.dtype != torch.float64 or not out.is_contiguous() or out.numel() < 3:
+        raise ValueError("lbm_sum_forces_static: out must be a contiguous float64 tensor of at least 3 values")
+    if not (g.is_cuda and out.is_cuda):
+        raise ValueError("lbm_sum_forces_static: g and out must be CUDA tensors")
+    dev = torch.cuda.current_device()
+    if g.device.index != dev or out.device.index != dev:
+        raise ValueError("lbm_sum_forces_static: g and out must be on the current CUDA device")
     if stream is None:
         stream = torch.cuda.current_stream().cuda_stream
-    count = g.numel() // 3
+    count = g.shape[0]
     rc = library().lbm_sum_forces_static(C.c_void_p(g.data_ptr()) if count else None, count,
                                          C.c_void_p(out.data_ptr()), C.c_void_p(stream))
-    _check(rc)
+    if rc != LBM_OK:
+        raise LBMError(rc, f"lbm_sum_forces_static failed for {count} samples")
 
 
 # ---- convenience wrapper -----------------------------------------------------------
@@ -411,9 +467,12 @@ class Solver:
     def set_motion(self, motion=None):
         lbm_set_motion(self.h, motion)
 
-    def solid_samples(self, count):
-        """Current sample positions (count, 3), in the order given to set_solids."""
-        out = np.empty((count, 3), np.float32)
+    def solid_samples(self, count=None):
+        """Current sample positions (S, 3), in the order given to set_solids."""
+        S = lbm_solid_count(self.h)
+        if count is not None and int(count) != S:
+            raise ValueError(f"solid_samples: count {count} differs from the context's {S} samples")
+        out = np.empty((S, 3), np.float32)
         lbm_solid_samples(self.h, out)
         return out
 
@@ -437,8 +496,12 @@ class Solver:
         lbm_tracer_density(self.h, s, out)
         return out
 
-    def ib_forces(self, count):
-        g = np.empty((count, 3), np.float32)
+    def ib_forces(self, count=None):
+        """Penalty forces (S, 3) of the last step, in the order given to set_solids."""
+        S = lbm_solid_count(self.h)
+        if count is not None and int(count) != S:
+            raise ValueError(f"ib_forces: count {count} differs from the context's {S} samples")
+        g = np.empty((S, 3), np.float32)
         lbm_ib_forces(self.h, g)
         return g
 
@@ -447,7 +510,7 @@ class Solver:
         lbm_populations(self.h, f)
         return f
 
-    def adjoint(self, n, K=20, w_drag=1.0, w_ke=0.0, ke_x0=0, ke_x1=0, count=0):
+    def adjoint(self, n, K=20, w_drag=1.0, w_ke=0.0, ke_x0=0, ke_x1=0, count=None):
         return lbm_adjoint(self.h, n, K, w_drag, w_ke, ke_x0, ke_x1, count)
 
     def set_inflow(self, coef):

@@ -96,3 +96,38 @@ def test_async_binding_refuses_converted_temporaries():
                 torch.zeros(4, 6)[:, ::2], [1.0, 2.0]):
         with pytest.raises(ValueError):
             _ptr_nocopy(bad)
+
+
+def test_output_binding_refuses_temporaries_and_short_buffers():
+    """Outputs are filled in place: a buffer that would need a converted temporary (the caller's
+    array would keep stale data) or that is shorter than what the library writes is refused."""
+    import numpy as np
+    import torch
+    from paper_2101_11856_gb300.lbm import _ptr_out
+    a = np.zeros((3, 4), np.float32)
+    assert _ptr_out(a, 12, "x").value == a.ctypes.data
+    t = torch.zeros(5)
+    assert _ptr_out(t, 5, "x").value == t.data_ptr()
+    for bad in (np.zeros(12), np.zeros((3, 8), np.float32)[:, ::2], torch.zeros(12, dtype=torch.float64),
+                torch.zeros(3, 8)[:, ::2], [0.0] * 12, np.zeros(11, np.float32), torch.zeros(11)):
+        with pytest.raises(ValueError):
+            _ptr_out(bad, 12, "x")
+    ro = np.zeros(12, np.float32)
+    ro.flags.writeable = False
+    with pytest.raises(ValueError):
+        _ptr_out(ro, 12, "x")
+
+
+def test_static_force_sum_binding_validates_before_the_call():
+    """The allocation-free force sum's binding checks types, shapes and devices itself (the C
+    function takes bare pointers and cannot)."""
+    import torch
+    from paper_2101_11856_gb300.lbm import lbm_sum_forces_static
+    g, out = torch.zeros(10, 3), torch.zeros(3, dtype=torch.float64)
+    for args in ((torch.zeros(10, 3, dtype=torch.float64), out), (torch.zeros(30), out), (torch.zeros(10, 4), out),
+                 (g, torch.zeros(3)), (g, torch.zeros(2, dtype=torch.float64)), (g.numpy(), out),
+                 (torch.zeros(3, 10).t(), out)):
+        with pytest.raises(ValueError):
+            lbm_sum_forces_static(*args)
+    with pytest.raises(ValueError):                 # host tensors of the right shapes
+        lbm_sum_forces_static(g, out)

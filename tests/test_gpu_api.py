@@ -65,7 +65,7 @@ def test_zero_steps_and_time_counter():
 
 @pytest.mark.parametrize("storage", ["f32", "f16"])
 def test_checkpoint_roundtrip_is_bit_exact(storage):
-    from paper_2101_11856_gb300 import lbm
+    from paper_2101_11856_gb300 import LBMError, Solver, lbm
     kw = dict(faces=("inlet", "outlet", "noslip", "noslip", "periodic", "periodic"), u_in=0.03, noise=0.01,
               storage=storage)
     s = make(12, **kw)
@@ -85,6 +85,44 @@ def test_checkpoint_roundtrip_is_bit_exact(storage):
     other = make(10)
     with pytest.raises(Exception):
         lbm.lbm_load(other.h, blob)
+    # same dims and storage under another configuration: refused, the state is kept
+    for change in (dict(nu=0.06), dict(u_in=0.04), dict(noise=0.02), dict(omega_hi=(1.0, 1.2, 1.0, 1.0))):
+        kw2 = dict(kw, **{k: v for k, v in change.items() if k != "nu"})
+        o2 = Solver(12, 12, 12, change.get("nu", 0.05), **kw2)
+        o2.set_state(rho, u)
+        o2.step(1)
+        with pytest.raises(LBMError) as e:
+            lbm.lbm_load(o2.h, blob)
+        assert e.value.code == lbm.LBM_EINVAL and o2.time == 1, change
+        o2.close()
+
+
+def test_per_sample_outputs_take_their_length_from_the_context():
+    """adjoint() and ib_forces() with default arguments return one row per installed sample;
+    a count that differs from the context's is refused before the library writes anything."""
+    from paper_2101_11856_gb300 import lbm
+    n = 12
+    s = make(n, faces=("inlet", "outlet", "periodic", "periodic", "periodic", "periodic"), u_in=0.03)
+    s.set_state(*scenes.uniform_flow(n, n, n, (0.03, 0, 0)))
+    X, A = scenes.fibonacci_sphere((5.5, 6.0, 6.0), 2.5, 80)
+    s.set_solids(X, A)
+    assert lbm.lbm_solid_count(s.h) == 80 and lbm.lbm_dims(s.h) == (n, n, n)
+    L, dc, dx = s.adjoint(3, 2)
+    assert dx.shape == (80, 3) and np.all(np.isfinite(dx)) and np.isfinite(L)
+    assert s.ib_forces().shape == (80, 3)
+    for bad in (0, 79, 81):
+        with pytest.raises(ValueError):
+            s.adjoint(2, 1, count=bad)
+        with pytest.raises(ValueError):
+            s.ib_forces(bad)
+    with pytest.raises(ValueError):
+        lbm.lbm_ib_forces(s.h, np.empty((79, 3), np.float32))
+    with pytest.raises(ValueError):
+        lbm.lbm_macroscopic(s.h, np.empty(n ** 3, np.float64), None)
+    s.set_solids(None)
+    L, dc, dx = s.adjoint(2, 1)
+    assert dx.shape == (0, 3)
+    s.close()
 
 
 def test_device_and_host_pointers_agree():
