@@ -2,10 +2,13 @@
 
 Workload: the single-GPU large scene, 1200 x 250 x 840 cells (252M) with ~3.8M procedural
 "building" samples at 0.5-cell spacing, inlet u = 0.08 with 1 % seeded noise, outlet,
-no-slip ground and top, periodic z (stand-in for the paper's Fig. 1 / Table 3 scene).
+no-slip ground, free-slip top, periodic z (stand-in for the paper's Fig. 1 / Table 3 scene).
 One timed step = one time step of the whole hot path (band moments, interpolation +
 penalty, spreading, fused stream + collide over all cells).  The state (27 GB FP32)
-is far larger than L2, so no flush is needed between steps.
+is far larger than L2, so no flush is needed between steps.  The K timed steps run in five
+timed regions without per-kernel events (value = K steps over their summed time; runs,
+median and spread per region); the per-kernel times come from a second, profiled region of
+K steps.
 
 Prints ONE JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle instead
 (the baseline of this method; there is no other reference implementation).
@@ -309,6 +312,148 @@ def main_cells(nx, ny, nz, faces):
     return (nx - 2 * xedge) * rows
 
 
+def region_steps(solver, steps, torch, regions=5):
+    """Time exactly ``steps`` steps without per-kernel profiling, split into ``regions`` timed
+    regions of (nearly) equal step counts, each between CUDA events on the solver's stream (torch's
+    current stream) with a synchronize on both sides.  Returns (total ms, [(steps, ms) per region])."""
+    regions = max(1, min(regions, steps))
+    counts = [steps // regions + (1 if r < steps % regions else 0) for r in range(regions)]
+    out = []
+    for n in counts:
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        s0.record()
+        solver.step(n)
+        s1.record()
+        torch.cuda.synchronize()
+        out.append((n, s0.elapsed_time(s1)))
+    return sum(ms for _, ms in out), out
+
+
+def run_stats(N, regions, world):
+    """MLUPS of every timed region, their median and relative spread (max - min) / median."""
+    vals = [world * N * n / (ms * 1e-3) / 1e6 for n, ms in regions]
+    med = float(np.median(vals))
+    return {"runs": [round(v, 1) for v in vals], "median": med,
+            "spread": float((max(vals) - min(vals)) / med) if med > 0 else None}
+
+
+GOLDEN_C2 = os.path.join(ROOT, "tests", "golden", "sphere_channel_256x128x128_100steps.npz")
+
+
+def precision_vs_oracle(torch, lbm, Solver):
+    """Per-field error of each storage against the FP64 oracle on the sphere channel 256 x 128 x 128
+    after 100 steps (the oracle's density and velocity at about 110,000 cells, stored by
+    tests/golden/make_sphere_channel_golden.py): relative L2 of rho - 1, u_x, u_y, u_z."""
+    if not os.path.exists(GOLDEN_C2):
+        return None
+    z = np.load(GOLDEN_C2)
+    idx, rho_o, u_o, meta = z["idx"].astype(np.int64), z["rho"], z["u"], json.loads(str(z["meta"]))
+    sc = scenes.scene_sphere_channel(256, 128, 128, radius=meta["radius"], count=meta["count"], u_in=meta["u_in"],
+                                     nu=meta["nu"], noise=meta["noise"])
+    N = sc["nx"] * sc["ny"] * sc["nz"]
+    ti = torch.from_numpy(idx).cuda()
+    out = {"workload": sc["name"], "steps": meta["steps"], "cells_compared": int(idx.size),
+           "what": "relative L2 over the stored cells against the FP64 oracle"}
+    for st in ("f32", "f16", "bf16"):
+        g = Solver(sc["nx"], sc["ny"], sc["nz"], sc["nu"], storage=st, faces=sc["faces"], u_in=sc["u_in"],
+                   noise=sc["noise"], seed=meta["seed"])
+        g.set_state(sc["rho"], sc["u"])
+        g.set_solids(sc["samples"].astype(np.float32), sc["area"].astype(np.float32))
+        g.step(meta["steps"])
+        rho = torch.empty(N, device="cuda")
+        u = torch.empty(3, N, device="cuda")
+        lbm.lbm_macroscopic(g.h, rho, u)
+        g.close()
+        rg = rho[ti].double().cpu().numpy()
+        ug = u[:, ti].double().cpu().numpy()
+        rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
+        out[st] = {"rho-1": rel(rg - 1.0, rho_o - 1.0), "u_x": rel(ug[0], u_o[0]), "u_y": rel(ug[1], u_o[1]),
+                   "u_z": rel(ug[2], u_o[2]), "rho": rel(rg, rho_o), "u": rel(ug, u_o)}
+        del rho, u
+    torch.cuda.empty_cache()
+    return out
+
+
+def cpu_model():
+    """Host CPU model (lscpu, else /proc/cpuinfo, else platform)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu model")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def oracle_config_sample(name, steps, dims=None):
+    """The FP64 oracle on one configuration, or on a block of it: (MLUPS, seconds, description).
+    tgv32: 32^3 periodic Taylor-Green vortex; sphere: the 256 x 128 x 128 sphere channel (a slab
+    of it keeps the samples inside); adjoint: the 128^3 channel with its sphere (forward steps)."""
+    from oracle.solver import OracleSolver, Problem
+    if name == "tgv32":
+        sc = scenes.scene_tgv32()
+        nx, ny, nz = dims or (32, 32, 32)
+        p = Problem(nx, ny, nz, nu=sc["nu"])
+        o = OracleSolver(p)
+        o.set_state(sc["rho"][:nz, :ny, :nx], sc["u"][:, :nz, :ny, :nx])
+    else:
+        if name == "sphere":
+            sc = scenes.scene_sphere_channel(256, 128, 128, radius=16.0, count=3200, u_in=0.05, nu=0.008)
+        else:
+            sc = scenes.scene_sphere_channel(128, 128, 128, radius=12.6, count=2000, u_in=0.05, nu=0.01,
+                                             center=(40.0, 64.0, 64.0))
+        nx, ny, nz = dims or (sc["nx"], sc["ny"], sc["nz"])
+        z0 = (sc["nz"] - nz) // 2
+        p = Problem(nx, ny, nz, nu=sc["nu"], faces=sc["faces"], u_in=sc["u_in"], noise=sc["noise"], seed=2101)
+        o = OracleSolver(p)
+        o.set_state(sc["rho"][:nz, :ny, :nx], sc["u"][:, :nz, :ny, :nx])
+        X = sc["samples"] - np.array([0.0, 0.0, z0])
+        keep = np.all((X >= 0) & (X < np.array([nx - 1, ny - 1, nz - 1])), axis=1)
+        if keep.any():
+            o.set_solids(X[keep], sc["area"][keep])
+    t0 = time.perf_counter()
+    o.step(steps)
+    dt = time.perf_counter() - t0
+    return nx * ny * nz * steps / dt / 1e6, dt, f"{nx}x{ny}x{nz}, {steps} steps"
+
+
+def cpu_baselines(d, args):
+    """The oracle as it stands (FP64, PyTorch CPU) on the host: the benchmark workload's slab with
+    all host threads and with one, and bounded samples of the other configurations."""
+    import torch
+    all_threads = torch.get_num_threads()
+    out = {}
+    head, _ = oracle_sample(d, 1, (0, d["nx"] // 2, 0, d["ny"], 4))
+    torch.set_num_threads(1)
+    try:
+        one, _ = oracle_sample(d, 1, (0, d["nx"] // 8, 0, d["ny"], 4))
+        plan = (("tgv32_100_steps", "tgv32", 100, None, 10, None),
+                ("sphere_channel_256x128x128", "sphere", 1, (256, 128, 16), 1, (256, 128, 4)),
+                ("adjoint_channel_128^3_forward", "adjoint", 1, (128, 128, 32), 1, (128, 128, 4)))
+        for key, name, st_all, dims_all, st_one, dims_one in plan:
+            v1, _, s1 = oracle_config_sample(name, st_one, dims_one)
+            torch.set_num_threads(all_threads)
+            va, _, sa = oracle_config_sample(name, st_all, dims_all)
+            torch.set_num_threads(1)
+            out[key] = {"cores_all": {"value": va, "sample": sa}, "cores_1": {"value": v1, "sample": s1}}
+    finally:
+        torch.set_num_threads(all_threads)
+    head.update({"cores_all": all_threads, "cpu_model": cpu_model(),
+                 "cores_1": {"value": one["value"], "sample": one["sample"]},
+                 "configs": out, "unit_note": "MLUPS of the FP64 oracle (cells x steps / s)"})
+    return head
+
+
 def timed_steps(solver, steps, torch):
     from paper_2101_11856_gb300 import lbm
     s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -386,11 +531,14 @@ def main():
     torch.cuda.synchronize()
     barrier()
     with Clocks(local) as clk:
-        ms, kt = timed_steps(s, args.steps, torch)
+        ms, regions = region_steps(s, args.steps, torch)
     barrier()
     ms_max = max_over_ranks(ms, dist, "cuda" if torch.cuda.is_available() else "cpu")
     ms_step = ms_max / args.steps
     mlups = world * N / (ms_step * 1e-3) / 1e6
+    stats = run_stats(N, regions, world)
+    # per-kernel times (CUDA events around every launch) from a second region of the same length
+    ms_prof, kt = timed_steps(s, args.steps, torch)
     n_int = main_cells(nx, ny, nz, d["faces"])   # cells of one k_step_main launch
     step_ms, step_n = kt["step"]
     k_ms = step_ms / max(step_n, 1)
@@ -455,6 +603,9 @@ def main():
     # ---- FP16-stored deviations (same workload) ---------------------------------------
     n_side = max(10, args.steps // 2)
     fp16 = None if args.no_fp16 else side_run("f16", "acm", n_side)
+    if fp16 is not None:
+        fp16["bf16"] = side_run("bf16", "acm", n_side)
+        fp16["per_field_error"] = precision_vs_oracle(torch, lbm, Solver) if args.scale == 1.0 else None
 
     # ---- comparison collisions of Sec. 6.1 (same workload, same step structure) -------------
     models = None
@@ -481,7 +632,7 @@ def main():
 
     cpu = None
     if not args.no_cpu and rank == 0 and world == 1:
-        cpu, _ = oracle_sample(d, 2)
+        cpu = cpu_baselines(d, args)
 
     if rank == 0:
         line = {
@@ -499,6 +650,11 @@ def main():
                          "kernel": "k_step_main (fused stream+collide, 32 <= x < nx-32 of the rows off the y/z faces)",
                          "cells_per_launch": n_int, "bytes_per_cell": 216,
                          "peak_kind": peak_kind},
+            "runs": stats["runs"], "median": stats["median"], "spread": stats["spread"],
+            "timing": {"regions": len(regions), "steps_per_region": [n for n, _ in regions],
+                       "what": "value = K steps / their summed time over the regions (no per-kernel events); "
+                               "runs = MLUPS of each region; kernel times from a separate profiled region of K "
+                               f"steps ({ms_prof / args.steps:.3f} ms/step with the events)"},
             "kernel_ms": breakdown,
             "kernel_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in kt.items() if v[1]},
             "gpu_launches": launches,

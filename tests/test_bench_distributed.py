@@ -67,3 +67,17 @@ def test_main_kernel_cells():
     assert bench.main_cells(1200, 250, 840, closed) == 1136 * 250 * 840
     assert bench.main_cells(65, 2, 7, city) == 0            # every row on a face
     assert bench.main_cells(64, 9, 9, closed) == 0          # no main range
+
+
+def test_run_statistics_and_cpu_samples():
+    """The per-region statistics of the headline (MLUPS per region, median, relative spread) and
+    one bounded oracle sample of another configuration, on the host."""
+    sys.path.insert(0, ROOT)
+    import bench
+    st = bench.run_stats(1_000_000, [(4, 2.0), (4, 4.0), (4, 2.0)], 1)
+    assert st["runs"] == [2000.0, 1000.0, 2000.0] and st["median"] == 2000.0 and abs(st["spread"] - 0.5) < 1e-12
+    v, dt, desc = bench.oracle_config_sample("tgv32", 1, (8, 8, 8))
+    assert v > 0 and dt > 0 and desc == "8x8x8, 1 steps"
+    v, dt, desc = bench.oracle_config_sample("sphere", 1, (24, 12, 6))
+    assert v > 0 and desc.startswith("24x12x6")
+    assert isinstance(bench.cpu_model(), str) and bench.cpu_model()
