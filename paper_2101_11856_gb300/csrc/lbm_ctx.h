@@ -38,6 +38,7 @@ struct lbm_ctx {
     float *X = nullptr, *area = nullptr, *ub = nullptr, *g = nullptr;
     int *corner_band = nullptr, *band_cell = nullptr, *base_nbr = nullptr, *cstart = nullptr, *ccount = nullptr;
     float *band_rho = nullptr, *band_u = nullptr, *bandF = nullptr;
+    bool ub_zero = false;           // every boundary velocity is 0 (the interpolation skips ub)
     uint32_t *tile_mask = nullptr;
     int *tile_off = nullptr;
     std::vector<long long> order;   // sorted position -> caller's sample index
@@ -202,14 +203,25 @@ inline lbm::StepParams make_params(const lbm_ctx *h, long long t) {
         const double r3 = 1.0 - h->cfg.omega_hi[0], r4 = 1.0 - h->cfg.omega_hi[1];
         const double r5 = 1.0 - h->cfg.omega_hi[2], r6 = 1.0 - h->cfg.omega_hi[3];
         const double q3 = 1.0 - 0.5 * h->cfg.omega_hi[0], q5 = 1.0 - 0.5 * h->cfg.omega_hi[2];
-        P.a2 = (float)(rs / 4); P.b2 = (float)(-(1 - rs) / 4 * r0);
-        P.tb6 = (float)(rb / 6); P.ts6 = (float)(rs / 6); P.r0h = (float)(r0 / 2);
-        P.a3 = (float)(r3 / 4); P.b3 = (float)((1 - r3) / 4 * r0); P.f3 = (float)(q3 / 3 / 4);
-        P.a3e = (float)(r3 / 8); P.b3e = (float)((1 - r3) / 8 * r0);
-        P.a4 = (float)(r4 / 4); P.b4r = (float)((1 - r4) / 4 / 9); P.b4u = (float)(-(1 - r4) / 4 * r0 / 3);
-        P.a4m = (float)(r4 / 8); P.b4m = (float)(-(1 - r4) / 8 * r0);
-        P.a5 = (float)(r5 / 8); P.b5 = (float)((1 - r5) / 8 * r0); P.f5 = (float)(q5 / 9 / 8);
-        P.a6 = (float)(r6 / 8); P.b6r = (float)((1 - r6) / 8 / 27); P.b6u = (float)(-(1 - r6) / 8 * r0);
+        lbm::CollCoef<float> &k = P.cc;
+        k.rho0 = (float)r0; k.r0h = (float)(r0 / 2); k.mr0h = -k.r0h;
+        k.a2 = (float)(rs / 4); k.b2 = (float)(-(1 - rs) / 4 * r0);
+        k.tb6 = (float)(rb / 6); k.ts6 = (float)(rs / 6);
+        k.a3 = (float)(r3 / 4); k.b3 = (float)((1 - r3) / 4 * r0); k.f3 = (float)(q3 / 3 / 4);
+        k.a3e = (float)(r3 / 8); k.b3e = (float)((1 - r3) / 8 * r0);
+        k.a4 = (float)(r4 / 4); k.b4r = (float)((1 - r4) / 4 / 9); k.b4u = (float)(-(1 - r4) / 4 * r0 / 3);
+        k.a4m = (float)(r4 / 8); k.b4m = (float)(-(1 - r4) / 8 * r0);
+        k.a5 = (float)(r5 / 8); k.b5 = (float)((1 - r5) / 8 * r0); k.f5 = (float)(q5 / 9 / 8);
+        k.a6 = (float)(r6 / 8); k.b6r = (float)((1 - r6) / 8 / 27); k.b6u = (float)(-(1 - r6) / 8 * r0);
+        // the transform's fixed constants: FP32 values (third and ninth rounded once from 1/3
+        // and 1/9, sixth = third / 2 exactly)
+        k.half = 0.5f; k.quarter = 0.25f; k.third = 1.0f / 3.0f; k.mthird = -k.third; k.sixth = 0.5f * k.third;
+        k.ninth = 1.0f / 9.0f; k.three = 3.0f; k.mtwo = -2.0f; k.mone = -1.0f;
+        // node pairs: every coefficient twice
+        const float *src = reinterpret_cast<const float *>(&k);
+        float2 *dst = reinterpret_cast<float2 *>(&P.cc2);
+        static_assert(sizeof(lbm::CollCoef<float2>) == 2 * sizeof(lbm::CollCoef<float>), "coefficient layout");
+        for (size_t i = 0; i < sizeof(lbm::CollCoef<float>) / sizeof(float); ++i) dst[i] = make_float2(src[i], src[i]);
     }
     P.u_in = (float)h->cfg.u_in;
     P.noise = (float)h->cfg.inlet_noise;
@@ -337,6 +349,7 @@ inline void free_solid(lbm_ctx *h) {
     h->motion_ws = nullptr;
     h->motion_ws_bytes = 0;
     h->moving = false;
+    h->ub_zero = false;
     h->posed_tau = -1;
     h->S = h->nband = h->ntiles = 0;
     h->order.clear();

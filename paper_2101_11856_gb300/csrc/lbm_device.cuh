@@ -67,6 +67,24 @@ struct Geometry {
     int face[6];         // FaceType of -x, +x, -y, +y, -z, +z
 };
 
+// Coefficients of the central-moment collision (collide_v), for one node (S = float) or for a
+// node pair in the packed FP32 instructions (S = float2, the same value in both halves).  The
+// relaxation products sigma rr and sigma (1 - rr) e of every moment group are precomputed on the
+// host (make_params) with sigma = 2^-(number of nonzero indices); the remaining members are the
+// fixed constants of the transform, held here so that a node pair reads them as operand pairs.
+template <typename S> struct CollCoef {
+    S rho0, r0h, mr0h;           // rho0, rho0 / 2, -rho0 / 2
+    S a2, b2;                    // shear off-diagonal: sigma 1/4, e = -rho0 u_a u_b
+    S tb6, ts6;                  // trace / deviators: rb / 6, rs / 6
+    S a3, b3, f3;                // order 3 with force: sigma 1/4, e = rho0 u t; force q3 / 3
+    S a3e, b3e;                  // kappa_111: sigma 1/8
+    S a4, b4r, b4u;              // kappa_220-type: sigma 1/4, e = rhop / 9 - rho0 / 3 (3 u2 v2 + u2 + v2)
+    S a4m, b4m;                  // kappa_211-type: sigma 1/8, e = -rho0 t_a u_b u_c
+    S a5, b5, f5;                // order 5: sigma 1/8, e = rho0 u_c t_a t_b; force q5 / 9
+    S a6, b6r, b6u;              // kappa_222: sigma 1/8, e = rhop / 27 - rho0 (s1 / 9 + s2 / 3 + s3)
+    S half, quarter, third, mthird, sixth, ninth, three, mtwo, mone;
+};
+
 struct StepParams {
     void *f;                     // populations, 27 planes (AA in place)
     void *fp[27];                // start of the plane of each direction (read)
@@ -79,16 +97,8 @@ struct StepParams {
     float rs, rb, r3, r4, r5, r6;   // 1 - omega of shear, bulk, orders 3..6
     float q3, q5;                // 1 - omega/2 of orders 3 and 5 (their force moments)
     float u_in, noise;           // inlet velocity and relative noise amplitude
-    // relaxation coefficients of the central-moment collision in the form
-    // sigma (rr h + (1 - rr) e + force), sigma = 2^-(number of nonzero indices): see collide_v
-    float a2, b2;                // shear off-diagonal: sigma 1/4, e = -rho0 u_a u_b
-    float tb6, ts6, r0h;         // trace / deviators: rb / 6, rs / 6; rho0 / 2
-    float a3, b3, f3;            // order 3 with force: sigma 1/4, e = rho0 u t; force q3 / 3
-    float a3e, b3e;              // kappa_111: sigma 1/8
-    float a4, b4r, b4u;          // kappa_220-type: sigma 1/4, e = rhop / 9 - rho0 / 3 (3 u2 v2 + u2 + v2)
-    float a4m, b4m;              // kappa_211-type: sigma 1/8, e = -rho0 t_a u_b u_c
-    float a5, b5, f5;            // order 5: sigma 1/8, e = rho0 u_c t_a t_b; force q5 / 9
-    float a6, b6r, b6u;          // kappa_222: sigma 1/8, e = rhop / 27 - rho0 (s1 / 9 + s2 / 3 + s3)
+    CollCoef<float> cc;          // the collision's coefficients (one node)
+    CollCoef<float2> cc2;        // the same, for node pairs (packed FP32)
     unsigned long long seed;
     long long t;                 // index of the step being computed (1-based)
     const float *inlet_profile;  // [nyz] Fourier part of the inflow, or nullptr
@@ -167,10 +177,35 @@ __device__ __forceinline__ Nbr neighbour(const Geometry &g, int D, int x, int y,
     return n;
 }
 
-// ---- scalar helpers of the templated arithmetic ---------------------------------------
+// ---- arithmetic of the templated collision: one node (float) or a node pair (F2) --------
+// F2 holds the values of two nodes and maps every operation to the packed FP32 instructions of
+// sm_100+ (one f32x2 add / multiply / fma for both nodes): each half is the IEEE FP32 result
+// with round-to-nearest, so a node pair computes bit for bit what two single nodes compute.
+struct F2 {
+    float2 v;
+};
+__device__ __forceinline__ float2 f2sub(float2 a, float2 b) {
+    unsigned long long ra = *reinterpret_cast<unsigned long long *>(&a);
+    unsigned long long rb = *reinterpret_cast<unsigned long long *>(&b), rd;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(rd) : "l"(ra), "l"(rb));
+    return *reinterpret_cast<float2 *>(&rd);
+}
+__device__ __forceinline__ F2 operator+(F2 a, F2 b) { return {__fadd2_rn(a.v, b.v)}; }
+__device__ __forceinline__ F2 operator-(F2 a, F2 b) { return {f2sub(a.v, b.v)}; }
+__device__ __forceinline__ F2 operator*(F2 a, F2 b) { return {__fmul2_rn(a.v, b.v)}; }
+__device__ __forceinline__ F2 operator+(float2 a, F2 b) { return {__fadd2_rn(a, b.v)}; }
+__device__ __forceinline__ F2 operator*(float2 a, F2 b) { return {__fmul2_rn(a, b.v)}; }
+__device__ __forceinline__ F2 vfma(F2 a, F2 b, F2 c) { return {__ffma2_rn(a.v, b.v, c.v)}; }
+__device__ __forceinline__ F2 vfma(float2 a, F2 b, F2 c) { return {__ffma2_rn(a, b.v, c.v)}; }
+__device__ __forceinline__ F2 vrcp(F2 a) { return {make_float2(__frcp_rn(a.v.x), __frcp_rn(a.v.y))}; }
 __device__ __forceinline__ float vfma(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ float vrcp(float a) { return __frcp_rn(a); }
-template <typename V> __device__ __forceinline__ V vconst(float s) { return V(s); }
+// a coefficient as an operand of V's arithmetic (float for one node, float2 for a pair)
+template <typename V> struct CoefOf { using T = float; };
+template <> struct CoefOf<F2> { using T = float2; };
+template <typename V> __device__ __forceinline__ const CollCoef<typename CoefOf<V>::T> &coefs(const StepParams &P);
+template <> __device__ __forceinline__ const CollCoef<float> &coefs<float>(const StepParams &P) { return P.cc; }
+template <> __device__ __forceinline__ const CollCoef<float2> &coefs<F2>(const StepParams &P) { return P.cc2; }
 
 // ---- the 3-point transforms of the factorised central-moment basis -------------------
 // A triplet holds (v(c=-1), v(c=0), v(c=+1)) of one axis; after a forward transform the
@@ -183,21 +218,26 @@ template <typename V> __device__ __forceinline__ void raw3(V &a, V &b, V &c) {
     b = d;
     c = s;
 }
-// raw -> central moments about u
-template <typename V> __device__ __forceinline__ void shift3(V &m0, V &m1, V &m2, V u) {
-    const V u2 = u * u, m2u = -2.0f * u;   // shared by the nine triplets of a sweep
+// raw -> central moments about u; u2 = u^2, m2u = -2 u, mu = -u (shared by the nine triplets
+// of a sweep)
+template <typename V> __device__ __forceinline__ void shift3(V &m0, V &m1, V &m2, V u2, V m2u, V mu) {
     m2 = vfma(u2, m0, vfma(m2u, m1, m2));
-    m1 = vfma(-u, m0, m1);
+    m1 = vfma(mu, m0, m1);
+}
+// the same for one triplet, forming u^2, -2 u and -u itself (the adjoint's recompute)
+__device__ __forceinline__ void shift3(float &m0, float &m1, float &m2, float u) {
+    shift3(m0, m1, m2, u * u, -2.0f * u, -u);
 }
 // central moments about u -> populations, with the order-1 and order-2 moments given halved
-// (k0, k1 / 2, k2 / 2); hu = u / 2, tu = 2 u, u2h = u^2 / 2
-__device__ __forceinline__ void inv3h(float &m0, float &m1, float &m2, float hu, float tu, float u2h) {
-    const float r1h = fmaf(hu, m0, m1);                 // (k1 + u k0) / 2
-    const float R2 = fmaf(u2h, m0, fmaf(tu, m1, m2));   // (k2 + 2 u k1 + u^2 k0) / 2
-    const float k0 = m0;
+// (k0, k1 / 2, k2 / 2); hu = u / 2, tu = 2 u, u2h = u^2 / 2, mtwo = -2
+template <typename V, typename C>
+__device__ __forceinline__ void inv3h(V &m0, V &m1, V &m2, V hu, V tu, V u2h, C mtwo) {
+    const V r1h = vfma(hu, m0, m1);                 // (k1 + u k0) / 2
+    const V R2 = vfma(u2h, m0, vfma(tu, m1, m2));   // (k2 + 2 u k1 + u^2 k0) / 2
+    const V k0 = m0;
     m0 = R2 - r1h;
     m2 = R2 + r1h;
-    m1 = fmaf(-2.0f, R2, k0);
+    m1 = vfma(mtwo, R2, k0);
 }
 
 // base index of the k-th triplet along the axis with stride S (1: x, 3: y, 9: z)
@@ -209,14 +249,17 @@ template <int S, typename V> __device__ __forceinline__ void sweep_raw(V (&h)[27
 #pragma unroll
     for (int k = 0; k < 9; ++k) raw3(h[tri_base<S>(k)], h[tri_base<S>(k) + S], h[tri_base<S>(k) + 2 * S]);
 }
-template <int S, typename V> __device__ __forceinline__ void sweep_shift(V (&h)[27], V u) {
+template <int S, typename V, typename C> __device__ __forceinline__ void sweep_shift(V (&h)[27], V u, const C &k) {
+    const V u2 = u * u, m2u = k.mtwo * u, mu = k.mone * u;
 #pragma unroll
-    for (int k = 0; k < 9; ++k) shift3(h[tri_base<S>(k)], h[tri_base<S>(k) + S], h[tri_base<S>(k) + 2 * S], u);
+    for (int j = 0; j < 9; ++j)
+        shift3(h[tri_base<S>(j)], h[tri_base<S>(j) + S], h[tri_base<S>(j) + 2 * S], u2, m2u, mu);
 }
-template <int S> __device__ __forceinline__ void sweep_invh(float (&h)[27], float u, float u2) {
-    const float hu = 0.5f * u, tu = u + u, u2h = 0.5f * u2;
+template <int S, typename V, typename C> __device__ __forceinline__ void sweep_invh(V (&h)[27], V u, V u2, const C &k) {
+    const V hu = k.half * u, tu = u + u, u2h = k.half * u2;
 #pragma unroll
-    for (int k = 0; k < 9; ++k) inv3h(h[tri_base<S>(k)], h[tri_base<S>(k) + S], h[tri_base<S>(k) + 2 * S], hu, tu, u2h);
+    for (int j = 0; j < 9; ++j)
+        inv3h(h[tri_base<S>(j)], h[tri_base<S>(j) + S], h[tri_base<S>(j) + 2 * S], hu, tu, u2h, k.mtwo);
 }
 
 // ---- collision (Eqs. 4-5) ---------------------------------------------------------------
@@ -237,84 +280,84 @@ template <int S> __device__ __forceinline__ void sweep_invh(float (&h)[27], floa
 template <typename V>
 __device__ __forceinline__ void collide_v(V (&h)[27], V Fx, V Fy, V Fz, const StepParams &P, V &rho, V &ux, V &uy,
                                           V &uz) {
+    const auto &k = coefs<V>(P);
     sweep_raw<1>(h);
     sweep_raw<3>(h);
     sweep_raw<9>(h);
     const V rhop = h[K(0, 0, 0)];            // rho - rho0
-    rho = P.rho0 + rhop;
+    rho = k.rho0 + rhop;
     const V inv = vrcp(rho);
-    ux = vfma(0.5f, Fx, h[K(1, 0, 0)]) * inv;
-    uy = vfma(0.5f, Fy, h[K(0, 1, 0)]) * inv;
-    uz = vfma(0.5f, Fz, h[K(0, 0, 1)]) * inv;
-    sweep_shift<1>(h, ux);
-    sweep_shift<3>(h, uy);
-    sweep_shift<9>(h, uz);
+    ux = vfma(k.half, Fx, h[K(1, 0, 0)]) * inv;
+    uy = vfma(k.half, Fy, h[K(0, 1, 0)]) * inv;
+    uz = vfma(k.half, Fz, h[K(0, 0, 1)]) * inv;
+    sweep_shift<1>(h, ux, k);
+    sweep_shift<3>(h, uy, k);
+    sweep_shift<9>(h, uz, k);
 
     const V ux2 = ux * ux, uy2 = uy * uy, uz2 = uz * uz;
-    const float third = 1.0f / 3.0f;
-    const V tx = third + ux2, ty = third + uy2, tz = third + uz2;
+    const V tx = k.third + ux2, ty = k.third + uy2, tz = k.third + uz2;
     const V uxy = ux * uy, uxz = ux * uz, uyz = uy * uz;
 
     // order 1: conserved, kappa'_100 = F_x / 2 (stored as deviation moment rho0 u_x + F_x/2), times 1/2
-    h[K(1, 0, 0)] = vfma(P.r0h, ux, 0.25f * Fx);
-    h[K(0, 1, 0)] = vfma(P.r0h, uy, 0.25f * Fy);
-    h[K(0, 0, 1)] = vfma(P.r0h, uz, 0.25f * Fz);
+    h[K(1, 0, 0)] = vfma(k.r0h, ux, k.quarter * Fx);
+    h[K(0, 1, 0)] = vfma(k.r0h, uy, k.quarter * Fy);
+    h[K(0, 0, 1)] = vfma(k.r0h, uz, k.quarter * Fz);
 
     // sigma (rr h + (1 - rr) e + f) with A = sigma rr and B e_term = sigma (1 - rr) e
-#define RELAX(idx, A, Be) h[idx] = vfma(vconst<V>(A), h[idx], (Be))
+#define RELAX(idx, A, Be) h[idx] = vfma((A), h[idx], (Be))
     // order 2, off-diagonal (shear)
-    RELAX(K(1, 1, 0), P.a2, P.b2 * uxy);
-    RELAX(K(1, 0, 1), P.a2, P.b2 * uxz);
-    RELAX(K(0, 1, 1), P.a2, P.b2 * uyz);
+    RELAX(K(1, 1, 0), k.a2, k.b2 * uxy);
+    RELAX(K(1, 0, 1), k.a2, k.b2 * uxz);
+    RELAX(K(0, 1, 1), k.a2, k.b2 * uyz);
     // order 2, diagonal: trace (bulk) and two deviators (shear), times 1/2
     {
-        const V a = vfma(P.rho0, ux2, vfma(-third, rhop, h[K(2, 0, 0)]));   // kappa - e, e = rhop/3 - rho0 u^2
-        const V b = vfma(P.rho0, uy2, vfma(-third, rhop, h[K(0, 2, 0)]));
-        const V c = vfma(P.rho0, uz2, vfma(-third, rhop, h[K(0, 0, 2)]));
-        const V sixth_rhop = (0.5f * third) * rhop;
-        const V T = P.tb6 * (a + b + c);
-        const V D1 = P.ts6 * (a - b);
-        const V D2 = P.ts6 * (a - c);
+        const V a = vfma(k.rho0, ux2, vfma(k.mthird, rhop, h[K(2, 0, 0)]));   // kappa - e, e = rhop/3 - rho0 u^2
+        const V b = vfma(k.rho0, uy2, vfma(k.mthird, rhop, h[K(0, 2, 0)]));
+        const V c = vfma(k.rho0, uz2, vfma(k.mthird, rhop, h[K(0, 0, 2)]));
+        const V sixth_rhop = k.sixth * rhop;
+        const V T = k.tb6 * (a + b + c);
+        const V D1 = k.ts6 * (a - b);
+        const V D2 = k.ts6 * (a - c);
         const V TD1 = T + D1;
-        h[K(2, 0, 0)] = (TD1 + D2) + vfma(-P.r0h, ux2, sixth_rhop);
-        h[K(0, 2, 0)] = vfma(-2.0f, D1, T + D2) + vfma(-P.r0h, uy2, sixth_rhop);
-        h[K(0, 0, 2)] = vfma(-2.0f, D2, TD1) + vfma(-P.r0h, uz2, sixth_rhop);
+        h[K(2, 0, 0)] = (TD1 + D2) + vfma(k.mr0h, ux2, sixth_rhop);
+        h[K(0, 2, 0)] = vfma(k.mtwo, D1, T + D2) + vfma(k.mr0h, uy2, sixth_rhop);
+        h[K(0, 0, 2)] = vfma(k.mtwo, D2, TD1) + vfma(k.mr0h, uz2, sixth_rhop);
     }
     // order 3 (force moments F/3 on 210, 201, 120, 021, 102, 012)
-    const V gx3 = P.f3 * Fx, gy3 = P.f3 * Fy, gz3 = P.f3 * Fz;
-    RELAX(K(2, 1, 0), P.a3, vfma(P.b3, uy * tx, gy3));
-    RELAX(K(2, 0, 1), P.a3, vfma(P.b3, uz * tx, gz3));
-    RELAX(K(1, 2, 0), P.a3, vfma(P.b3, ux * ty, gx3));
-    RELAX(K(0, 2, 1), P.a3, vfma(P.b3, uz * ty, gz3));
-    RELAX(K(1, 0, 2), P.a3, vfma(P.b3, ux * tz, gx3));
-    RELAX(K(0, 1, 2), P.a3, vfma(P.b3, uy * tz, gy3));
-    RELAX(K(1, 1, 1), P.a3e, P.b3e * (uxy * uz));
+    const V gx3 = k.f3 * Fx, gy3 = k.f3 * Fy, gz3 = k.f3 * Fz;
+    RELAX(K(2, 1, 0), k.a3, vfma(k.b3, uy * tx, gy3));
+    RELAX(K(2, 0, 1), k.a3, vfma(k.b3, uz * tx, gz3));
+    RELAX(K(1, 2, 0), k.a3, vfma(k.b3, ux * ty, gx3));
+    RELAX(K(0, 2, 1), k.a3, vfma(k.b3, uz * ty, gz3));
+    RELAX(K(1, 0, 2), k.a3, vfma(k.b3, ux * tz, gx3));
+    RELAX(K(0, 1, 2), k.a3, vfma(k.b3, uy * tz, gy3));
+    RELAX(K(1, 1, 1), k.a3e, k.b3e * (uxy * uz));
     // order 4
     {
-        const V x3 = 3.0f * ux2, y3 = 3.0f * uy2;
-        const V r4 = P.b4r * rhop;
-        RELAX(K(2, 2, 0), P.a4, vfma(P.b4u, vfma(x3, uy2, ux2 + uy2), r4));
-        RELAX(K(2, 0, 2), P.a4, vfma(P.b4u, vfma(x3, uz2, ux2 + uz2), r4));
-        RELAX(K(0, 2, 2), P.a4, vfma(P.b4u, vfma(y3, uz2, uy2 + uz2), r4));
+        const V x3 = k.three * ux2, y3 = k.three * uy2;
+        const V r4 = k.b4r * rhop;
+        RELAX(K(2, 2, 0), k.a4, vfma(k.b4u, vfma(x3, uy2, ux2 + uy2), r4));
+        RELAX(K(2, 0, 2), k.a4, vfma(k.b4u, vfma(x3, uz2, ux2 + uz2), r4));
+        RELAX(K(0, 2, 2), k.a4, vfma(k.b4u, vfma(y3, uz2, uy2 + uz2), r4));
     }
-    RELAX(K(2, 1, 1), P.a4m, P.b4m * (tx * uyz));
-    RELAX(K(1, 2, 1), P.a4m, P.b4m * (ty * uxz));
-    RELAX(K(1, 1, 2), P.a4m, P.b4m * (tz * uxy));
+    RELAX(K(2, 1, 1), k.a4m, k.b4m * (tx * uyz));
+    RELAX(K(1, 2, 1), k.a4m, k.b4m * (ty * uxz));
+    RELAX(K(1, 1, 2), k.a4m, k.b4m * (tz * uxy));
     // order 5 (force moments F/9 on 221, 212, 122)
-    RELAX(K(2, 2, 1), P.a5, vfma(P.b5, uz * (tx * ty), P.f5 * Fz));
-    RELAX(K(2, 1, 2), P.a5, vfma(P.b5, uy * (tx * tz), P.f5 * Fy));
-    RELAX(K(1, 2, 2), P.a5, vfma(P.b5, ux * (ty * tz), P.f5 * Fx));
+    RELAX(K(2, 2, 1), k.a5, vfma(k.b5, uz * (tx * ty), k.f5 * Fz));
+    RELAX(K(2, 1, 2), k.a5, vfma(k.b5, uy * (tx * tz), k.f5 * Fy));
+    RELAX(K(1, 2, 2), k.a5, vfma(k.b5, ux * (ty * tz), k.f5 * Fx));
     // order 6
     {
         const V s1 = ux2 + uy2 + uz2;
         const V s2 = vfma(ux2, uy2 + uz2, uy2 * uz2);
         const V s3 = ux2 * uy2 * uz2;
-        RELAX(K(2, 2, 2), P.a6, vfma(P.b6u, vfma(1.0f / 9.0f, s1, vfma(third, s2, s3)), P.b6r * rhop));
+        RELAX(K(2, 2, 2), k.a6, vfma(k.b6u, vfma(k.ninth, s1, vfma(k.third, s2, s3)), k.b6r * rhop));
     }
 #undef RELAX
-    sweep_invh<9>(h, uz, uz2);
-    sweep_invh<3>(h, uy, uy2);
-    sweep_invh<1>(h, ux, ux2);
+    sweep_invh<9>(h, uz, uz2, k);
+    sweep_invh<3>(h, uy, uy2, k);
+    sweep_invh<1>(h, ux, ux2, k);
 }
 
 __device__ __forceinline__ void collide(float (&h)[27], float Fx, float Fy, float Fz, const StepParams &P,

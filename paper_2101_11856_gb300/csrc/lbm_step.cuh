@@ -242,6 +242,108 @@ __device__ __forceinline__ void store_yzface2(const StepParams &P, int y, int z,
     }
 }
 
+// ---- node pairs (x, x + 1) with x even, 16-bit storage ---------------------------------------
+// With nx even every pair starts on an even cell index, so one aligned 32-bit word holds both
+// nodes' values of a direction wherever the access is not shifted along x: every access of an
+// even step and the c_x = 0 directions of an odd step.  The c_x = +-1 directions of an odd step
+// are shifted by one element: their two values are the high half of the aligned word before and
+// the low half of the aligned word after (the neighbouring threads read the same words, so the
+// second read is served by L1), and they are written as two 16-bit halves.
+template <typename St> struct Half2Of;
+template <> struct Half2Of<__half> {
+    static __device__ __forceinline__ F2 unpack(uint32_t w) { return {__half22float2(*reinterpret_cast<const __half2 *>(&w))}; }
+    static __device__ __forceinline__ uint32_t pack(F2 v) {
+        const __half2 p = __float22half2_rn(v.v);
+        return *reinterpret_cast<const uint32_t *>(&p);
+    }
+};
+template <> struct Half2Of<__nv_bfloat16> {
+    static __device__ __forceinline__ F2 unpack(uint32_t w) {
+        return {__bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&w))};
+    }
+    static __device__ __forceinline__ uint32_t pack(F2 v) {
+        const __nv_bfloat162 p = __float22bfloat162_rn(v.v);
+        return *reinterpret_cast<const uint32_t *>(&p);
+    }
+};
+// the values of elements e, e + 1 of a plane; SHIFTED: e is odd
+template <typename St, bool SHIFTED> __device__ __forceinline__ F2 ld_pair(const St *plane, long long e) {
+    if (!SHIFTED) return Half2Of<St>::unpack(*reinterpret_cast<const uint32_t *>(plane + e));
+    const uint32_t lo = *reinterpret_cast<const uint32_t *>(plane + (e - 1));
+    const uint32_t hi = *reinterpret_cast<const uint32_t *>(plane + (e + 1));
+    return Half2Of<St>::unpack(__byte_perm(lo, hi, 0x5432));
+}
+template <typename St, bool SHIFTED> __device__ __forceinline__ void st_pair(St *plane, long long e, F2 v) {
+    const uint32_t w = Half2Of<St>::pack(v);
+    if (!SHIFTED) {
+        *reinterpret_cast<uint32_t *>(plane + e) = w;
+    } else {
+        *reinterpret_cast<uint16_t *>(plane + e) = (uint16_t)(w & 0xffffu);
+        *reinterpret_cast<uint16_t *>(plane + (e + 1)) = (uint16_t)(w >> 16);
+    }
+}
+
+// streamed populations of the pair at `cell` (x even, 1 <= x, x + 1 <= nx - 2); row offsets off
+// and bounce-back flags bb of the 9 (c_y, c_z) source rows (odd steps)
+template <typename St, bool NB>
+__device__ __forceinline__ void load_pair(const StepParams &P, int cell, const int (&off)[9], const bool (&bb)[9],
+                                          F2 (&h)[27]) {
+#pragma unroll
+    for (int d = 0; d < 27; ++d) {
+        if (!NB || bb[d / 3]) {
+            h[d] = ld_pair<St, false>(static_cast<const St *>(P.fp[d]), cell);
+        } else {
+            const St *pl = static_cast<const St *>(P.fp[opp(d)]);
+            const long long e = (long long)cell + off[d / 3] - cx(d);
+            h[d] = cx(d) == 0 ? ld_pair<St, false>(pl, e) : ld_pair<St, true>(pl, e);
+        }
+    }
+}
+
+template <typename St, bool NB>
+__device__ __forceinline__ void store_pair(const StepParams &P, int cell, const int (&off)[9], const bool (&bb)[9],
+                                           const F2 (&h)[27]) {
+#pragma unroll
+    for (int d = 0; d < 27; ++d) {
+        if (!NB || bb[d / 3]) {
+            st_pair<St, false>(static_cast<St *>(P.fpo[opp(d)]), cell, h[d]);
+        } else {
+            St *pl = static_cast<St *>(P.fpo[d]);
+            const long long e = (long long)cell + off[d / 3] + cx(d);
+            if (cx(d) == 0) st_pair<St, false>(pl, e, h[d]);
+            else st_pair<St, true>(pl, e, h[d]);
+        }
+    }
+}
+
+// body force plus the band's immersed-boundary force of the pair (cell, cell + 1), cell even:
+// both nodes lie in the same 32-cell word of the band bitmap
+template <bool BAND>
+__device__ __forceinline__ void band_force_pair(const StepParams &P, int cell, F2 &Fx, F2 &Fy, F2 &Fz) {
+    Fx = {make_float2(P.Fx, P.Fx)};
+    Fy = {make_float2(P.Fy, P.Fy)};
+    Fz = {make_float2(P.Fz, P.Fz)};
+    if (BAND) {
+        const uint32_t mask = P.tile_mask[cell >> 5];
+        const int lane = cell & 31;
+        const uint32_t two = (mask >> lane) & 3u;
+        if (two) {
+            const long long b = P.tile_off[cell >> 5] + __popc(mask & ((1u << lane) - 1u));
+            if (two & 1u) {
+                Fx.v.x += P.bandF[b];
+                Fy.v.x += P.bandF[P.nband + b];
+                Fz.v.x += P.bandF[2 * P.nband + b];
+            }
+            if (two & 2u) {
+                const long long b1 = b + (two & 1u);
+                Fx.v.y += P.bandF[b1];
+                Fy.v.y += P.bandF[P.nband + b1];
+                Fz.v.y += P.bandF[2 * P.nband + b1];
+            }
+        }
+    }
+}
+
 // ---- the edge strips: y/z faces per block, x faces per lane --------------------------------
 // The pull rules of load_general and the matching push rules, arranged for a block that covers one
 // strip of one (y, z) row: the y/z rows come from yz_rows (uniform), and only the lanes at

@@ -95,6 +95,52 @@ __global__ void __launch_bounds__(STEP_BX) k_step_main(StepParams P) {
     }
 }
 
+// Main range with 16-bit storage and the method's collision on a grid with nx even: node pairs
+// (x, x + 1), x = XEDGE + 2 i, the packed FP32 collision (collide_v<F2>: bit for bit the same
+// arithmetic as one node at a time) and 32-bit accesses for both nodes wherever the AA addressing
+// keeps the pair aligned (load_pair / store_pair).  Rows as k_step_main without FS.
+template <typename St, bool NB, bool BAND, bool VOUT>
+__global__ void __launch_bounds__(STEP_BX) k_step_pair(StepParams P) {
+    const int y = blockIdx.y, z = blockIdx.z;
+    const bool inner = y >= 1 && y <= P.g.ny - 2 && z >= 1 && z <= P.g.nz - 2;   // uniform per block
+    if (P.inner_rows && !inner) return;
+    const int x = XEDGE + 2 * (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    if (x >= P.g.nx - XEDGE) return;
+    const int cell = x + P.g.nx * (y + P.g.ny * z);
+    int off[9], mir[9];
+    bool bb[9];
+    F2 h[27];
+    if (!NB || inner) {
+        row_offsets<-1, true, false>(P.g, y, z, off, bb, mir);
+        load_pair<St, NB>(P, cell, off, bb, h);
+    } else {
+        row_offsets<-1, false, false>(P.g, y, z, off, bb, mir);
+        load_pair<St, NB>(P, cell, off, bb, h);
+    }
+    F2 Fx, Fy, Fz, rho, ux, uy, uz;
+    band_force_pair<BAND>(P, cell, Fx, Fy, Fz);
+    collide_v<F2>(h, Fx, Fy, Fz, P, rho, ux, uy, uz);
+    if (VOUT) {
+        const long long n = P.g.ncell;
+        *reinterpret_cast<float2 *>(P.u_out + cell) = ux.v;
+        *reinterpret_cast<float2 *>(P.u_out + n + cell) = uy.v;
+        *reinterpret_cast<float2 *>(P.u_out + 2 * n + cell) = uz.v;
+    }
+    if (!NB || inner) {
+        row_offsets<+1, true, false>(P.g, y, z, off, bb, mir);
+        store_pair<St, NB>(P, cell, off, bb, h);
+    } else {
+        row_offsets<+1, false, false>(P.g, y, z, off, bb, mir);
+        store_pair<St, NB>(P, cell, off, bb, h);
+    }
+}
+
+// the main range runs in node pairs: 16-bit storage, the method's collision, nx even
+template <typename St, int COLL> __host__ __device__ constexpr bool pair_storage() {
+    return sizeof(St) == 2 && COLL == COLL_ACM;
+}
+inline bool pair_grid(const Geometry &g) { return g.nx % 2 == 0; }
+
 // one warp per edge strip of one row, EDGE_ROWS rows (y) per block: blockIdx.y * EDGE_ROWS +
 // threadIdx.y = y, blockIdx.z = z.  With a main range, blockIdx.x picks the left (0) or right
 // (1) strip (one launch for both: measured faster than a launch per side); short rows run the
@@ -160,8 +206,18 @@ cudaError_t launch_step_tt(const StepParams &P, int part, cudaStream_t st) {
             k_step_rows<St, NB, BAND, COLL, VOUT, FS><<<grid, block, 0, st>>>(P);
         }
     } else if (has_interior(g)) {
-        if constexpr (FS) return cudaErrorInvalidValue;
-        else k_step_main<St, NB, BAND, COLL, VOUT, FS><<<dim3(xb, g.ny, g.nz), threads, 0, st>>>(P);
+        if constexpr (FS) {
+            return cudaErrorInvalidValue;
+        } else if constexpr (pair_storage<St, COLL>()) {
+            if (pair_grid(g)) {
+                const int pairs = range / 2, pthreads = pairs <= 32 ? 32 : STEP_BX;
+                k_step_pair<St, NB, BAND, VOUT><<<dim3(step_blocks(pairs, pthreads), g.ny, g.nz), pthreads, 0, st>>>(P);
+            } else {
+                k_step_main<St, NB, BAND, COLL, VOUT, FS><<<dim3(xb, g.ny, g.nz), threads, 0, st>>>(P);
+            }
+        } else {
+            k_step_main<St, NB, BAND, COLL, VOUT, FS><<<dim3(xb, g.ny, g.nz), threads, 0, st>>>(P);
+        }
     }
     return cudaGetLastError();
 }
