@@ -129,9 +129,16 @@ def test_samples_on_faces_and_edges_of_cells():
 
 @pytest.mark.parametrize("storage,tol", [("f16", 5e-3), ("bf16", 4e-2)])
 def test_reduced_precision_storage(storage, tol):
-    """FP16/BF16 deviation storage, FP32 math: error against the FP64 oracle, reported."""
+    """FP16/BF16 deviation storage, FP32 math: error against the FP64 oracle after the 100 steps of
+    the Taylor-Green 32^3 configuration, reported per field (rho - 1, u_x, u_y, u_z); the pass
+    bar is stability only."""
     s = scenes.scene_tgv32()
-    g, o = run_pair(32, 32, 32, s["nu"], 50, s["rho"], s["u"], storage=storage)
+    g, o = run_pair(32, 32, 32, s["nu"], 100, s["rho"], s["u"], storage=storage)
     e_rho, e_drho, e_u = compare_fields(g, o)
-    print(f"{storage} TGV32 50 steps: rel L2 rho {e_rho:.2e}, rho-1 {e_drho:.2e}, u {e_u:.2e}")
+    rg, ug = g.macroscopic()
+    uo = o.macroscopic()[1].numpy()
+    comp = [rel_l2(ug[a], uo[a]) for a in range(3)]
+    print(f"{storage} TGV32 100 steps: rel L2 rho {e_rho:.2e}, rho-1 {e_drho:.2e}, u {e_u:.2e} "
+          f"(u_x {comp[0]:.2e}, u_y {comp[1]:.2e}, u_z {comp[2]:.2e}; u_z of the oracle is "
+          f"{np.linalg.norm(uo[2]):.1e} in L2)")
     assert np.isfinite(e_u) and e_u <= tol
