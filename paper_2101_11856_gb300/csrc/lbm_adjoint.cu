@@ -741,7 +741,7 @@ extern "C" int lbm_adjoint(lbm_ctx *h, int n, int K, const lbm_loss *loss, doubl
             if (S > 0) {
                 if (!kept) {
                     CK(launch_band_moments(h->storage, P, h->band_cell, h->band_rho, h->band_u, st));
-                    CK(launch_ib_interp(S, nb, h->X, h->area, h->ub, h->corner_band, h->band_rho, h->band_u, h->g, st));
+                    CK(launch_ib_interp(P, S, h->X, h->area, h->ub_zero ? nullptr : h->ub, h->band_rho, h->band_u, h->g, st));
                     CK(launch_ib_spread(S, nb, nullptr, h->X, h->g, h->base_nbr, h->cstart, h->ccount, h->bandF, st));
                 }
                 CK(with_storage(h->storage, [&](auto tag) {

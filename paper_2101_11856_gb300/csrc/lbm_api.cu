@@ -30,7 +30,7 @@ int step_with(lbm_ctx *h, const StepParams &P) {
     const bool band = h->S > 0;
     if (band) {
         { Timed tm(h, LBM_KERNEL_BAND); CK(launch_band_moments(h->storage, P, h->band_cell, h->band_rho, h->band_u, h->stream)); }
-        { Timed tm(h, LBM_KERNEL_INTERP); CK(launch_ib_interp(h->S, h->nband, h->X, h->area, h->ub, h->corner_band, h->band_rho, h->band_u, h->g, h->stream)); }
+        { Timed tm(h, LBM_KERNEL_INTERP); CK(launch_ib_interp(P, h->S, h->X, h->area, h->ub_zero ? nullptr : h->ub, h->band_rho, h->band_u, h->g, h->stream)); }
         { Timed tm(h, LBM_KERNEL_SPREAD); CK(launch_ib_spread(h->S, h->nband, h->band_count_dev, h->X, h->g, h->base_nbr, h->cstart, h->ccount, h->bandF, h->stream)); }
     }
     {
@@ -367,6 +367,7 @@ int lbm_set_solids(lbm_ctx *h, const float *samples, long long count, const floa
     free_solid(h);
     h->S = (long long)S;
     h->nband = nb;
+    h->ub_zero = std::all_of(vb.begin(), vb.end(), [](float v) { return v == 0.0f; });
     h->ntiles = ntiles;
     h->order = ord;
     if ((rc = upload(h, &h->X, Xs)) || (rc = upload(h, &h->area, As)) || (rc = upload(h, &h->ub, Us)) ||

@@ -49,9 +49,9 @@ cudaError_t launch_macro(int storage, const StepParams &P, bool band, int force_
 cudaError_t launch_finalize(const double *partial, long long n, int count, double *out, cudaStream_t st);
 cudaError_t launch_band_moments(int storage, const StepParams &P, const int *band_cell, float *band_rho, float *band_u,
                                 cudaStream_t st);
-cudaError_t launch_ib_interp(long long S, long long nband, const float *X, const float *area, const float *ub,
-                             const int *corner_band, const float *band_rho, const float *band_u, float *g,
-                             cudaStream_t st);
+// the band bitmap, band stride (nband) and geometry come from P; ub = nullptr: zero boundary velocity
+cudaError_t launch_ib_interp(const StepParams &P, long long S, const float *X, const float *area, const float *ub,
+                             const float *band_rho, const float *band_u, float *g, cudaStream_t st);
 // nband: band nodes (or the stride of the band arrays when count is set); count: device
 // count of band nodes (moving solids) or nullptr
 cudaError_t launch_ib_spread(long long S, long long nband, const int *count, const float *X, const float *g,

@@ -189,19 +189,32 @@ __device__ __forceinline__ float corner_weight(int c, float wx, float wy, float 
     return ((c & 1) ? wx : 1.0f - wx) * ((c & 2) ? wy : 1.0f - wy) * ((c & 4) ? wz : 1.0f - wz);
 }
 
-// interpolation (Eq. 6) and penalty force (Eq. 7) per sample
-__global__ void __launch_bounds__(256) k_ib_interp(long long S, long long nband, const float *__restrict__ X,
+// band index of a node known to be in the band, from the band bitmap (one mask and one offset
+// word per 32 cells)
+__device__ __forceinline__ int band_of(const StepParams &P, long long cell) {
+    const uint32_t mask = P.tile_mask[cell >> 5];
+    return P.tile_off[cell >> 5] + __popc(mask & ((1u << (cell & 31)) - 1u));
+}
+
+// interpolation (Eq. 6) and penalty force (Eq. 7) per sample; the 8 stencil nodes' band indices
+// come from the bitmap (cached words, shared by the neighbouring samples of the cell-sorted
+// order) instead of a stored table; ub = nullptr: boundary velocity 0
+__global__ void __launch_bounds__(256) k_ib_interp(StepParams P, long long S, const float *__restrict__ X,
                                                    const float *__restrict__ area, const float *__restrict__ ub,
-                                                   const int *__restrict__ corner_band, const float *__restrict__ band_rho,
-                                                   const float *__restrict__ band_u, float *__restrict__ g) {
+                                                   const float *__restrict__ band_rho, const float *__restrict__ band_u,
+                                                   float *__restrict__ g) {
     const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= S) return;
+    const long long nband = P.nband;
     const float x = X[s], y = X[S + s], z = X[2 * S + s];
-    const float wx = x - floorf(x), wy = y - floorf(y), wz = z - floorf(z);
+    const float fx = floorf(x), fy = floorf(y), fz = floorf(z);
+    const float wx = x - fx, wy = y - fy, wz = z - fz;
+    const long long base = (long long)fx + P.g.nx * ((long long)fy + (long long)P.g.ny * (long long)fz);
     float rs = 0.0f, us = 0.0f, vs = 0.0f, ws = 0.0f;
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
-        const int b = corner_band[(long long)c * S + s];
+        const long long cell = base + (c & 1) + ((c & 2) ? P.g.nx : 0) + ((c & 4) ? (long long)P.g.nxy : 0);
+        const int b = band_of(P, cell);
         const float K = corner_weight(c, wx, wy, wz);
         rs = fmaf(K, band_rho[b], rs);
         us = fmaf(K, band_u[b], us);
@@ -209,9 +222,10 @@ __global__ void __launch_bounds__(256) k_ib_interp(long long S, long long nband,
         ws = fmaf(K, band_u[2 * nband + b], ws);
     }
     const float a = rs * area[s];
-    g[s] = a * (ub[s] - us);
-    g[S + s] = a * (ub[S + s] - vs);
-    g[2 * S + s] = a * (ub[2 * S + s] - ws);
+    const float bx = ub ? ub[s] : 0.0f, by = ub ? ub[S + s] : 0.0f, bz = ub ? ub[2 * S + s] : 0.0f;
+    g[s] = a * (bx - us);
+    g[S + s] = a * (by - vs);
+    g[2 * S + s] = a * (bz - ws);
 }
 
 // spreading (Eq. 8) as a deterministic gather: band node k sums K g over the samples whose
@@ -360,10 +374,9 @@ cudaError_t launch_band_moments(int storage, const StepParams &P, const int *ban
     });
 }
 
-cudaError_t launch_ib_interp(long long S, long long nband, const float *X, const float *area, const float *ub,
-                             const int *corner_band, const float *band_rho, const float *band_u, float *g,
-                             cudaStream_t st) {
-    k_ib_interp<<<blocks_for(S, 256), 256, 0, st>>>(S, nband, X, area, ub, corner_band, band_rho, band_u, g);
+cudaError_t launch_ib_interp(const StepParams &P, long long S, const float *X, const float *area, const float *ub,
+                             const float *band_rho, const float *band_u, float *g, cudaStream_t st) {
+    k_ib_interp<<<blocks_for(S, 256), 256, 0, st>>>(P, S, X, area, ub, band_rho, band_u, g);
     return cudaGetLastError();
 }
 
