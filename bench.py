@@ -32,9 +32,10 @@ import scenes  # noqa: E402
 
 BYTES_PER_CELL = {"f32": 216, "f16": 108, "bf16": 108}   # 27 loads + 27 stores per cell update
 PAPER_MLUPS = 1200 * 250 * 840 / 1.21 / 1e6                # Table 3, Fig. 1 scene: 1.21 s/step on 4x P40
-# DRAM bytes per cell of k_step_main (FP32) from one ncu capture of the current kernel
-# (profiles/k_step_main_box_city_480x100x336.md); None once the kernel changes
-TRAFFIC_PER_CELL = {"f32": 215.8}
+# DRAM bytes per cell of the main-range kernel from one ncu capture of the current kernel, mean of
+# the two AA parities: k_step_main for FP32 (profiles/k_step_main_box_city_480x100x336.md),
+# k_step_pair for FP16 (profiles/k_step_pair_box_city_480x100x336.md); absent once a kernel changes
+TRAFFIC_PER_CELL = {"f32": 215.8, "f16": 110.8}
 
 
 def parse():
@@ -46,6 +47,7 @@ def parse():
     ap.add_argument("--scale", type=float, default=1.0, help="shrink every grid axis (testing only)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp16", action="store_true")
+    ap.add_argument("--no-precision", action="store_true", help="skip the per-field errors against the stored oracle run")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-models", action="store_true", help="skip the BGK / raw-MRT comparison runs")
@@ -181,20 +183,29 @@ def run_reference(args):
     print(json.dumps(line))
 
 
-def adjoint_cost(torch, args):
+def adjoint_cost(torch, args, dims=None, K=None):
     """Adjoint workload: 128^3 channel, IB sphere r = 12.6 at (40, 64, 64) with 2,000 samples,
     200 steps, loss = mean drag + kinetic energy of the slab 96 <= x < 128, checkpoints every
     20 steps (--adjoint-steps / --adjoint-k change the last two, for small profiling runs).
-    Reports the adjoint (forward + backward) time against the same number of forward steps."""
+    ``dims`` = (nx, ny, nz) runs the same channel scaled to that grid (sphere centre at 40/128 of
+    the length, radius and sample count scaled with ny, slab the last quarter); ``K`` overrides
+    the checkpoint interval.  Reports the adjoint (forward + backward) time against the same
+    number of forward steps."""
     from paper_2101_11856_gb300 import Solver
-    n = max(8, int(round(128 * args.scale))) if args.scale < 1.0 else 128
-    steps, K = args.adjoint_steps, args.adjoint_k
-    X, A = scenes.fibonacci_sphere((40.0 * n / 128, n / 2, n / 2), 12.6 * n / 128, 2000)
-    rho, u = scenes.uniform_flow(n, n, n, (0.05, 0, 0))
+    if dims is None:
+        n = max(8, int(round(128 * args.scale))) if args.scale < 1.0 else 128
+        dims = (n, n, n)
+    nx, ny, nz = dims
+    steps, K = args.adjoint_steps, (args.adjoint_k if K is None else K)
+    f = ny / 128.0
+    count = int(round(2000 * f * f))
+    X, A = scenes.fibonacci_sphere((40.0 * nx / 128, ny / 2, nz / 2), 12.6 * f, count)
+    rho, u = scenes.uniform_flow(nx, ny, nz, (0.05, 0, 0))
     faces = ("inlet", "outlet", "periodic", "periodic", "periodic", "periodic")
+    x0 = int(96 * nx / 128)
 
     def make():
-        s = Solver(n, n, n, 0.01, faces=faces, u_in=0.05, noise=0.01, seed=2101)
+        s = Solver(nx, ny, nz, 0.01, faces=faces, u_in=0.05, noise=0.01, seed=2101)
         s.set_state(rho, u)
         s.set_solids(X, A)
         return s
@@ -208,18 +219,21 @@ def adjoint_cost(torch, args):
     fwd = time.perf_counter() - t0
     s.close()
     s = make()
-    s.adjoint(2, 1, 1.0, 1.0, int(96 * n / 128), n, 2000)     # warm-up (allocations, module load)
+    s.adjoint(2, 1, 1.0, 1.0, x0, nx)     # warm-up (allocations, module load)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    L, dcoef, dpos = s.adjoint(steps, K, 1.0, 1.0, int(96 * n / 128), n, 2000)
+    L, dcoef, dpos = s.adjoint(steps, K, 1.0, 1.0, x0, nx)
     torch.cuda.synchronize()
     adj = time.perf_counter() - t0
     s.close()
+    torch.cuda.empty_cache()
     ok = bool(np.isfinite(L) and np.all(np.isfinite(dcoef)) and np.all(np.isfinite(dpos)))
-    return {"workload": f"channel_sphere_{n}^3", "samples": 2000, "steps": steps, "checkpoint_K": K,
+    N = nx * ny * nz
+    return {"workload": f"channel_sphere_{nx}x{ny}x{nz}", "samples": count, "steps": steps, "checkpoint_K": K,
+            "state_mb": round(N * 27 * 4 / 1e6, 1),
             "forward_ms": fwd * 1e3, "adjoint_ms": adj * 1e3, "adjoint_over_forward": adj / fwd,
-            "adjoint_mlups": n ** 3 * steps / adj / 1e6, "finite": ok,
-            "what": "lbm_adjoint (forward with checkpoints + segment recompute + backward) vs lbm_step x 200"}
+            "adjoint_mlups": N * steps / adj / 1e6, "finite": ok,
+            "what": f"lbm_adjoint (forward with checkpoints + segment recompute + backward) vs lbm_step x {steps}"}
 
 
 def tracer_run(torch, lbm, make, d, args, N, n_int, peak, world, steps):
@@ -436,7 +450,7 @@ def cpu_baselines(d, args):
     head, _ = oracle_sample(d, 1, (0, d["nx"] // 2, 0, d["ny"], 4))
     torch.set_num_threads(1)
     try:
-        one, _ = oracle_sample(d, 1, (0, d["nx"] // 8, 0, d["ny"], 4))
+        one, _ = oracle_sample(d, 1, (2 * d["nx"] // 5, d["nx"] // 8, 0, d["ny"], 4))   # among the buildings
         plan = (("tgv32_100_steps", "tgv32", 100, None, 10, None),
                 ("sphere_channel_256x128x128", "sphere", 1, (256, 128, 16), 1, (256, 128, 4)),
                 ("adjoint_channel_128^3_forward", "adjoint", 1, (128, 128, 32), 1, (128, 128, 4)))
@@ -522,7 +536,9 @@ def main():
             raise RuntimeError(f"non-finite state in the {storage}/{collision} run")
         return {"mlups": world * N / (msx / steps * 1e-3) / 1e6, "ms_per_step": msx / steps, "step_kernel_ms": kx,
                 "roofline": {"bound": "hbm", "achieved": achx, "peak": peak, "unit": "GB/s", "frac": achx / peak,
-                             "bytes_per_cell": BYTES_PER_CELL[storage]}}
+                             "bytes_per_cell": BYTES_PER_CELL[storage],
+                             "traffic": (TRAFFIC_PER_CELL[storage] * n_int
+                                         if collision == "acm" and storage in TRAFFIC_PER_CELL else None)}}
 
     # ---- FP32, device-resident: the headline value -----------------------------------
     s = make("f32")
@@ -605,7 +621,8 @@ def main():
     fp16 = None if args.no_fp16 else side_run("f16", "acm", n_side)
     if fp16 is not None:
         fp16["bf16"] = side_run("bf16", "acm", n_side)
-        fp16["per_field_error"] = precision_vs_oracle(torch, lbm, Solver) if args.scale == 1.0 else None
+        fp16["per_field_error"] = (precision_vs_oracle(torch, lbm, Solver)
+                                   if args.scale == 1.0 and not args.no_precision else None)
 
     # ---- comparison collisions of Sec. 6.1 (same workload, same step structure) -------------
     models = None
@@ -629,6 +646,11 @@ def main():
     adjoint = None
     if not args.no_adjoint:
         adjoint = adjoint_cost(torch, args)
+        if args.scale == 1.0:
+            # the same channel on a grid whose state (1.5 GB) is far larger than L2, and the 128^3
+            # workload with one segment (every state kept, no recompute)
+            adjoint["large_grid"] = adjoint_cost(torch, args, dims=(384, 192, 192))
+            adjoint["one_segment"] = adjoint_cost(torch, args, K=args.adjoint_steps)
 
     cpu = None
     if not args.no_cpu and rank == 0 and world == 1:

@@ -1,14 +1,16 @@
 // Moving and rotating solids (Algorithm 2 (c): the sample update after the IB stage, and the
-// torque reduction).  At the start of every step the samples are placed at the pose of the
-// previous time in FP64, re-sorted by base cell with the stable radix sort, and the band
-// (bitmap + tile offsets), the corner band indices and the spreading lists are rebuilt on the
-// device, the same structures lbm_set_solids builds on the host for a static solid.  The
-// band arrays have the fixed stride nband = 8 S (or N) and the band size is a device count,
-// so the host never waits for the rebuild.
+// torque reduction).  At the start of every step one cooperative launch (k_rebuild) places the
+// samples at the pose of the previous time in FP64, re-sorts them by base cell with a stable
+// radix sort, and rebuilds the band (bitmap + tile offsets), the corner band indices and the
+// spreading lists on the device, the same structures lbm_set_solids builds on the host for a
+// static solid.  The band arrays have the fixed stride nband = 8 S (or N) and the band size is
+// a device count, so the host never waits for the rebuild.
 #include <algorithm>
 #include <cmath>
 #include <string>
 #include <vector>
+
+#include <cooperative_groups.h>
 
 #include "lbm_ctx.h"
 #include "lbm_sort.cuh"
@@ -45,73 +47,8 @@ __device__ __forceinline__ long long base_cell(const Lattice &L, float x, float 
     return bx + (long long)L.nx * by + L.nxy * bz;
 }
 
-// positions of the reference samples (in their current order) at the new pose, with keys
-__global__ void __launch_bounds__(256) k_pose(long long S, const float *__restrict__ rel, Pose p, Lattice L,
-                                              float *__restrict__ Xtmp, uint32_t *__restrict__ key,
-                                              uint32_t *__restrict__ slot) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= S) return;
-    double X[3];
-    pose_point(p, rel, S, i, X);
-    const float x = (float)X[0], y = (float)X[1], z = (float)X[2];
-    Xtmp[i] = x;
-    Xtmp[S + i] = y;
-    Xtmp[2 * S + i] = z;
-    key[i] = (uint32_t)base_cell(L, x, y, z);
-    slot[i] = (uint32_t)i;
-}
-
-// the samples in sorted order: positions, reference coordinates, area, caller index and the
-// rigid-body boundary velocity V + Om x (X - c) (FP64)
-__global__ void __launch_bounds__(256) k_gather_samples(long long S, const uint32_t *__restrict__ slot,
-                                                        const float *__restrict__ Xtmp, const float *__restrict__ rel,
-                                                        const float *__restrict__ area, const int *__restrict__ sid,
-                                                        Pose p, float *__restrict__ X, float *__restrict__ rel_o,
-                                                        float *__restrict__ area_o, int *__restrict__ sid_o,
-                                                        float *__restrict__ ub) {
-    const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= S) return;
-    const long long i = slot[j];
-    double P[3];
-    pose_point(p, rel, S, i, P);
-    const double d[3] = {P[0] - p.c[0], P[1] - p.c[1], P[2] - p.c[2]};
-    const double u[3] = {p.V[0] + p.Om[1] * d[2] - p.Om[2] * d[1], p.V[1] + p.Om[2] * d[0] - p.Om[0] * d[2],
-                         p.V[2] + p.Om[0] * d[1] - p.Om[1] * d[0]};
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        X[a * S + j] = Xtmp[a * S + i];
-        rel_o[a * S + j] = rel[a * S + i];
-        ub[a * S + j] = (float)u[a];
-    }
-    area_o[j] = area[i];
-    sid_o[j] = sid[i];
-}
-
 __device__ __forceinline__ long long corner_cell(const Lattice &L, long long base, int c) {
     return base + (c & 1) + ((c >> 1) & 1) * (long long)L.nx + ((c >> 2) & 1) * L.nxy;
-}
-
-// band bitmap: the 8 stencil nodes of every sample
-__global__ void __launch_bounds__(256) k_mark_band(long long S, const float *__restrict__ X, Lattice L,
-                                                   uint32_t *__restrict__ mask) {
-    const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= S) return;
-    const long long b = base_cell(L, X[j], X[S + j], X[2 * S + j]);
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        const long long cell = corner_cell(L, b, c);
-        atomicOr(&mask[cell >> 5], 1u << (cell & 31));
-    }
-}
-
-__global__ void __launch_bounds__(256) k_popc(long long ntiles, const uint32_t *__restrict__ mask, int *__restrict__ off) {
-    const long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (w < ntiles) off[w] = __popc(mask[w]);
-}
-
-__global__ void k_band_total(long long ntiles, const uint32_t *__restrict__ mask, const int *__restrict__ off,
-                             int *__restrict__ count) {
-    *count = off[ntiles - 1] + __popc(mask[ntiles - 1]);
 }
 
 __device__ __forceinline__ int band_index(const uint32_t *__restrict__ mask, const int *__restrict__ off, long long cell) {
@@ -119,62 +56,6 @@ __device__ __forceinline__ int band_index(const uint32_t *__restrict__ mask, con
     const int l = (int)(cell & 31);
     if (!((m >> l) & 1u)) return -1;
     return off[cell >> 5] + __popc(m & ((1u << l) - 1u));
-}
-
-// band index of the 8 corners of every sample, and the cell of every band node
-__global__ void __launch_bounds__(256) k_corner_band(long long S, const float *__restrict__ X, Lattice L,
-                                                     const uint32_t *__restrict__ mask, const int *__restrict__ off,
-                                                     int *__restrict__ corner_band, int *__restrict__ band_cell) {
-    const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= S) return;
-    const long long b = base_cell(L, X[j], X[S + j], X[2 * S + j]);
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        const long long cell = corner_cell(L, b, c);
-        const int bi = band_index(mask, off, cell);
-        corner_band[c * S + j] = bi;
-        band_cell[bi] = (int)cell;   // equal values from every sample sharing the node
-    }
-}
-
-// the run of samples based at each band node: first sorted index, then its length
-__global__ void __launch_bounds__(256) k_run_start(long long S, const uint32_t *__restrict__ key,
-                                                   const int *__restrict__ corner_band, int *__restrict__ cstart) {
-    const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= S) return;
-    if (j == 0 || key[j - 1] != key[j]) cstart[corner_band[j]] = (int)j;
-}
-__global__ void __launch_bounds__(256) k_run_count(long long S, const uint32_t *__restrict__ key,
-                                                   const int *__restrict__ corner_band, const int *__restrict__ cstart,
-                                                   int *__restrict__ ccount) {
-    const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= S) return;
-    if (j == S - 1 || key[j + 1] != key[j]) {
-        const int bi = corner_band[j];
-        ccount[bi] = (int)(j - cstart[bi] + 1);
-    }
-}
-
-// for every band node, the band node of each of its 8 lower neighbours that is the base of
-// at least one sample (-1 otherwise); stride = the band array stride
-__global__ void __launch_bounds__(256) k_base_nbr(long long stride, const int *__restrict__ count,
-                                                  const int *__restrict__ band_cell, Lattice L,
-                                                  const uint32_t *__restrict__ mask, const int *__restrict__ off,
-                                                  const int *__restrict__ ccount, int *__restrict__ base_nbr) {
-    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= *count) return;
-    const long long cell = band_cell[k];
-    const int x = (int)(cell % L.nx), y = (int)((cell / L.nx) % L.ny), z = (int)(cell / L.nxy);
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        const int bx = x - (c & 1), by = y - ((c >> 1) & 1), bz = z - ((c >> 2) & 1);
-        int v = -1;
-        if (bx >= 0 && by >= 0 && bz >= 0) {
-            const int bi = band_index(mask, off, bx + (long long)L.nx * by + L.nxy * bz);
-            if (bi >= 0 && ccount[bi] > 0) v = bi;
-        }
-        base_nbr[c * stride + k] = v;
-    }
 }
 
 // FP64 block partial sums of the torque sum (X - c) x (-g)
@@ -207,6 +88,263 @@ __global__ void __launch_bounds__(256) k_rel(long long S, const float *__restric
     rel[i] = (float)((double)X[i] - cx);
     rel[S + i] = (float)((double)X[S + i] - cy);
     rel[2 * S + i] = (float)((double)X[2 * S + i] - cz);
+}
+
+// ---- the whole rebuild in one cooperative launch ----------------------------------------------
+// Phases of one kernel whose blocks are all resident (cooperative launch) and meet at grid-wide
+// barriers between the phases: pose and
+// keys (with the bitmap and run counters cleared), a stable LSD radix sort of the keys (8-bit
+// digits; the first REBUILD_SORT_BLOCKS blocks sort contiguous chunks, so the order within a digit
+// is the input order, as in sort_pairs), the samples gathered in sorted order, the band bitmap,
+// its prefix offsets and the band count, the corner band indices and band cells, the runs of
+// samples per base cell and the spreading lists (the structures lbm_set_solids builds on the host
+// for a static solid).
+constexpr int REBUILD_THREADS = 256;
+constexpr int REBUILD_SORT_BLOCKS = 32;
+
+struct RebuildArgs {
+    long long S, ntiles, stride;   // samples, bitmap words, band array stride
+    int bits;                      // significant bits of the keys
+    Pose p;
+    Lattice L;
+    const float *rel, *area_in;
+    const int *sid_in;
+    float *Xtmp, *X, *rel_o, *area_o, *ub;
+    int *sid_o;
+    uint32_t *key, *slot, *tkey, *tslot;
+    int *hist;                     // [256][REBUILD_SORT_BLOCKS]
+    int *bsum;                     // [gridDim.x]
+    uint32_t *mask;
+    int *off, *count, *corner_band, *band_cell, *cstart, *ccount, *base_nbr;
+};
+
+// exclusive scan of one value per thread over the block (REBUILD_THREADS threads); returns the
+// block total through *total (all threads)
+__device__ __forceinline__ long long block_exclusive(long long v, long long *total) {
+    __shared__ long long warp_tot[REBUILD_THREADS / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    long long incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) warp_tot[warp] = incl;
+    __syncthreads();
+    long long before = 0, all = 0;
+#pragma unroll
+    for (int w = 0; w < REBUILD_THREADS / 32; ++w) {
+        if (w < warp) before += warp_tot[w];
+        all += warp_tot[w];
+    }
+    __syncthreads();
+    *total = all;
+    return before + incl - v;
+}
+
+__global__ void __launch_bounds__(REBUILD_THREADS) k_rebuild(RebuildArgs a) {
+    namespace cg = cooperative_groups;
+    cg::grid_group grid = cg::this_grid();
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long nthr = (long long)gridDim.x * blockDim.x;
+    const long long S = a.S;
+    // pose, keys; clear the bitmap and the run counters
+    for (long long i = tid; i < S; i += nthr) {
+        double X[3];
+        pose_point(a.p, a.rel, S, i, X);
+        const float x = (float)X[0], y = (float)X[1], z = (float)X[2];
+        a.Xtmp[i] = x;
+        a.Xtmp[S + i] = y;
+        a.Xtmp[2 * S + i] = z;
+        a.key[i] = (uint32_t)base_cell(a.L, x, y, z);
+        a.slot[i] = (uint32_t)i;
+    }
+    for (long long w = tid; w < a.ntiles; w += nthr) a.mask[w] = 0u;
+    for (long long k = tid; k < a.stride; k += nthr) a.ccount[k] = 0;
+    grid.sync();
+
+    // stable radix sort of (key, slot) by 8-bit digits
+    __shared__ int cnt[256];
+    __shared__ int wcnt[REBUILD_THREADS / 32][256];
+    const int SB = REBUILD_SORT_BLOCKS;
+    const long long chunk = (S + SB - 1) / SB;
+    uint32_t *ka = a.key, *va = a.slot, *kb = a.tkey, *vb = a.tslot;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int shift = 0; shift < a.bits; shift += 8) {
+        const bool sorter = blockIdx.x < SB;
+        const long long c0 = blockIdx.x * chunk, c1 = c0 + chunk < S ? c0 + chunk : S;
+        if (sorter) {
+            cnt[threadIdx.x] = 0;
+            __syncthreads();
+            for (long long e = c0 + threadIdx.x; e < c1; e += blockDim.x) atomicAdd(&cnt[(ka[e] >> shift) & 255u], 1);
+            __syncthreads();
+            a.hist[threadIdx.x * SB + blockIdx.x] = cnt[threadIdx.x];
+        }
+        grid.sync();
+        if (blockIdx.x == 0) {
+            // exclusive scan of the digit-major histogram: thread d owns digit d's SB entries
+            long long local = 0;
+            for (int g = 0; g < SB; ++g) local += a.hist[threadIdx.x * SB + g];
+            long long total;
+            long long run = block_exclusive(local, &total);
+            for (int g = 0; g < SB; ++g) {
+                const int c = a.hist[threadIdx.x * SB + g];
+                a.hist[threadIdx.x * SB + g] = (int)run;
+                run += c;
+            }
+        }
+        grid.sync();
+        if (sorter) {
+            // running start of each digit for this chunk, tile by tile in (warp, item, lane) order
+            cnt[threadIdx.x] = a.hist[threadIdx.x * SB + blockIdx.x];
+            __syncthreads();
+            const uint32_t lt = (1u << lane) - 1u;
+            for (long long t0 = c0; t0 < c1; t0 += SORT_TILE) {
+                for (int k = threadIdx.x; k < (REBUILD_THREADS / 32) * 256; k += blockDim.x) (&wcnt[0][0])[k] = 0;
+                __syncthreads();
+                const long long base = t0 + (long long)warp * 32 * SORT_ITEMS;
+                uint32_t key[SORT_ITEMS], val[SORT_ITEMS];
+                int rank[SORT_ITEMS];
+#pragma unroll
+                for (int it = 0; it < SORT_ITEMS; ++it) {
+                    const long long e = base + it * 32 + lane;
+                    const bool valid = e < c1;
+                    key[it] = valid ? ka[e] : 0u;
+                    val[it] = valid ? va[e] : 0u;
+                    const uint32_t digit = valid ? (key[it] >> shift) & 255u : 256u;
+                    const uint32_t peers = __match_any_sync(0xffffffffu, digit);
+                    const int before = valid ? wcnt[warp][digit] : 0;
+                    rank[it] = before + __popc(peers & lt);
+                    __syncwarp();
+                    if (valid && lane == __ffs(peers) - 1) wcnt[warp][digit] = before + __popc(peers);
+                    __syncwarp();
+                }
+                __syncthreads();
+                {
+                    const int d = threadIdx.x;
+                    int run = cnt[d];
+#pragma unroll
+                    for (int w = 0; w < REBUILD_THREADS / 32; ++w) {
+                        const int c = wcnt[w][d];
+                        wcnt[w][d] = run;
+                        run += c;
+                    }
+                    cnt[d] = run;
+                }
+                __syncthreads();
+#pragma unroll
+                for (int it = 0; it < SORT_ITEMS; ++it) {
+                    const long long e = base + it * 32 + lane;
+                    if (e < c1) {
+                        const int pos = wcnt[warp][(key[it] >> shift) & 255u] + rank[it];
+                        kb[pos] = key[it];
+                        vb[pos] = val[it];
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        grid.sync();
+        uint32_t *t = ka; ka = kb; kb = t;
+        t = va; va = vb; vb = t;
+    }
+
+    // samples in sorted order, rigid-body boundary velocities
+    for (long long j = tid; j < S; j += nthr) {
+        const long long i = va[j];
+        double P[3];
+        pose_point(a.p, a.rel, S, i, P);
+        const double d[3] = {P[0] - a.p.c[0], P[1] - a.p.c[1], P[2] - a.p.c[2]};
+        const double u[3] = {a.p.V[0] + a.p.Om[1] * d[2] - a.p.Om[2] * d[1],
+                             a.p.V[1] + a.p.Om[2] * d[0] - a.p.Om[0] * d[2],
+                             a.p.V[2] + a.p.Om[0] * d[1] - a.p.Om[1] * d[0]};
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            a.X[c * S + j] = a.Xtmp[c * S + i];
+            a.rel_o[c * S + j] = a.rel[c * S + i];
+            a.ub[c * S + j] = (float)u[c];
+        }
+        a.area_o[j] = a.area_in[i];
+        a.sid_o[j] = a.sid_in[i];
+    }
+    grid.sync();
+    // band bitmap
+    for (long long j = tid; j < S; j += nthr) {
+        const long long b = base_cell(a.L, a.X[j], a.X[S + j], a.X[2 * S + j]);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const long long cell = corner_cell(a.L, b, c);
+            atomicOr(&a.mask[cell >> 5], 1u << (cell & 31));
+        }
+    }
+    grid.sync();
+    // offsets of the bitmap words (exclusive scan of their popcounts) over contiguous chunks
+    {
+        const long long wchunk = (a.ntiles + gridDim.x - 1) / gridDim.x;
+        const long long w0 = blockIdx.x * wchunk, w1 = w0 + wchunk < a.ntiles ? w0 + wchunk : a.ntiles;
+        const long long per = (wchunk + blockDim.x - 1) / blockDim.x;
+        const long long t0 = w0 + threadIdx.x * per, t1 = t0 + per < w1 ? t0 + per : w1;
+        long long local = 0;
+        for (long long w = t0; w < t1; ++w) local += __popc(a.mask[w]);
+        long long total;
+        const long long before = block_exclusive(local, &total);
+        if (threadIdx.x == 0) a.bsum[blockIdx.x] = (int)total;
+        grid.sync();
+        if (blockIdx.x == 0) {
+            const long long v = threadIdx.x < gridDim.x ? a.bsum[threadIdx.x] : 0;
+            long long all;
+            // gridDim.x <= REBUILD_THREADS (checked on the host)
+            const long long ex = block_exclusive(v, &all);
+            __syncthreads();
+            if (threadIdx.x < gridDim.x) a.bsum[threadIdx.x] = (int)ex;
+            if (threadIdx.x == 0) *a.count = (int)all;
+        }
+        grid.sync();
+        long long run = a.bsum[blockIdx.x] + before;
+        for (long long w = t0; w < t1; ++w) {
+            a.off[w] = (int)run;
+            run += __popc(a.mask[w]);
+        }
+    }
+    grid.sync();
+    // corner band indices and band cells
+    for (long long j = tid; j < S; j += nthr) {
+        const long long b = base_cell(a.L, a.X[j], a.X[S + j], a.X[2 * S + j]);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const long long cell = corner_cell(a.L, b, c);
+            const int bi = band_index(a.mask, a.off, cell);
+            a.corner_band[c * S + j] = bi;
+            a.band_cell[bi] = (int)cell;
+        }
+    }
+    grid.sync();
+    for (long long j = tid; j < S; j += nthr)
+        if (j == 0 || ka[j - 1] != ka[j]) a.cstart[a.corner_band[j]] = (int)j;
+    grid.sync();
+    for (long long j = tid; j < S; j += nthr)
+        if (j == S - 1 || ka[j + 1] != ka[j]) {
+            const int bi = a.corner_band[j];
+            a.ccount[bi] = (int)(j - a.cstart[bi] + 1);
+        }
+    grid.sync();
+    // spreading lists: for every band node, the band node of each of its 8 lower neighbours that
+    // is the base of at least one sample
+    const long long nb = *a.count;
+    for (long long k = tid; k < nb; k += nthr) {
+        const long long cell = a.band_cell[k];
+        const int x = (int)(cell % a.L.nx), y = (int)((cell / a.L.nx) % a.L.ny), z = (int)(cell / a.L.nxy);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const int bx = x - (c & 1), by = y - ((c >> 1) & 1), bz = z - ((c >> 2) & 1);
+            int v = -1;
+            if (bx >= 0 && by >= 0 && bz >= 0) {
+                const int bi = band_index(a.mask, a.off, bx + (long long)a.L.nx * by + a.L.nxy * bz);
+                if (bi >= 0 && a.ccount[bi] > 0) v = bi;
+            }
+            a.base_nbr[c * a.stride + k] = v;
+        }
+    }
 }
 
 inline unsigned blocks_of(long long n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -258,7 +396,7 @@ struct MotionWs {
 int motion_ws(lbm_ctx *h, MotionWs &w) {
     const long long S = h->S;
     const size_t pw = lbm::al256((size_t)4 * S);
-    const size_t need = 4 * pw + lbm::al256(std::max(lbm::sort_workspace_bytes(S), lbm::scan_workspace_bytes(h->ntiles)));
+    const size_t need = 4 * pw + lbm::al256(sizeof(int) * ((size_t)256 * lbm::REBUILD_SORT_BLOCKS + lbm::REBUILD_THREADS));
     if (need > h->motion_ws_bytes) {
         if (h->motion_ws) cudaFree(h->motion_ws);
         h->motion_ws = nullptr;
@@ -279,6 +417,25 @@ int motion_ws(lbm_ctx *h, MotionWs &w) {
     return LBM_OK;
 }
 
+// blocks of the cooperative rebuild (one per SM, at most REBUILD_THREADS so that one block scans
+// the per-block sums), or 0 when the device cannot run it (no cooperative launch)
+int rebuild_grid() {
+    static int grid = -1;
+    if (grid < 0) {
+        int dev = 0, coop = 0, sms = 0, per_sm = 0;
+        grid = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess && coop &&
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lbm::k_rebuild, lbm::REBUILD_THREADS, 0) ==
+                cudaSuccess &&
+            per_sm >= 1)
+            grid = std::min(sms, lbm::REBUILD_THREADS);
+        cudaGetLastError();
+    }
+    return grid;
+}
+
 // the samples at the pose of time `abs_t` (absolute step count); rebuilds every IB structure
 int rebuild(lbm_ctx *h, long long abs_t) {
     const long long S = h->S;
@@ -293,32 +450,47 @@ int rebuild(lbm_ctx *h, long long abs_t) {
     int rc = motion_ws(h, w);
     if (rc) return rc;
     const lbm::Lattice L = lbm::lattice(h);
-    const unsigned bs = lbm::blocks_of(S, 256);
+    const int coop_grid = rebuild_grid();
+    if (coop_grid <= 0) return fail(h, LBM_ECUDA, "the device cannot run the cooperative rebuild of a moving solid");
     Timed tm(h, LBM_KERNEL_MOTION);
-    lbm::k_pose<<<bs, 256, 0, h->stream>>>(S, h->X0, p, L, h->Xtmp, w.key, w.slot);
-    CK(cudaGetLastError());
-    CK(lbm::sort_pairs(w.key, w.slot, w.tkey, w.tslot, S, lbm::bits_for(h->N), w.sort, h->stream));
-    lbm::k_gather_samples<<<bs, 256, 0, h->stream>>>(S, w.slot, h->Xtmp, h->X0, h->area, h->sid, p, h->X, h->X0_alt,
-                                                     h->area_alt, h->sid_alt, h->ub);
-    CK(cudaGetLastError());
-    std::swap(h->X0, h->X0_alt);
-    std::swap(h->area, h->area_alt);
-    std::swap(h->sid, h->sid_alt);
-    CK(cudaMemsetAsync(h->tile_mask, 0, (size_t)4 * h->ntiles, h->stream));
-    lbm::k_mark_band<<<bs, 256, 0, h->stream>>>(S, h->X, L, h->tile_mask);
-    lbm::k_popc<<<lbm::blocks_of(h->ntiles, 256), 256, 0, h->stream>>>(h->ntiles, h->tile_mask, h->tile_off);
-    CK(cudaGetLastError());
-    CK(lbm::exclusive_scan(h->tile_off, h->tile_off, h->ntiles, w.sort, h->stream));
-    lbm::k_band_total<<<1, 1, 0, h->stream>>>(h->ntiles, h->tile_mask, h->tile_off, h->band_count_dev);
-    lbm::k_corner_band<<<bs, 256, 0, h->stream>>>(S, h->X, L, h->tile_mask, h->tile_off, h->corner_band, h->band_cell);
-    CK(cudaGetLastError());
-    CK(cudaMemsetAsync(h->ccount, 0, (size_t)4 * h->nband, h->stream));
-    lbm::k_run_start<<<bs, 256, 0, h->stream>>>(S, w.key, h->corner_band, h->cstart);
-    lbm::k_run_count<<<bs, 256, 0, h->stream>>>(S, w.key, h->corner_band, h->cstart, h->ccount);
-    lbm::k_base_nbr<<<lbm::blocks_of(h->nband, 256), 256, 0, h->stream>>>(h->nband, h->band_count_dev, h->band_cell, L,
-                                                                          h->tile_mask, h->tile_off, h->ccount,
-                                                                          h->base_nbr);
-    CK(cudaGetLastError());
+    {
+        lbm::RebuildArgs a{};
+        a.S = S;
+        a.ntiles = h->ntiles;
+        a.stride = h->nband;
+        a.bits = lbm::bits_for(h->N);
+        a.p = p;
+        a.L = L;
+        a.rel = h->X0;
+        a.area_in = h->area;
+        a.sid_in = h->sid;
+        a.Xtmp = h->Xtmp;
+        a.X = h->X;
+        a.rel_o = h->X0_alt;
+        a.area_o = h->area_alt;
+        a.ub = h->ub;
+        a.sid_o = h->sid_alt;
+        a.key = w.key;
+        a.slot = w.slot;
+        a.tkey = w.tkey;
+        a.tslot = w.tslot;
+        a.hist = static_cast<int *>(w.sort);
+        a.bsum = a.hist + 256 * lbm::REBUILD_SORT_BLOCKS;
+        a.mask = h->tile_mask;
+        a.off = h->tile_off;
+        a.count = h->band_count_dev;
+        a.corner_band = h->corner_band;
+        a.band_cell = h->band_cell;
+        a.cstart = h->cstart;
+        a.ccount = h->ccount;
+        a.base_nbr = h->base_nbr;
+        void *args[] = {&a};
+        CK(cudaLaunchCooperativeKernel((const void *)lbm::k_rebuild, dim3(coop_grid), dim3(lbm::REBUILD_THREADS), args,
+                                       0, h->stream));
+        std::swap(h->X0, h->X0_alt);
+        std::swap(h->area, h->area_alt);
+        std::swap(h->sid, h->sid_alt);
+    }
     h->posed_tau = abs_t;
     return LBM_OK;
 }
