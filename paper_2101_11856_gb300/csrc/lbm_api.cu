@@ -26,14 +26,38 @@ int fail(lbm_ctx *h, int code, const std::string &msg) {
     return code;
 }
 
+// the three immersed-boundary kernels of step P.t on stream st
+int ib_stage(lbm_ctx *h, const StepParams &P, cudaStream_t st) {
+    { Timed tm(h, LBM_KERNEL_BAND, 1, st); CK(launch_band_moments(h->storage, P, h->band_cell, h->band_rho, h->band_u, st)); }
+    { Timed tm(h, LBM_KERNEL_INTERP, 1, st); CK(launch_ib_interp(P, h->S, h->X, h->area, h->ub_zero ? nullptr : h->ub, h->band_rho, h->band_u, h->g, st)); }
+    { Timed tm(h, LBM_KERNEL_SPREAD, 1, st); CK(launch_ib_spread(h->S, h->nband, h->band_count_dev, h->X, h->g, h->base_nbr, h->cstart, h->ccount, h->bandF, st)); }
+    return LBM_OK;
+}
+
 int step_with(lbm_ctx *h, const StepParams &P) {
     const bool band = h->S > 0;
-    if (band) {
-        { Timed tm(h, LBM_KERNEL_BAND); CK(launch_band_moments(h->storage, P, h->band_cell, h->band_rho, h->band_u, h->stream)); }
-        { Timed tm(h, LBM_KERNEL_INTERP); CK(launch_ib_interp(P, h->S, h->X, h->area, h->ub_zero ? nullptr : h->ub, h->band_rho, h->band_u, h->g, h->stream)); }
-        { Timed tm(h, LBM_KERNEL_SPREAD); CK(launch_ib_spread(h->S, h->nband, h->band_count_dev, h->X, h->g, h->base_nbr, h->cstart, h->ccount, h->bandF, h->stream)); }
-    }
-    {
+    int rc;
+    if (band && h->ib_overlap && has_interior(P.g)) {
+        // No band node lies in the edge strips, so the strips neither read the band forces nor
+        // write a slot the band pass reads (AA: every slot is read and written by its own node):
+        // the IB stage runs on its own stream beside the strips, and the face rows and the main
+        // range wait for it.
+        if ((rc = ensure_ib_stream(h))) return rc;
+        CK(cudaEventRecord(h->ib_in, h->stream));
+        CK(cudaStreamWaitEvent(h->ibs, h->ib_in, 0));
+        if ((rc = ib_stage(h, P, h->ibs))) return rc;
+        CK(cudaEventRecord(h->ib_done, h->ibs));
+        {
+            Timed tm(h, LBM_KERNEL_BOUNDARY, step_launches(P, STEP_STRIPS));
+            CK(launch_step(h->storage, P, band, STEP_STRIPS, h->cfg.collision, h->stream));
+        }
+        CK(cudaStreamWaitEvent(h->stream, h->ib_done, 0));
+        if (step_launches(P, STEP_FACE_ROWS) > 0) {
+            Timed tm(h, LBM_KERNEL_BOUNDARY, step_launches(P, STEP_FACE_ROWS));
+            CK(launch_step(h->storage, P, band, STEP_FACE_ROWS, h->cfg.collision, h->stream));
+        }
+    } else {
+        if (band && (rc = ib_stage(h, P, h->stream))) return rc;
         Timed tm(h, LBM_KERNEL_BOUNDARY, step_launches(P, STEP_BOUNDARY));
         CK(launch_step(h->storage, P, band, STEP_BOUNDARY, h->cfg.collision, h->stream));
     }
@@ -188,6 +212,7 @@ int lbm_destroy(lbm_ctx *h) {
     if (!h) return LBM_OK;
     if (h->f) cudaStreamSynchronize(h->stream);
     free_async(h);
+    free_ib_stream(h);
     free_solid(h);
     free_tracers(h);
     dev_free(h->stage);
@@ -368,6 +393,11 @@ int lbm_set_solids(lbm_ctx *h, const float *samples, long long count, const floa
     h->S = (long long)S;
     h->nband = nb;
     h->ub_zero = std::all_of(vb.begin(), vb.end(), [](float v) { return v == 0.0f; });
+    // the IB stage may overlap the edge strips when no band node lies in them
+    h->ib_overlap = h->nx >= 2 * XEDGE + 1 && std::all_of(bcell.begin(), bcell.end(), [&](int c) {
+        const int x = c % h->nx;
+        return x >= XEDGE && x < h->nx - XEDGE;
+    });
     h->ntiles = ntiles;
     h->order = ord;
     if ((rc = upload(h, &h->X, Xs)) || (rc = upload(h, &h->area, As)) || (rc = upload(h, &h->ub, Us)) ||

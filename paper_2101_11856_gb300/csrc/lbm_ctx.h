@@ -100,6 +100,13 @@ struct lbm_ctx {
     float *stage_out = nullptr;
     cudaEvent_t out_ready = nullptr, out_free = nullptr;
 
+    // the immersed-boundary stage on its own stream, overlapping the edge strips (static solids
+    // with no band node in the strips: ib_overlap): ib_in = the step's inputs are ready, ib_done =
+    // band forces written; made on first use
+    bool ib_overlap = false;
+    cudaStream_t ibs = nullptr;
+    cudaEvent_t ib_in = nullptr, ib_done = nullptr;
+
     std::string err;
 };
 
@@ -151,21 +158,23 @@ inline cudaEvent_t pool_event(lbm_ctx *h) {
     return e;
 }
 
+// event pair around the launches of one kernel kind on stream st (the context's stream by default)
 struct Timed {
     lbm_ctx *h;
     int kind;
+    cudaStream_t st;
     cudaEvent_t a = nullptr;
-    Timed(lbm_ctx *h_, int k, int nlaunch = 1) : h(h_), kind(k) {
+    Timed(lbm_ctx *h_, int k, int nlaunch = 1, cudaStream_t s = nullptr) : h(h_), kind(k), st(s ? s : h_->stream) {
         h->launches[kind] += nlaunch;
         if (h->prof) {
             a = pool_event(h);
-            cudaEventRecord(a, h->stream);
+            cudaEventRecord(a, st);
         }
     }
     ~Timed() {
         if (h->prof) {
             cudaEvent_t b = pool_event(h);
-            cudaEventRecord(b, h->stream);
+            cudaEventRecord(b, st);
             h->recs.push_back({kind, a, b});
         }
     }
@@ -297,6 +306,38 @@ inline int ensure_async(lbm_ctx *h) {
     return LBM_OK;
 }
 
+// the stream and events of the overlapped IB stage, all or none (higher priority than the
+// context's stream: the main kernel waits for the stage)
+inline int ensure_ib_stream(lbm_ctx *h) {
+    if (h->ibs) return LBM_OK;
+    int lo = 0, hi = 0;
+    cudaStream_t s = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, hi);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&e0, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&e1, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        if (s) cudaStreamDestroy(s);
+        return fail(h, LBM_ECUDA, std::string("IB stream: ") + cudaGetErrorString(e));
+    }
+    h->ibs = s;
+    h->ib_in = e0;
+    h->ib_done = e1;
+    return LBM_OK;
+}
+
+inline void free_ib_stream(lbm_ctx *h) {
+    if (!h->ibs) return;
+    cudaStreamSynchronize(h->ibs);
+    cudaEventDestroy(h->ib_in);
+    cudaEventDestroy(h->ib_done);
+    cudaStreamDestroy(h->ibs);
+    h->ibs = nullptr;
+}
+
 inline void free_async(lbm_ctx *h) {
     if (!h->h2d) return;
     cudaStreamSynchronize(h->h2d);
@@ -350,6 +391,7 @@ inline void free_solid(lbm_ctx *h) {
     h->motion_ws_bytes = 0;
     h->moving = false;
     h->ub_zero = false;
+    h->ib_overlap = false;
     h->posed_tau = -1;
     h->S = h->nband = h->ntiles = 0;
     h->order.clear();

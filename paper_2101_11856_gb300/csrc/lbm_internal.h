@@ -7,7 +7,11 @@
 
 namespace lbm {
 
-enum { STEP_BOUNDARY = 0, STEP_INTERIOR = 1 };
+// parts of a step: STEP_BOUNDARY = the edge strips and (grids with a free-slip face) the face
+// rows; STEP_INTERIOR = the main range; STEP_STRIPS / STEP_FACE_ROWS = the two halves of
+// STEP_BOUNDARY (the strips of the rows the main kernel runs, and the face-row kernels), launched
+// apart when the immersed-boundary stage overlaps the strips
+enum { STEP_BOUNDARY = 0, STEP_INTERIOR = 1, STEP_STRIPS = 2, STEP_FACE_ROWS = 3 };
 // collision models, numbered as LBM_COLL_* of the C ABI
 enum CollisionModel { COLL_ACM = 0, COLL_BGK = 1, COLL_RAW = 2 };
 // The x range is split into two edge strips of XEDGE nodes per row, run by the general face

@@ -314,20 +314,27 @@ cudaError_t launch_step_fs(int storage, const StepParams &P, bool band, int part
 
 int step_launches(const StepParams &P, int part) {
     if (part == STEP_INTERIOR) return has_interior(P.g) ? 1 : 0;
-    return has_freeslip(P.g) && has_interior(P.g) ? 3 : 1;
+    const bool split = has_freeslip(P.g) && has_interior(P.g);
+    if (part == STEP_STRIPS) return 1;
+    if (part == STEP_FACE_ROWS) return split ? 2 : 0;
+    return split ? 3 : 1;
 }
 
 cudaError_t launch_step(int storage, const StepParams &P, bool band, int part, int collision, cudaStream_t st) {
-    if (!has_freeslip(P.g)) return launch_step_fs<false>(storage, P, band, part, collision, st);
+    if (!has_freeslip(P.g)) {
+        if (part == STEP_FACE_ROWS) return cudaSuccess;
+        return launch_step_fs<false>(storage, P, band, part == STEP_STRIPS ? STEP_BOUNDARY : part, collision, st);
+    }
     StepParams Pi = P;
     Pi.inner_rows = 1;
     if (part == STEP_INTERIOR)
         return has_interior(P.g) ? launch_step_fs<false>(storage, Pi, band, part, collision, st) : cudaSuccess;
-    if (has_interior(P.g)) {
-        const cudaError_t e = launch_step_fs<false>(storage, Pi, band, part, collision, st);
+    if (part != STEP_FACE_ROWS && has_interior(P.g)) {
+        const cudaError_t e = launch_step_fs<false>(storage, Pi, band, STEP_BOUNDARY, collision, st);
         if (e != cudaSuccess) return e;
     }
-    return launch_step_fs<true>(storage, P, band, part, collision, st);
+    if (part == STEP_STRIPS && has_interior(P.g)) return cudaSuccess;
+    return launch_step_fs<true>(storage, P, band, STEP_BOUNDARY, collision, st);
 }
 
 cudaError_t launch_init(int storage, const StepParams &P, const float *rho, const float *u, cudaStream_t st) {

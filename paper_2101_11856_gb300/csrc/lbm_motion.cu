@@ -571,6 +571,7 @@ int lbm_set_motion(lbm_ctx *h, const lbm_motion *m) {
     h->r_max = std::sqrt(r2);
     h->moving = true;
     h->ub_zero = false;             // the rigid-body velocities are written at every pose
+    h->ib_overlap = false;          // the band moves
     h->posed_tau0 = h->t;
     h->posed_tau = -1;
     if ((rc = rebuild(h, h->t))) {
