@@ -651,7 +651,7 @@ extern "C" int lbm_adjoint(lbm_ctx *h, int n, int K, const lbm_loss *loss, doubl
     auto point_slot = [&](long long j) {
         ib.point(k_rho + j * nb, k_u + j * 3 * nb, k_g + j * 3 * S, k_F + j * 3 * nb);
     };
-    const int fblk = force_sum_blocks();
+    const int fblk = force_sum_blocks(S);
     StepParams P0 = make_params(h, h->t);
     const long long mblk = macro_blocks(P0);
     if ((rc = ensure_partial(h, (size_t)std::max<long long>(MACRO_SUMS * mblk, 3 * fblk)))) return rc;

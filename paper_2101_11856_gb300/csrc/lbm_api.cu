@@ -491,7 +491,7 @@ int lbm_reductions(lbm_ctx *h, double *mass, double mom[3], double drag[3]) {
     if (rc) return rc;
     StepParams P = make_params(h, h->t);
     const long long nblk = macro_blocks(P);
-    const int fblk = force_sum_blocks();
+    const int fblk = force_sum_blocks(h->S);
     if ((rc = ensure_partial(h, (size_t)std::max<long long>(MACRO_SUMS * nblk, 3 * fblk)))) return rc;
     {
         Timed tm(h, LBM_KERNEL_OTHER);

@@ -60,7 +60,7 @@ cudaError_t launch_ib_interp(const StepParams &P, long long S, const float *X, c
 // count of band nodes (moving solids) or nullptr
 cudaError_t launch_ib_spread(long long S, long long nband, const int *count, const float *X, const float *g,
                              const int *base_nbr, const int *cstart, const int *ccount, float *bandF, cudaStream_t st);
-int force_sum_blocks();
+int force_sum_blocks(long long S);
 cudaError_t launch_sum_forces(long long S, const float *g, double *partial, cudaStream_t st);
 
 }  // namespace lbm

@@ -393,10 +393,15 @@ cudaError_t launch_ib_spread(long long S, long long nband, const int *count, con
     return cudaGetLastError();
 }
 
-int force_sum_blocks() { return 1024; }
+// blocks of the per-sample sums: at least 2048 samples per block (small solids take one block,
+// so the per-step drag of the adjoint's forward pass costs no idle blocks), at most 1024
+int force_sum_blocks(long long S) {
+    const long long b = (S + 2047) / 2048;
+    return (int)(b < 1 ? 1 : (b > 1024 ? 1024 : b));
+}
 
 cudaError_t launch_sum_forces(long long S, const float *g, double *partial, cudaStream_t st) {
-    k_sum_forces<<<force_sum_blocks(), 256, 0, st>>>(S, g, partial);
+    k_sum_forces<<<force_sum_blocks(S), 256, 0, st>>>(S, g, partial);
     return cudaGetLastError();
 }
 

@@ -613,7 +613,7 @@ int lbm_solid_torque(lbm_ctx *h, const double center[3], double torque[3]) {
         for (int a = 0; a < 3; ++a) torque[a] = 0.0;
         return LBM_OK;
     }
-    const int blocks = lbm::force_sum_blocks();
+    const int blocks = lbm::force_sum_blocks(h->S);
     int rc = ensure_partial(h, (size_t)3 * blocks);
     if (rc) return rc;
     {
