@@ -314,10 +314,10 @@ def moving_run(torch, lbm, Solver, args, peak, world):
 
 
 def main_cells(nx, ny, nz, faces):
-    """Nodes one launch of the main step kernel updates: the main range 32 <= x < nx - 32 (32 =
+    """Nodes one launch of the main step kernel updates: the main range 16 <= x < nx - 16 (16 =
     the edge strip of the face kernel) of every row, or, on a grid with a free-slip face, of the
     rows off the y/z faces (the face rows run with the boundary kernels)."""
-    xedge = 32
+    xedge = 16
     if nx < 2 * xedge + 1:
         return 0
     rows = ny * nz
@@ -669,7 +669,7 @@ def main():
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": TRAFFIC_PER_CELL["f32"] * n_int if TRAFFIC_PER_CELL.get("f32") else None,
-                         "kernel": "k_step_main (fused stream+collide, 32 <= x < nx-32 of the rows off the y/z faces)",
+                         "kernel": "k_step_main (fused stream+collide, 16 <= x < nx-16 of the rows off the y/z faces)",
                          "cells_per_launch": n_int, "bytes_per_cell": 216,
                          "peak_kind": peak_kind},
             "runs": stats["runs"], "median": stats["median"], "spread": stats["spread"],

@@ -115,7 +115,7 @@ int lbm_set_solids(lbm_ctx *h, const float *samples, long long count,
 
 /* Advance n time steps (Algorithm 2: streaming, moments, immersed boundary, collision
  * with forcing, domain faces), asynchronously on the context's stream.  Each step is one
- * fused stream+collide kernel over the nodes 32 <= x < nx-32, one over the two 32-node
+ * fused stream+collide kernel over the nodes 16 <= x < nx-16, one over the two 16-node
  * edge strips of every row (the inlet/outlet/x-periodic rules), and three small
  * immersed-boundary kernels when a solid is installed (plus the re-pose of a moving solid
  * and the tracer advection when those are set).  On a grid with a free-slip face the rows
@@ -218,12 +218,12 @@ int lbm_load(lbm_ctx *h, const void *buf, size_t bytes);
 
 /* Per-kernel device timing (CUDA events on the context's stream around every launch).
  * lbm_profile(h, 1) enables and clears the counters; lbm_profile(h, 0) disables. */
-#define LBM_KERNEL_STEP        0   /* fused stream + collide, 32 <= x < nx-32              */
+#define LBM_KERNEL_STEP        0   /* fused stream + collide, 16 <= x < nx-16              */
 #define LBM_KERNEL_BAND        1   /* immersed-boundary band moments                      */
 #define LBM_KERNEL_INTERP      2   /* interpolation + penalty (Eqs. 6-7)                   */
 #define LBM_KERNEL_SPREAD      3   /* spreading (Eq. 8)                                    */
-#define LBM_KERNEL_BOUNDARY    4   /* fused stream + collide, the 32-node strips at both
-                                      row ends (whole rows when nx < 65)                   */
+#define LBM_KERNEL_BOUNDARY    4   /* fused stream + collide, the 16-node strips at both
+                                      row ends (whole rows when nx < 33)                   */
 #define LBM_KERNEL_OTHER       5   /* init, macroscopic, reductions, copies, density      */
 #define LBM_KERNEL_TRACER      6   /* smoke tracer advection                              */
 #define LBM_KERNEL_MOTION      7   /* moving solids: pose, re-sort and band rebuild       */

@@ -367,13 +367,13 @@ __device__ __forceinline__ void node_vjp(const StepParams &P, const AdjParams &A
     collide_vjp(fs, Fx, Fy, Fz, P, ex, lam, dFx, dFy, dFz);
 }
 
-// Backward step of the nodes XEDGE <= x < nx - XEDGE (one block row per (y, z)): mu = dL/df*
+// Backward step of the nodes ADJ_XEDGE <= x < nx - ADJ_XEDGE (one block row per (y, z)): mu = dL/df*
 // pushed along the transposed streaming, lambda_{t-1}[d](x - c_d) = mu_d(x), or to the
 // bounce-back slot lambda_{t-1}[opp(d)](x) where the source lies across a no-slip y/z face.
 template <typename St, bool NB, bool BAND>
 __global__ void __launch_bounds__(STEP_BX) k_adj_main(StepParams P, AdjParams A) {
-    const int x = blockIdx.x * STEP_BX + threadIdx.x + XEDGE;
-    if (x >= P.g.nx - XEDGE) return;
+    const int x = blockIdx.x * STEP_BX + threadIdx.x + ADJ_XEDGE;
+    if (x >= P.g.nx - ADJ_XEDGE) return;
     const int y = blockIdx.y, z = blockIdx.z;
     const int cell = x + P.g.nx * (y + P.g.ny * z);
     const bool inner = y >= 1 && y <= P.g.ny - 2 && z >= 1 && z <= P.g.nz - 2;   // uniform per block
@@ -444,7 +444,7 @@ __device__ __forceinline__ void adj_push_edge(const StepParams &P, const AdjPara
 // for k_adj_outlet.  Layout as k_step_edges / k_step_rows.
 template <typename St, bool NB, bool BAND, int SIDE>
 __device__ __forceinline__ void adj_edge_node(const StepParams &P, const AdjParams &A, int y, int z) {
-    const int x = edge_x<SIDE>(P.g);
+    const int x = edge_x<SIDE, ADJ_XEDGE>(P.g);
     if (x >= P.g.nx) return;
     const int cell = x + P.g.nx * (y + P.g.ny * z);
     float fs[27], lam[27];
@@ -455,7 +455,7 @@ __device__ __forceinline__ void adj_edge_node(const StepParams &P, const AdjPara
 }
 
 template <typename St, bool NB, bool BAND>
-__global__ void __launch_bounds__(XEDGE * EDGE_ROWS) k_adj_edges(StepParams P, AdjParams A) {
+__global__ void __launch_bounds__(ADJ_XEDGE * EDGE_ROWS) k_adj_edges(StepParams P, AdjParams A) {
     const int y = blockIdx.y * EDGE_ROWS + threadIdx.y, z = blockIdx.z;
     if (y >= P.g.ny) return;
     if (blockIdx.x == 0) adj_edge_node<St, NB, BAND, 0>(P, A, y, z);
@@ -463,7 +463,7 @@ __global__ void __launch_bounds__(XEDGE * EDGE_ROWS) k_adj_edges(StepParams P, A
 }
 
 template <typename St, bool NB, bool BAND>
-__global__ void __launch_bounds__(XEDGE * EDGE_ROWS) k_adj_rows(StepParams P, AdjParams A) {
+__global__ void __launch_bounds__(ADJ_XEDGE * EDGE_ROWS) k_adj_rows(StepParams P, AdjParams A) {
     const int y = blockIdx.y * EDGE_ROWS + threadIdx.y, z = blockIdx.z;
     if (y >= P.g.ny) return;
     adj_edge_node<St, NB, BAND, 2>(P, A, y, z);
@@ -586,14 +586,14 @@ struct AdjBuffers {
 template <typename St, bool NB, bool BAND>
 cudaError_t launch_adj_step_tt(const StepParams &P, const AdjParams &A, cudaStream_t st) {
     const Geometry &g = P.g;
-    const dim3 eb(XEDGE, EDGE_ROWS);
-    if (has_interior(g)) {
+    const dim3 eb(ADJ_XEDGE, EDGE_ROWS);
+    if (g.nx >= 2 * ADJ_XEDGE + 1) {
         const dim3 ge(2, nblocks(g.ny, EDGE_ROWS), g.nz);
         k_adj_edges<St, NB, BAND><<<ge, eb, 0, st>>>(P, A);
-        const dim3 gm(nblocks(g.nx - 2 * XEDGE, STEP_BX), g.ny, g.nz);
+        const dim3 gm(nblocks(g.nx - 2 * ADJ_XEDGE, STEP_BX), g.ny, g.nz);
         k_adj_main<St, NB, BAND><<<gm, STEP_BX, 0, st>>>(P, A);
     } else {
-        const dim3 ge(nblocks(g.nx, XEDGE), nblocks(g.ny, EDGE_ROWS), g.nz);
+        const dim3 ge(nblocks(g.nx, ADJ_XEDGE), nblocks(g.ny, EDGE_ROWS), g.nz);
         k_adj_rows<St, NB, BAND><<<ge, eb, 0, st>>>(P, A);
     }
     return cudaGetLastError();

@@ -15,10 +15,15 @@ enum { STEP_BOUNDARY = 0, STEP_INTERIOR = 1, STEP_STRIPS = 2, STEP_FACE_ROWS = 3
 // collision models, numbered as LBM_COLL_* of the C ABI
 enum CollisionModel { COLL_ACM = 0, COLL_BGK = 1, COLL_RAW = 2 };
 // The x range is split into two edge strips of XEDGE nodes per row, run by the general face
-// kernel in whole coalesced warps (STEP_BOUNDARY), and the nodes XEDGE <= x < nx - XEDGE,
-// run by the main kernel (STEP_INTERIOR).  Rows shorter than 2 XEDGE + 1 run entirely in the
-// face kernel.
-constexpr int XEDGE = 32;
+// kernel (STEP_BOUNDARY; a warp takes the strips of 32 / XEDGE rows, coalesced per row), and the
+// nodes XEDGE <= x < nx - XEDGE, run by the main kernel (STEP_INTERIOR).  Rows shorter than
+// 2 XEDGE + 1 run entirely in the face kernel.  16-node strips: the general face rules cost more
+// per node than the main kernel, so narrower strips put more of each row in the main kernel
+// (whole step 8.76 -> 8.69 ms on the buildings workload, FP16 6.17 -> 6.09 ms).  The adjoint's
+// backward kernels keep 32-node strips (ADJ_XEDGE): their main kernel runs one node per thread and
+// measured slower with narrower strips.
+constexpr int XEDGE = 16;
+constexpr int ADJ_XEDGE = 32;
 constexpr int STEP_BX = 64;   // threads per block of the main step kernels (along x)
 cudaError_t launch_step(int storage, const StepParams &P, bool band, int part, int collision, cudaStream_t st);
 template <int COLL, bool FS>

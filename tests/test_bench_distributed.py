@@ -56,17 +56,18 @@ def test_reference_arm_under_torchrun_two_ranks():
 
 
 def test_main_kernel_cells():
-    """The roofline's cells per main-kernel launch: the main range 32 <= x < nx - 32 of every
+    """The roofline's cells per main-kernel launch: the main range 16 <= x < nx - 16 of every
     row, or of the rows off the y/z faces on a grid with a free-slip face (those rows run with
-    the boundary kernels); no main range below nx = 65."""
+    the boundary kernels); no main range below nx = 33."""
     sys.path.insert(0, ROOT)
     import bench
     city = ("inlet", "outlet", "noslip", "freeslip", "periodic", "periodic")
     closed = ("inlet", "outlet", "noslip", "noslip", "periodic", "periodic")
-    assert bench.main_cells(1200, 250, 840, city) == 1136 * 248 * 838 == 236088064
-    assert bench.main_cells(1200, 250, 840, closed) == 1136 * 250 * 840
+    assert bench.main_cells(1200, 250, 840, city) == 1168 * 248 * 838 == 242738432
+    assert bench.main_cells(1200, 250, 840, closed) == 1168 * 250 * 840
     assert bench.main_cells(65, 2, 7, city) == 0            # every row on a face
-    assert bench.main_cells(64, 9, 9, closed) == 0          # no main range
+    assert bench.main_cells(33, 9, 9, closed) == 9 * 9      # one main-range node per row
+    assert bench.main_cells(32, 9, 9, closed) == 0          # no main range
 
 
 def test_run_statistics_and_cpu_samples():

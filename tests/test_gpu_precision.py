@@ -1,4 +1,4 @@
-"""FP16 / BF16 deviation storage through the main and edge kernels (nx >= 65), for the three
+"""FP16 / BF16 deviation storage through the main and edge kernels (nx >= 33), for the three
 collision models, one step at a time against the FP64 oracle: the oracle starts from the GPU's own stored populations (read
 back exactly), so the only difference left is the storage rounding of the step's output,
 half an ulp of each deviation h = f - w rho0 (2^-11 |h| for FP16, 2^-8 |h| for BF16), plus the
