@@ -9,7 +9,7 @@
 // transposes of spreading and interpolation, and the trilinear weights' derivatives for the
 // positions), and pushes mu = dL/df* back along the streaming (its transpose):
 // lambda_{t-1}[i](x - c_i) = mu_i(x), bounce-back slots get mu of the reflected direction,
-// the outlet ghost's duplicate goes through a small fix-up.  States f_{t-1} come from
+// the slots the outlet ghost copied take its second use on top.  States f_{t-1} come from
 // segment recomputation between checkpoints taken every K steps.
 #include <algorithm>
 #include <cmath>
@@ -45,12 +45,7 @@ __device__ __forceinline__ void shiftT3(float &a, float &b, float &c, float u) {
     a = fmaf(u * u, l2, fmaf(-u, l1, a));
     b = fmaf(-2.0f * u, l2, l1);
 }
-// inverse shift Sh(u)^-1 = [[1,0,0],[u,1,0],[u^2,2u,1]] and its transpose
-__device__ __forceinline__ void invshift3(float &m0, float &m1, float &m2, float u) {
-    const float r1 = fmaf(u, m0, m1);
-    m2 = fmaf(u, m1 + r1, m2);
-    m1 = r1;
-}
+// transpose of the inverse shift Sh(u)^-1 = [[1,0,0],[u,1,0],[u^2,2u,1]]
 __device__ __forceinline__ void invshiftT3(float &a, float &b, float &c, float u) {
     a = fmaf(u * u, c, fmaf(u, b, a));
     b = fmaf(2.0f * u, c, b);
@@ -98,55 +93,57 @@ __device__ __forceinline__ void collide_vjp(const float (&fs)[27], float Fx, flo
     sweep<1>(k, [ux](float &a, float &b, float &c) { shift3(a, b, c, ux); });
     sweep<3>(k, [uy](float &a, float &b, float &c) { shift3(a, b, c, uy); });
     sweep<9>(k, [uz](float &a, float &b, float &c) { shift3(a, b, c, uz); });
-    // k = central moments kappa; rp = post-collision central moments, then raw moments
     const float wb = 1.0f - P.rb, w4 = 1.0f - P.r4, w6 = 1.0f - P.r6;
     const float third = 1.0f / 3.0f, ninth = 1.0f / 9.0f;
-    float rp[27];
-#pragma unroll
-    for (int d = 0; d < 27; ++d) rp[d] = k[d];
-    rp[K(1, 0, 0)] += Fx;
-    rp[K(0, 1, 0)] += Fy;
-    rp[K(0, 0, 1)] += Fz;
-    rp[K(1, 1, 0)] *= P.rs;
-    rp[K(1, 0, 1)] *= P.rs;
-    rp[K(0, 1, 1)] *= P.rs;
-    {
-        const float a = k[K(2, 0, 0)] - rho * third, b = k[K(0, 2, 0)] - rho * third, c = k[K(0, 0, 2)] - rho * third;
-        const float s3 = (a + b + c) * third;
-        rp[K(2, 0, 0)] = rho * third + P.rb * s3 + P.rs * (a - s3);
-        rp[K(0, 2, 0)] = rho * third + P.rb * s3 + P.rs * (b - s3);
-        rp[K(0, 0, 2)] = rho * third + P.rb * s3 + P.rs * (c - s3);
-    }
-    rp[K(2, 1, 0)] = fmaf(P.r3, k[K(2, 1, 0)], P.q3 * third * Fy);
-    rp[K(2, 0, 1)] = fmaf(P.r3, k[K(2, 0, 1)], P.q3 * third * Fz);
-    rp[K(1, 2, 0)] = fmaf(P.r3, k[K(1, 2, 0)], P.q3 * third * Fx);
-    rp[K(0, 2, 1)] = fmaf(P.r3, k[K(0, 2, 1)], P.q3 * third * Fz);
-    rp[K(1, 0, 2)] = fmaf(P.r3, k[K(1, 0, 2)], P.q3 * third * Fx);
-    rp[K(0, 1, 2)] = fmaf(P.r3, k[K(0, 1, 2)], P.q3 * third * Fy);
-    rp[K(1, 1, 1)] = P.r3 * k[K(1, 1, 1)];
-    rp[K(2, 2, 0)] = fmaf(P.r4, k[K(2, 2, 0)], w4 * ninth * rho);
-    rp[K(2, 0, 2)] = fmaf(P.r4, k[K(2, 0, 2)], w4 * ninth * rho);
-    rp[K(0, 2, 2)] = fmaf(P.r4, k[K(0, 2, 2)], w4 * ninth * rho);
-    rp[K(2, 1, 1)] = P.r4 * k[K(2, 1, 1)];
-    rp[K(1, 2, 1)] = P.r4 * k[K(1, 2, 1)];
-    rp[K(1, 1, 2)] = P.r4 * k[K(1, 1, 2)];
-    rp[K(2, 2, 1)] = fmaf(P.r5, k[K(2, 2, 1)], P.q5 * ninth * Fz);
-    rp[K(2, 1, 2)] = fmaf(P.r5, k[K(2, 1, 2)], P.q5 * ninth * Fy);
-    rp[K(1, 2, 2)] = fmaf(P.r5, k[K(1, 2, 2)], P.q5 * ninth * Fx);
-    rp[K(2, 2, 2)] = fmaf(P.r6, k[K(2, 2, 2)], w6 * (1.0f / 27.0f) * rho);
-    sweep<1>(rp, [ux](float &a, float &b, float &c) { invshift3(a, b, c, ux); });
-    sweep<3>(rp, [uy](float &a, float &b, float &c) { invshift3(a, b, c, uy); });
-    sweep<9>(rp, [uz](float &a, float &b, float &c) { invshift3(a, b, c, uz); });
 
-    // backward: populations -> post-collision raw moments
+    // backward: populations -> post-collision raw moments -> post-collision central moments
     sweep<1>(lam, [](float &a, float &b, float &c) { invrawT3(a, b, c); });
     sweep<3>(lam, [](float &a, float &b, float &c) { invrawT3(a, b, c); });
     sweep<9>(lam, [](float &a, float &b, float &c) { invrawT3(a, b, c); });
-    // u through the inverse shift: d/du_a (Sh^-1 kappa') = A_a r'
-    float dux = gen_contract<1>(lam, rp), duy = gen_contract<3>(lam, rp), duz = gen_contract<9>(lam, rp);
     sweep<1>(lam, [ux](float &a, float &b, float &c) { invshiftT3(a, b, c, ux); });
     sweep<3>(lam, [uy](float &a, float &b, float &c) { invshiftT3(a, b, c, uy); });
     sweep<9>(lam, [uz](float &a, float &b, float &c) { invshiftT3(a, b, c, uz); });
+    // u through the inverse shift: d/du_a (Sh^-1 kappa') = A_a Sh^-1 kappa' = Sh^-1 A_a kappa'
+    // (A_a generates the shifts and commutes with them), so the contraction pairs dL/dkappa'
+    // with the post-collision central moments kappa', formed here from kappa (k)
+    float dux, duy, duz;
+    {
+        float kp[27];
+#pragma unroll
+        for (int d = 0; d < 27; ++d) kp[d] = k[d];
+        kp[K(1, 0, 0)] += Fx;
+        kp[K(0, 1, 0)] += Fy;
+        kp[K(0, 0, 1)] += Fz;
+        kp[K(1, 1, 0)] *= P.rs;
+        kp[K(1, 0, 1)] *= P.rs;
+        kp[K(0, 1, 1)] *= P.rs;
+        {
+            const float a = k[K(2, 0, 0)] - rho * third, b = k[K(0, 2, 0)] - rho * third, c = k[K(0, 0, 2)] - rho * third;
+            const float s3 = (a + b + c) * third;
+            kp[K(2, 0, 0)] = rho * third + P.rb * s3 + P.rs * (a - s3);
+            kp[K(0, 2, 0)] = rho * third + P.rb * s3 + P.rs * (b - s3);
+            kp[K(0, 0, 2)] = rho * third + P.rb * s3 + P.rs * (c - s3);
+        }
+        kp[K(2, 1, 0)] = fmaf(P.r3, k[K(2, 1, 0)], P.q3 * third * Fy);
+        kp[K(2, 0, 1)] = fmaf(P.r3, k[K(2, 0, 1)], P.q3 * third * Fz);
+        kp[K(1, 2, 0)] = fmaf(P.r3, k[K(1, 2, 0)], P.q3 * third * Fx);
+        kp[K(0, 2, 1)] = fmaf(P.r3, k[K(0, 2, 1)], P.q3 * third * Fz);
+        kp[K(1, 0, 2)] = fmaf(P.r3, k[K(1, 0, 2)], P.q3 * third * Fx);
+        kp[K(0, 1, 2)] = fmaf(P.r3, k[K(0, 1, 2)], P.q3 * third * Fy);
+        kp[K(1, 1, 1)] = P.r3 * k[K(1, 1, 1)];
+        kp[K(2, 2, 0)] = fmaf(P.r4, k[K(2, 2, 0)], w4 * ninth * rho);
+        kp[K(2, 0, 2)] = fmaf(P.r4, k[K(2, 0, 2)], w4 * ninth * rho);
+        kp[K(0, 2, 2)] = fmaf(P.r4, k[K(0, 2, 2)], w4 * ninth * rho);
+        kp[K(2, 1, 1)] = P.r4 * k[K(2, 1, 1)];
+        kp[K(1, 2, 1)] = P.r4 * k[K(1, 2, 1)];
+        kp[K(1, 1, 2)] = P.r4 * k[K(1, 1, 2)];
+        kp[K(2, 2, 1)] = fmaf(P.r5, k[K(2, 2, 1)], P.q5 * ninth * Fz);
+        kp[K(2, 1, 2)] = fmaf(P.r5, k[K(2, 1, 2)], P.q5 * ninth * Fy);
+        kp[K(1, 2, 2)] = fmaf(P.r5, k[K(1, 2, 2)], P.q5 * ninth * Fx);
+        dux = gen_contract<1>(lam, kp);
+        duy = gen_contract<3>(lam, kp);
+        duz = gen_contract<9>(lam, kp);
+    }
     // relaxation: lam = dL/d kappa'
     float drho = 0.0f;
     dFx += lam[K(1, 0, 0)] + P.q3 * third * (lam[K(1, 2, 0)] + lam[K(1, 0, 2)]) + P.q5 * ninth * lam[K(1, 2, 2)];
@@ -224,7 +221,6 @@ __device__ __forceinline__ bool band_index(const StepParams &P, int cell, long l
 struct AdjParams {
     const float *lam_cur;        // [27][N] dL/df_t (canonical, library direction order)
     float *lam_prev;             // [27][N] dL/df_{t-1}
-    float *blam;                 // [9][nyz] outlet-ghost duplicates
     double *s_inlet;             // [nyz] accumulated sum_i mu_i 6 w_i rho0 c_ix per inlet node
     const float *adj_band;       // [4][nband] dL/d rho*, dL/d j of the band nodes
     float *dF_band;              // [3][nband] dL/dF of the band nodes
@@ -367,13 +363,16 @@ __device__ __forceinline__ void node_vjp(const StepParams &P, const AdjParams &A
     collide_vjp(fs, Fx, Fy, Fz, P, ex, lam, dFx, dFy, dFz);
 }
 
-// Backward step of the nodes ADJ_XEDGE <= x < nx - ADJ_XEDGE (one block row per (y, z)): mu = dL/df*
-// pushed along the transposed streaming, lambda_{t-1}[d](x - c_d) = mu_d(x), or to the
-// bounce-back slot lambda_{t-1}[opp(d)](x) where the source lies across a no-slip y/z face.
+// Backward step of the nodes 1 <= x <= nx - 2 (one block row per (y, z); the lanes of x = 0 and
+// x >= nx - 1 idle): mu = dL/df* pushed along the transposed streaming,
+// lambda_{t-1}[d](x - c_d) = mu_d(x), or to the bounce-back slot lambda_{t-1}[opp(d)](x) where
+// the source lies across a no-slip y/z face.  No lane crosses an x face, so every lane of a
+// warp runs the same addressing.  12 resident blocks per SM (80 registers, a few spilled values)
+// measured faster than the 96 registers the compiler picks alone (21 warps per SM).
 template <typename St, bool NB, bool BAND>
-__global__ void __launch_bounds__(STEP_BX) k_adj_main(StepParams P, AdjParams A) {
-    const int x = blockIdx.x * STEP_BX + threadIdx.x + ADJ_XEDGE;
-    if (x >= P.g.nx - ADJ_XEDGE) return;
+__global__ void __launch_bounds__(STEP_BX, 12) k_adj_main(StepParams P, AdjParams A) {
+    const int x = blockIdx.x * STEP_BX + threadIdx.x;
+    if (x < 1 || x > P.g.nx - 2) return;
     const int y = blockIdx.y, z = blockIdx.z;
     const int cell = x + P.g.nx * (y + P.g.ny * z);
     const bool inner = y >= 1 && y <= P.g.ny - 2 && z >= 1 && z <= P.g.nz - 2;   // uniform per block
@@ -398,99 +397,45 @@ __global__ void __launch_bounds__(STEP_BX) k_adj_main(StepParams P, AdjParams A)
     }
 }
 
-// push of mu from an edge-strip node: interior rows use constant row offsets, face rows the
-// wrapped / bounced rows.  Every lane pushes in the same instruction stream: a direction whose
-// source lies across the x face of the lane's side is redirected by address selection (x wrap,
-// the node's own slot for no-slip and inlet, no write for the outlet ghost, whose use goes to
-// the duplicate buffer for k_adj_outlet); the face type of a side is uniform.
-template <bool INNER, int SIDE>
-__device__ __forceinline__ void adj_push_edge(const StepParams &P, const AdjParams &A, int x, int y, int z, int cell,
-                                              const float (&lam)[27]) {
+// Backward step of the x-face nodes x = 0 (blockIdx.y = 0) and x = nx - 1 (blockIdx.y = 1), one
+// thread per node, launched after k_adj_main (nx >= 3).  Each mu_d goes back to the slot its
+// streamed value came from, by the pull's own per-direction rules: the wrapped neighbour
+// (periodic x), the node's reflected slot (no-slip; the inlet also feeds the inflow-coefficient
+// gradient), or, through the outlet ghost, the previous post-collision value of
+// (nx-1, y - c_y, z - c_z) that the ghost copied.  That slot (c_x = -1) already holds the push of
+// (nx-2, y, z) from k_adj_main and takes the ghost's use on top; no other thread writes it.
+// Slots of populations that left through the outlet have no use and are zeroed.
+template <typename St, bool NB, bool BAND>
+__global__ void __launch_bounds__(128) k_adj_xface(StepParams P, AdjParams A) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P.g.nyz) return;
+    const int z = i / P.g.ny, y = i - z * P.g.ny;
+    const int x = blockIdx.y ? P.g.nx - 1 : 0;
+    const int cell = x + P.g.nx * (y + P.g.ny * z);
+    float fs[27], lam[27];
+    load_general<St, NB>(P, x, y, z, cell, fs);
+    node_vjp<BAND>(P, A, x, cell, fs, lam);
     const long long N = P.g.ncell;
-    int off[9], mir[9];
-    bool bb[9];
-    row_offsets<-1, INNER, false>(P.g, y, z, off, bb, mir);   // free-slip faces are rejected by lbm_adjoint
-    const bool xlo = SIDE != 1 && x == 0, xhi = SIDE != 0 && x == P.g.nx - 1;
-    const int flo = P.g.face[0], fhi = P.g.face[1];
-    const bool outlet_node = xhi && fhi == FACE_OUTLET;
+    if (blockIdx.y && P.g.face[1] == FACE_OUTLET) {
+#pragma unroll
+        for (int d = 0; d < 27; ++d)
+            if (cx(d) == 1 && neighbour<+1>(P.g, d, x, y, z).kind == CROSS_OUTLET) A.lam_prev[d * N + cell] = 0.0f;
+    }
     float sth = 0.0f;   // this node's inflow sensitivity (accumulated over steps in FP64)
 #pragma unroll
     for (int d = 0; d < 27; ++d) {
-        const int j = d / 3;
+        const Nbr n = neighbour<-1>(P.g, d, x, y, z);
         const float mu = lam[d];
-        if (bb[j]) {                         // uniform per warp: the row crosses a no-slip y/z face
+        if (n.kind == 0) {
+            A.lam_prev[d * N + n.idx] = mu;
+        } else if (n.kind & (CROSS_NOSLIP | CROSS_INLET)) {
             A.lam_prev[opp(d) * N + cell] = mu;
-            if (outlet_node && cx(d) == -1) A.blam[(long long)j * P.g.nyz + y + P.g.ny * z] = 0.0f;
-            continue;
-        }
-        bool xc = false;
-        int ft = FACE_PERIODIC;
-        if (cx(d) == 1) { xc = xlo; ft = flo; }
-        if (cx(d) == -1) { xc = xhi; ft = fhi; }
-        const bool own = xc && (ft == FACE_NOSLIP || ft == FACE_INLET);
-        const bool ghost = xc && ft == FACE_OUTLET;
-        const long long idx = own ? (long long)opp(d) * N + cell
-                                  : (long long)d * N + cell + off[j] + (xc ? cx(d) * (P.g.nx - 1) : -cx(d));
-        if (!ghost) A.lam_prev[idx] = mu;
-        if (cx(d) == 1 && xc && ft == FACE_INLET) sth = fmaf(mu, 6.0f * wgt(d) * P.rho0, sth);
-        if (outlet_node && cx(d) == -1) A.blam[(long long)j * P.g.nyz + y + P.g.ny * z] = ghost ? mu : 0.0f;
-    }
-    if (xlo && flo == FACE_INLET) A.s_inlet[y + P.g.ny * z] += (double)sth;
-}
-
-// Backward step of the edge strips (one warp per strip and row, EDGE_ROWS rows per block; the
-// x-face rules per lane): periodic x wraps, no-slip and inlet faces bounce back (the inlet also
-// feeds the inflow-coefficient gradient), the outlet ghost's use goes to the duplicate buffer
-// for k_adj_outlet.  Layout as k_step_edges / k_step_rows.
-template <typename St, bool NB, bool BAND, int SIDE>
-__device__ __forceinline__ void adj_edge_node(const StepParams &P, const AdjParams &A, int y, int z) {
-    const int x = edge_x<SIDE, ADJ_XEDGE>(P.g);
-    if (x >= P.g.nx) return;
-    const int cell = x + P.g.nx * (y + P.g.ny * z);
-    float fs[27], lam[27];
-    load_edge<St, NB, SIDE, false>(P, x, y, z, cell, fs);
-    node_vjp<BAND>(P, A, x, cell, fs, lam);
-    if (y >= 1 && y <= P.g.ny - 2 && z >= 1 && z <= P.g.nz - 2) adj_push_edge<true, SIDE>(P, A, x, y, z, cell, lam);
-    else adj_push_edge<false, SIDE>(P, A, x, y, z, cell, lam);
-}
-
-template <typename St, bool NB, bool BAND>
-__global__ void __launch_bounds__(ADJ_XEDGE * EDGE_ROWS) k_adj_edges(StepParams P, AdjParams A) {
-    const int y = blockIdx.y * EDGE_ROWS + threadIdx.y, z = blockIdx.z;
-    if (y >= P.g.ny) return;
-    if (blockIdx.x == 0) adj_edge_node<St, NB, BAND, 0>(P, A, y, z);
-    else adj_edge_node<St, NB, BAND, 1>(P, A, y, z);
-}
-
-template <typename St, bool NB, bool BAND>
-__global__ void __launch_bounds__(ADJ_XEDGE * EDGE_ROWS) k_adj_rows(StepParams P, AdjParams A) {
-    const int y = blockIdx.y * EDGE_ROWS + threadIdx.y, z = blockIdx.z;
-    if (y >= P.g.ny) return;
-    adj_edge_node<St, NB, BAND, 2>(P, A, y, z);
-}
-
-// outlet plane: zero the slots of the populations that left through the outlet (no use in
-// f*) and add the ghost duplicates dL/df_{t-1, d}(nx-1, y, z) += mu_d(nx-1, y + c_y, z + c_z)
-__global__ void __launch_bounds__(128) k_adj_outlet(StepParams P, AdjParams A) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= P.g.nyz) return;
-    const int z = i / P.g.ny, y = i - z * P.g.ny, x = P.g.nx - 1;
-    const int cell = x + P.g.nx * (y + P.g.ny * z);
-    const long long N = P.g.ncell;
-#pragma unroll
-    for (int d = 0; d < 27; ++d) {
-        if (cx(d) == 1) {
-            const Nbr n = neighbour<+1>(P.g, d, x, y, z);
-            if (n.kind == CROSS_OUTLET) A.lam_prev[d * N + cell] = 0.0f;
-        } else if (cx(d) == -1) {
-            // the node (nx-1, y + c_y, z + c_z) pulled this slot through the ghost
-            int yy = y + cy(d), zz = z + cz(d);
-            bool ok = true;
-            if (yy < 0 || yy >= P.g.ny) { if (P.g.periodic[1]) yy = (yy + P.g.ny) % P.g.ny; else ok = false; }
-            if (zz < 0 || zz >= P.g.nz) { if (P.g.periodic[2]) zz = (zz + P.g.nz) % P.g.nz; else ok = false; }
-            if (ok) A.lam_prev[d * N + cell] += A.blam[(long long)(d / 3) * P.g.nyz + yy + P.g.ny * zz];
+            if (!(n.kind & CROSS_NOSLIP)) sth = fmaf(mu, 6.0f * wgt(d) * P.rho0, sth);   // inlet: c_x = +1
+        } else {
+            A.lam_prev[d * N + (P.g.nx - 1) + P.g.nx * (n.y + P.g.ny * n.z)] += mu;   // outlet ghost
         }
     }
+    if (!blockIdx.y && P.g.face[0] == FACE_INLET) A.s_inlet[y + P.g.ny * z] += (double)sth;
 }
 
 __global__ void k_finalize_add(const double *__restrict__ partial, long long n, int count, double *__restrict__ out) {
@@ -560,11 +505,15 @@ int adj_forward_step(lbm_ctx *h, void *src, void *dst) {
     return LBM_OK;
 }
 
+// the backward pass runs on a stream of the highest priority beside the segment recompute
+constexpr bool kBackwardPriority = true;
+
 struct AdjBuffers {
     lbm_ctx *h;
     size_t next = 0;
     explicit AdjBuffers(lbm_ctx *h_) : h(h_) {}
-    template <typename T> int get(lbm_ctx *, T **p, size_t n) {
+    // quiet: a failed allocation returns LBM_ENOMEM without recording an error message
+    template <typename T> int get(lbm_ctx *, T **p, size_t n, bool quiet = false) {
         const size_t bytes = n * sizeof(T);
         if (next == h->adj_ws.size()) h->adj_ws.push_back({nullptr, 0});
         auto &slot = h->adj_ws[next++];
@@ -574,6 +523,7 @@ struct AdjBuffers {
             void *q = nullptr;
             if (cudaMalloc(&q, bytes) != cudaSuccess) {
                 cudaGetLastError();
+                if (quiet) return LBM_ENOMEM;
                 return fail(h, LBM_ENOMEM, "cannot allocate the adjoint workspace (" + std::to_string(bytes) + " bytes)");
             }
             slot = {q, bytes};
@@ -586,16 +536,8 @@ struct AdjBuffers {
 template <typename St, bool NB, bool BAND>
 cudaError_t launch_adj_step_tt(const StepParams &P, const AdjParams &A, cudaStream_t st) {
     const Geometry &g = P.g;
-    const dim3 eb(ADJ_XEDGE, EDGE_ROWS);
-    if (g.nx >= 2 * ADJ_XEDGE + 1) {
-        const dim3 ge(2, nblocks(g.ny, EDGE_ROWS), g.nz);
-        k_adj_edges<St, NB, BAND><<<ge, eb, 0, st>>>(P, A);
-        const dim3 gm(nblocks(g.nx - 2 * ADJ_XEDGE, STEP_BX), g.ny, g.nz);
-        k_adj_main<St, NB, BAND><<<gm, STEP_BX, 0, st>>>(P, A);
-    } else {
-        const dim3 ge(nblocks(g.nx, ADJ_XEDGE), nblocks(g.ny, EDGE_ROWS), g.nz);
-        k_adj_rows<St, NB, BAND><<<ge, eb, 0, st>>>(P, A);
-    }
+    k_adj_main<St, NB, BAND><<<dim3(nblocks(g.nx - 1, STEP_BX), g.ny, g.nz), STEP_BX, 0, st>>>(P, A);
+    k_adj_xface<St, NB, BAND><<<dim3(nblocks(g.nyz, 128), 2), 128, 0, st>>>(P, A);
     return cudaGetLastError();
 }
 
@@ -613,6 +555,7 @@ extern "C" int lbm_adjoint(lbm_ctx *h, int n, int K, const lbm_loss *loss, doubl
     if (!h->has_state) return fail(h, LBM_ESTATE, "lbm_set_state (or lbm_load) has not been called");
     if (n < 1 || !loss) return fail(h, LBM_EINVAL, "n must be >= 1 and loss given");
     if (h->cfg.collision != LBM_COLL_ACM) return fail(h, LBM_EINVAL, "the adjoint exists for the ACM-MRT collision only");
+    if (h->nx < 3) return fail(h, LBM_EINVAL, "the adjoint needs nx >= 3");
     if (h->band_count_dev) return fail(h, LBM_EINVAL, "the adjoint exists for static solids only (lbm_set_motion was called)");
     for (int k = 2; k < 6; ++k)
         if (h->cfg.face_type[k] == LBM_FACE_FREESLIP) return fail(h, LBM_EINVAL, "the adjoint does not cover free-slip faces");
@@ -626,48 +569,86 @@ extern "C" int lbm_adjoint(lbm_ctx *h, int n, int K, const lbm_loss *loss, doubl
     const int nck = (n + K - 1) / K;
     AdjBuffers B(h);
     int rc;
-    std::vector<char *> ckpt(nck), seg(K);
+    std::vector<char *> ckpt(nck);
     // checkpoints of the segments but the last, whose states the forward pass keeps itself
     for (int i = 0; i + 1 < nck; ++i) if ((rc = B.get(h, &ckpt[i], state_bytes))) return rc;
-    for (int i = 0; i < K; ++i) if ((rc = B.get(h, &seg[i], state_bytes))) return rc;
-    float *lamA, *lamB, *blam = nullptr, *dF_band = nullptr, *adj_band = nullptr, *adj_samp = nullptr;
+    float *lamA, *lamB, *dF_band = nullptr, *adj_band = nullptr, *adj_samp = nullptr;
     double *s_inlet, *dX = nullptr, *acc;
+    const int fblk = force_sum_blocks(S);
+    double *step_sums = nullptr;   // [3][n * fblk] per-step, per-block sums of the penalty forces
     if ((rc = B.get(h, &lamA, (size_t)27 * N)) || (rc = B.get(h, &lamB, (size_t)27 * N)) ||
         (rc = B.get(h, &s_inlet, (size_t)nyz)) || (rc = B.get(h, &acc, 8)))
         return rc;
-    if (h->outlet && (rc = B.get(h, &blam, (size_t)9 * nyz))) return rc;
+    if (S > 0 && (rc = B.get(h, &step_sums, (size_t)3 * n * fblk))) return rc;
     if (S > 0 && ((rc = B.get(h, &dX, (size_t)3 * S)) || (rc = B.get(h, &dF_band, (size_t)3 * nb)) ||
                   (rc = B.get(h, &adj_band, (size_t)4 * nb)) || (rc = B.get(h, &adj_samp, (size_t)4 * S))))
         return rc;
-    // IB values of the recomputed steps of a segment (all but its last step): slot j holds those
-    // of the step from state t0 + j
-    float *k_rho = nullptr, *k_u = nullptr, *k_g = nullptr, *k_F = nullptr;
-    const size_t nslot = (size_t)(K - 1);
-    if (S > 0 && nslot > 0 &&
-        ((rc = B.get(h, &k_rho, nslot * nb)) || (rc = B.get(h, &k_u, nslot * 3 * nb)) ||
-         (rc = B.get(h, &k_g, nslot * 3 * S)) || (rc = B.get(h, &k_F, nslot * 3 * nb))))
-        return rc;
-    IBArrays ib(h);
-    auto point_slot = [&](long long j) {
-        ib.point(k_rho + j * nb, k_u + j * 3 * nb, k_g + j * 3 * S, k_F + j * 3 * nb);
+    float *g_last = nullptr, *F_last = nullptr;     // IB diagnostics of the last step, restored at the end
+    if (S > 0 && ((rc = B.get(h, &g_last, (size_t)3 * S)) || (rc = B.get(h, &F_last, (size_t)3 * nb)))) return rc;
+    // Segment sets: the states f_{t0 + k} of a segment and the IB values of its recomputed steps
+    // (slot j: the step from state t0 + j; the last step of a segment keeps none).  With two sets
+    // the recompute of segment s - 1 runs on a second stream beside the backward pass of segment
+    // s; a second set that does not fit in device memory leaves one, and the two alternate.
+    struct SegSet {
+        std::vector<char *> f;
+        float *rho = nullptr, *u = nullptr, *g = nullptr, *F = nullptr;
     };
-    const int fblk = force_sum_blocks(S);
+    const size_t nslot = (size_t)(K - 1);
+    auto get_set = [&](SegSet &q, bool quiet) -> int {
+        q.f.assign(K, nullptr);
+        for (int i = 0; i < K; ++i) if ((rc = B.get(h, &q.f[i], state_bytes, quiet))) return rc;
+        if (S > 0 && nslot > 0 &&
+            ((rc = B.get(h, &q.rho, nslot * nb, quiet)) || (rc = B.get(h, &q.u, nslot * 3 * nb, quiet)) ||
+             (rc = B.get(h, &q.g, nslot * 3 * S, quiet)) || (rc = B.get(h, &q.F, nslot * 3 * nb, quiet))))
+            return rc;
+        return LBM_OK;
+    };
+    SegSet sets[2];
+    if ((rc = get_set(sets[0], false))) return rc;
+    const int nset = nck > 1 && get_set(sets[1], true) == LBM_OK ? 2 : 1;
+    IBArrays ib(h);
+    auto point_slot = [&](const SegSet &q, long long j) {
+        ib.point(q.rho + j * nb, q.u + j * 3 * nb, q.g + j * 3 * S, q.F + j * 3 * nb);
+    };
     StepParams P0 = make_params(h, h->t);
     const long long mblk = macro_blocks(P0);
-    if ((rc = ensure_partial(h, (size_t)std::max<long long>(MACRO_SUMS * mblk, 3 * fblk)))) return rc;
+    if ((rc = ensure_partial(h, (size_t)MACRO_SUMS * mblk))) return rc;
     cudaStream_t st = h->stream;
+    // with two sets: the recompute stream, the backward pass on a stream of the highest priority
+    // (the block scheduler serves its launches first, the recompute fills the rest), and the
+    // events between them and the context's stream
+    struct SideStreams {
+        cudaStream_t s = nullptr, b = nullptr;
+        cudaEvent_t done[2] = {nullptr, nullptr}, free_[2] = {nullptr, nullptr}, fork = nullptr, join = nullptr;
+        ~SideStreams() {
+            if (s) cudaStreamSynchronize(s);
+            if (b) cudaStreamSynchronize(b);
+            for (cudaEvent_t e : {done[0], done[1], free_[0], free_[1], fork, join})
+                if (e) cudaEventDestroy(e);
+            if (s) cudaStreamDestroy(s);
+            if (b) cudaStreamDestroy(b);
+        }
+    } side;
+    if (nset == 2) {
+        int lo = 0, hi = 0;
+        CK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+        CK(cudaStreamCreateWithPriority(&side.s, cudaStreamNonBlocking, lo));
+        CK(cudaStreamCreateWithPriority(&side.b, cudaStreamNonBlocking, kBackwardPriority ? hi : lo));
+        for (cudaEvent_t *e : {&side.done[0], &side.done[1], &side.free_[0], &side.free_[1], &side.fork, &side.join})
+            CK(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+    }
     CK(cudaMemsetAsync(s_inlet, 0, nyz * sizeof(double), st));
     CK(cudaMemsetAsync(acc, 0, 8 * sizeof(double), st));
     if (dX) CK(cudaMemsetAsync(dX, 0, 3 * S * sizeof(double), st));
     CK(cudaMemsetAsync(lamA, 0, (size_t)27 * N * sizeof(float), st));
 
     // forward pass: checkpoints, drag accumulation, final kinetic energy.  The last segment runs
-    // out of place through the segment buffers and keeps its IB values, as its recompute would
-    // (the backward pass then starts without one); its last step writes the context's state.
+    // out of place through set 0 and keeps its IB values, as its recompute would (the backward
+    // pass then starts without one); its last step writes the context's state.
     const long long t_start = h->t;
     const int last0 = (nck - 1) * K, last_len = n - last0;
     for (int i = 0; i < n; ++i) {
-        char *keep = i < last0 ? (i % K == 0 ? ckpt[i / K] : nullptr) : (i == last0 ? seg[0] : nullptr);
+        char *keep = i < last0 ? (i % K == 0 ? ckpt[i / K] : nullptr) : (i == last0 ? sets[0].f[0] : nullptr);
         if (keep) {
             CK(cudaMemcpyAsync(keep, h->f, pop_bytes, cudaMemcpyDeviceToDevice, st));
             if (out_bytes) CK(cudaMemcpyAsync(keep + pop_bytes, h->outlet, out_bytes, cudaMemcpyDeviceToDevice, st));
@@ -678,16 +659,16 @@ extern "C" int lbm_adjoint(lbm_ctx *h, int n, int K, const lbm_loss *loss, doubl
             const int k = i - last0;
             const bool inner = k + 1 < last_len;
             if (S > 0) {
-                if (inner) point_slot(k);
+                if (inner) point_slot(sets[0], k);
                 else ib.restore();
             }
-            if ((rc = adj_forward_step(h, seg[k], inner ? seg[k + 1] : nullptr))) return rc;
+            if ((rc = adj_forward_step(h, sets[0].f[k], inner ? sets[0].f[k + 1] : nullptr))) return rc;
         }
-        if (S > 0) {
-            CK(launch_sum_forces(S, h->g, h->partial, st));
-            k_finalize_add<<<1, 256, 0, st>>>(h->partial, fblk, 3, acc);
-            CK(cudaGetLastError());
-        }
+        if (S > 0) CK(launch_sum_forces(S, h->g, step_sums + (size_t)i * fblk, st, (long long)n * fblk));
+    }
+    if (S > 0) {
+        k_finalize_add<<<1, 256, 0, st>>>(step_sums, (long long)n * fblk, 3, acc);
+        CK(cudaGetLastError());
     }
     {
         StepParams P = make_params(h, h->t);
@@ -696,41 +677,68 @@ extern "C" int lbm_adjoint(lbm_ctx *h, int n, int K, const lbm_loss *loss, doubl
         k_finalize_add<<<1, 256, 0, st>>>(h->partial + 4 * mblk, mblk, 1, acc + 3);
         CK(cudaGetLastError());
     }
-    float *g_last = nullptr, *F_last = nullptr;     // IB diagnostics of the last step, restored at the end
     if (S > 0) {
-        if ((rc = B.get(h, &g_last, (size_t)3 * S)) || (rc = B.get(h, &F_last, (size_t)3 * nb))) return rc;
         CK(cudaMemcpyAsync(g_last, h->g, 3 * S * sizeof(float), cudaMemcpyDeviceToDevice, st));
         CK(cudaMemcpyAsync(F_last, h->bandF, 3 * nb * sizeof(float), cudaMemcpyDeviceToDevice, st));
     }
 
-    // backward pass over the segments, last first
+    // recompute segment sgi's states out of place into set q on stream rs: f[k] = f_{t0 + k}
+    auto recompute = [&](int sgi, const SegSet &q, cudaStream_t rs) -> int {
+        const long long t0 = t_start + (long long)sgi * K;
+        const int len = (int)std::min<long long>(K, t_start + n - t0);
+        CK(cudaMemcpyAsync(q.f[0], ckpt[sgi], state_bytes, cudaMemcpyDeviceToDevice, rs));
+        struct StreamSwap {   // step_with launches on the context's stream
+            lbm_ctx *h;
+            cudaStream_t old;
+            StreamSwap(lbm_ctx *h_, cudaStream_t s) : h(h_), old(h_->stream) { h->stream = s; }
+            ~StreamSwap() { h->stream = old; }
+        } swap_(h, rs);
+        for (int k = 0; k + 1 < len; ++k) {
+            if (S > 0) point_slot(q, k);
+            StepParams Pf = make_params(h, t0 + k + 1);
+            point_states(Pf, h, q.f[k], q.f[k + 1]);
+            int r = step_with(h, Pf);
+            if (r) return r;
+        }
+        return LBM_OK;
+    };
+
+    // backward pass over the segments, last first; segment sgi uses set (nck - 1 - sgi) % nset
     float *lam_cur = lamA, *lam_prev = lamB;
     const float drag_w = (float)(-loss->w_drag / n);
+    cudaStream_t bs = st;   // stream of the backward pass
+    if (nset == 2) {
+        CK(cudaEventRecord(side.free_[1], st));   // checkpoints written, set 1 unused
+        CK(cudaEventRecord(side.fork, st));
+        CK(cudaStreamWaitEvent(side.b, side.fork, 0));
+        bs = side.b;
+    }
     for (int sgi = nck - 1; sgi >= 0; --sgi) {
         const long long t0 = t_start + (long long)sgi * K;
         const int len = (int)std::min<long long>(K, t_start + n - t0);
-        // recompute the segment's states out of place: seg[k] = f_{t0 + k} (the last segment's
-        // are there from the forward pass)
-        if (sgi + 1 < nck) {
-            CK(cudaMemcpyAsync(seg[0], ckpt[sgi], state_bytes, cudaMemcpyDeviceToDevice, st));
-            for (int k = 0; k + 1 < len; ++k) {
-                if (S > 0) point_slot(k);
-                StepParams Pf = make_params(h, t0 + k + 1);
-                point_states(Pf, h, seg[k], seg[k + 1]);
-                if ((rc = step_with(h, Pf))) return rc;
+        const int cur = (nck - 1 - sgi) % nset;
+        const SegSet &q = sets[cur];
+        if (nset == 2) {
+            if (sgi + 1 < nck) CK(cudaStreamWaitEvent(bs, side.done[cur], 0));
+            if (sgi >= 1) {
+                const int nxt = cur ^ 1;
+                CK(cudaStreamWaitEvent(side.s, side.free_[nxt], 0));
+                if ((rc = recompute(sgi - 1, sets[nxt], side.s))) return rc;
+                CK(cudaEventRecord(side.done[nxt], side.s));
             }
+        } else if (sgi + 1 < nck) {
+            if ((rc = recompute(sgi, q, st))) return rc;
         }
         for (long long t = t0 + len; t > t0; --t) {
             const long long j = t - 1 - t0;
             const bool kept = S > 0 && j + 1 < len;   // the recompute left this step's IB values
-            if (kept) point_slot(j);
+            if (kept) point_slot(q, j);
             else ib.restore();
             StepParams P = make_params(h, t);
-            point_states(P, h, seg[t - 1 - t0], seg[t - 1 - t0]);
+            point_states(P, h, q.f[j], q.f[j]);
             AdjParams A{};
             A.lam_cur = lam_cur;
             A.lam_prev = lam_prev;
-            A.blam = blam;
             A.s_inlet = s_inlet;
             A.adj_band = adj_band;
             A.dF_band = dF_band;
@@ -740,32 +748,33 @@ extern "C" int lbm_adjoint(lbm_ctx *h, int n, int K, const lbm_loss *loss, doubl
             const bool nbp = (t & 1) != 0;
             if (S > 0) {
                 if (!kept) {
-                    CK(launch_band_moments(h->storage, P, h->band_cell, h->band_rho, h->band_u, st));
-                    CK(launch_ib_interp(P, S, h->X, h->area, h->ub_zero ? nullptr : h->ub, h->band_rho, h->band_u, h->g, st));
-                    CK(launch_ib_spread(S, nb, nullptr, h->X, h->g, h->base_nbr, h->cstart, h->ccount, h->bandF, st));
+                    CK(launch_band_moments(h->storage, P, h->band_cell, h->band_rho, h->band_u, bs));
+                    CK(launch_ib_interp(P, S, h->X, h->area, h->ub_zero ? nullptr : h->ub, h->band_rho, h->band_u, h->g, bs));
+                    CK(launch_ib_spread(S, nb, nullptr, h->X, h->g, h->base_nbr, h->cstart, h->ccount, h->bandF, bs));
                 }
                 CK(with_storage(h->storage, [&](auto tag) {
                     using St = decltype(tag);
-                    if (nbp) k_adj_band_force<St, true><<<nblocks(nb, 128), 128, 0, st>>>(P, A, h->band_cell);
-                    else k_adj_band_force<St, false><<<nblocks(nb, 128), 128, 0, st>>>(P, A, h->band_cell);
+                    if (nbp) k_adj_band_force<St, true><<<nblocks(nb, 128), 128, 0, bs>>>(P, A, h->band_cell);
+                    else k_adj_band_force<St, false><<<nblocks(nb, 128), 128, 0, bs>>>(P, A, h->band_cell);
                     return cudaGetLastError();
                 }));
-                k_adj_samples<<<nblocks(S, 256), 256, 0, st>>>(S, nb, h->X, h->area, h->ub, h->corner_band, h->band_rho,
+                k_adj_samples<<<nblocks(S, 256), 256, 0, bs>>>(S, nb, h->X, h->area, h->ub, h->corner_band, h->band_rho,
                                                                h->band_u, h->g, dF_band, drag_w, adj_samp, dX);
-                k_adj_band_gather<<<nblocks(nb, 256), 256, 0, st>>>(S, nb, h->X, h->base_nbr, h->cstart, h->ccount,
+                k_adj_band_gather<<<nblocks(nb, 256), 256, 0, bs>>>(S, nb, h->X, h->base_nbr, h->cstart, h->ccount,
                                                                     adj_samp, h->band_rho, h->band_u, adj_band);
                 CK(cudaGetLastError());
             }
             CK(with_storage(h->storage, [&](auto tag) {
                 using St = decltype(tag);
-                return launch_adj_step<St>(P, A, nbp, S > 0, st);
+                return launch_adj_step<St>(P, A, nbp, S > 0, bs);
             }));
-            if (h->outlet) {
-                k_adj_outlet<<<nblocks(nyz, 128), 128, 0, st>>>(P, A);
-                CK(cudaGetLastError());
-            }
             std::swap(lam_cur, lam_prev);
         }
+        if (nset == 2) CK(cudaEventRecord(side.free_[cur], bs));
+    }
+    if (nset == 2) {
+        CK(cudaEventRecord(side.join, bs));
+        CK(cudaStreamWaitEvent(st, side.join, 0));
     }
     ib.restore();
     // the forward pass left the state at t_start + n; restore its IB diagnostics
@@ -784,14 +793,23 @@ extern "C" int lbm_adjoint(lbm_ctx *h, int n, int K, const lbm_loss *loss, doubl
     CK(cudaStreamSynchronize(st));
     if (L) *L = loss->w_drag * (-hacc[0]) / n + loss->w_ke * hacc[3];
     if (dL_dinflow) {
-        for (int m = 1; m <= 4; ++m)
-            for (int q = 1; q <= 4; ++q) {
+        // dL/da_mq = sum_z sin(q pi (z + 1/2) / nz) sum_y sin(m pi (y + 1/2) / ny) s(y, z)
+        std::vector<double> sy(4 * (size_t)h->ny), sz(4 * (size_t)h->nz), row(4 * (size_t)h->nz, 0.0);
+        for (int m = 1; m <= 4; ++m) {
+            for (int y = 0; y < h->ny; ++y) sy[(m - 1) * (size_t)h->ny + y] = std::sin(m * M_PI * (y + 0.5) / h->ny);
+            for (int z = 0; z < h->nz; ++z) sz[(m - 1) * (size_t)h->nz + z] = std::sin(m * M_PI * (z + 0.5) / h->nz);
+        }
+        for (int m = 0; m < 4; ++m)
+            for (int z = 0; z < h->nz; ++z) {
                 double v = 0.0;
-                for (int z = 0; z < h->nz; ++z)
-                    for (int y = 0; y < h->ny; ++y)
-                        v += sin_[y + (size_t)h->ny * z] * std::sin(m * M_PI * (y + 0.5) / h->ny) *
-                             std::sin(q * M_PI * (z + 0.5) / h->nz);
-                dL_dinflow[(m - 1) * 4 + (q - 1)] = h->cfg.face_type[0] == LBM_FACE_INLET ? v : 0.0;
+                for (int y = 0; y < h->ny; ++y) v += sin_[y + (size_t)h->ny * z] * sy[m * (size_t)h->ny + y];
+                row[m * (size_t)h->nz + z] = v;
+            }
+        for (int m = 0; m < 4; ++m)
+            for (int q = 0; q < 4; ++q) {
+                double v = 0.0;
+                for (int z = 0; z < h->nz; ++z) v += row[m * (size_t)h->nz + z] * sz[q * (size_t)h->nz + z];
+                dL_dinflow[m * 4 + q] = h->cfg.face_type[0] == LBM_FACE_INLET ? v : 0.0;
             }
     }
     if (dL_dpos && S > 0) {

@@ -20,10 +20,9 @@ enum CollisionModel { COLL_ACM = 0, COLL_BGK = 1, COLL_RAW = 2 };
 // 2 XEDGE + 1 run entirely in the face kernel.  16-node strips: the general face rules cost more
 // per node than the main kernel, so narrower strips put more of each row in the main kernel
 // (whole step 8.76 -> 8.69 ms on the buildings workload, FP16 6.17 -> 6.09 ms).  The adjoint's
-// backward kernels keep 32-node strips (ADJ_XEDGE): their main kernel runs one node per thread and
-// measured slower with narrower strips.
+// backward step has no strips: its main kernel takes 1 <= x <= nx - 2 and a one-thread-per-node
+// kernel the two x faces.
 constexpr int XEDGE = 16;
-constexpr int ADJ_XEDGE = 32;
 constexpr int STEP_BX = 64;   // threads per block of the main step kernels (along x)
 cudaError_t launch_step(int storage, const StepParams &P, bool band, int part, int collision, cudaStream_t st);
 template <int COLL, bool FS>
@@ -66,6 +65,8 @@ cudaError_t launch_ib_interp(const StepParams &P, long long S, const float *X, c
 cudaError_t launch_ib_spread(long long S, long long nband, const int *count, const float *X, const float *g,
                              const int *base_nbr, const int *cstart, const int *ccount, float *bandF, cudaStream_t st);
 int force_sum_blocks(long long S);
-cudaError_t launch_sum_forces(long long S, const float *g, double *partial, cudaStream_t st);
+// per-block force sums (force_sum_blocks(S) blocks); component k of block b at
+// partial[k * stride + b], stride = the block count when 0
+cudaError_t launch_sum_forces(long long S, const float *g, double *partial, cudaStream_t st, long long stride = 0);
 
 }  // namespace lbm

@@ -256,7 +256,10 @@ __global__ void __launch_bounds__(256) k_ib_spread(long long S, long long nband,
 }
 
 // FP64 block partial sums of the penalty forces (drag = -sum g)
-__global__ void __launch_bounds__(256) k_sum_forces(long long S, const float *__restrict__ g, double *__restrict__ partial) {
+// per-block FP64 sums of the three force components; component k of block b at
+// partial[k * stride + b]
+__global__ void __launch_bounds__(256) k_sum_forces(long long S, const float *__restrict__ g, double *__restrict__ partial,
+                                                    long long stride) {
     __shared__ double s[3][256];
     double a[3] = {0.0, 0.0, 0.0};
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < S; i += (long long)gridDim.x * blockDim.x) {
@@ -272,7 +275,7 @@ __global__ void __launch_bounds__(256) k_sum_forces(long long S, const float *__
         __syncthreads();
     }
     if (threadIdx.x == 0)
-        for (int k = 0; k < 3; ++k) partial[(long long)k * gridDim.x + blockIdx.x] = s[k][0];
+        for (int k = 0; k < 3; ++k) partial[(long long)k * stride + blockIdx.x] = s[k][0];
 }
 
 // ---- host launchers ------------------------------------------------------------------
@@ -400,8 +403,9 @@ int force_sum_blocks(long long S) {
     return (int)(b < 1 ? 1 : (b > 1024 ? 1024 : b));
 }
 
-cudaError_t launch_sum_forces(long long S, const float *g, double *partial, cudaStream_t st) {
-    k_sum_forces<<<force_sum_blocks(S), 256, 0, st>>>(S, g, partial);
+cudaError_t launch_sum_forces(long long S, const float *g, double *partial, cudaStream_t st, long long stride) {
+    const int nb = force_sum_blocks(S);
+    k_sum_forces<<<nb, 256, 0, st>>>(S, g, partial, stride > 0 ? stride : nb);
     return cudaGetLastError();
 }
 

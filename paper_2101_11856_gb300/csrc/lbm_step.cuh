@@ -474,8 +474,8 @@ __device__ __forceinline__ void store_edge(const StepParams &P, int x, int y, in
 
 // x of an edge-strip thread: SIDE 0 / 1 = left / right strip of a row with a main range,
 // SIDE 2 = consecutive warps over a row too short for the main kernel
-template <int SIDE, int W = XEDGE> __device__ __forceinline__ int edge_x(const Geometry &g) {
-    return SIDE == 0 ? (int)threadIdx.x : SIDE == 1 ? g.nx - W + (int)threadIdx.x : (int)(blockIdx.x * W + threadIdx.x);
+template <int SIDE> __device__ __forceinline__ int edge_x(const Geometry &g) {
+    return SIDE == 0 ? (int)threadIdx.x : SIDE == 1 ? g.nx - XEDGE + (int)threadIdx.x : (int)(blockIdx.x * XEDGE + threadIdx.x);
 }
 constexpr int EDGE_ROWS = 4;   // rows (y) per edge-kernel block, one warp each
 
