@@ -305,14 +305,12 @@ __global__ void __launch_bounds__(256) k_adj_samples(long long S, long long nban
 }
 
 // per band node: gather dL/d rho*, dL/du_IB from the samples (transpose of Eq. 6), then
-// through u_IB = (j + F_body/2)/rho* to dL/d rho*, dL/dj
-__global__ void __launch_bounds__(256) k_adj_band_gather(long long S, long long nband, const float *__restrict__ X,
-                                                         const int *__restrict__ base_nbr, const int *__restrict__ cstart,
-                                                         const int *__restrict__ ccount, const float *__restrict__ adj_samp,
-                                                         const float *__restrict__ band_rho,
-                                                         const float *__restrict__ band_u, float *__restrict__ adj_band) {
-    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= nband) return;
+// through u_IB = (j + F_body/2)/rho* to dL/d rho*, dL/dj (returned as x, y, z, w = rho*, j_x,
+// j_y, j_z)
+__device__ __forceinline__ float4 band_gather(long long k, long long S, long long nband, const float *__restrict__ X,
+                                              const int *__restrict__ base_nbr, const int *__restrict__ cstart,
+                                              const int *__restrict__ ccount, const float *__restrict__ adj_samp,
+                                              const float *__restrict__ band_rho, const float *__restrict__ band_u) {
     float dr = 0.0f, du = 0.0f, dv = 0.0f, dw = 0.0f;
 #pragma unroll 1
     for (int c = 0; c < 8; ++c) {
@@ -329,38 +327,73 @@ __global__ void __launch_bounds__(256) k_adj_band_gather(long long S, long long 
     }
     const float rho = band_rho[k], inv = 1.0f / rho;
     const float u = band_u[k], v = band_u[nband + k], w = band_u[2 * nband + k];
-    adj_band[k] = dr - (du * u + dv * v + dw * w) * inv;
-    adj_band[nband + k] = du * inv;
-    adj_band[2 * nband + k] = dv * inv;
-    adj_band[3 * nband + k] = dw * inv;
+    return make_float4(dr - (du * u + dv * v + dw * w) * inv, du * inv, dv * inv, dw * inv);
+}
+
+__global__ void __launch_bounds__(256) k_adj_band_gather(long long S, long long nband, const float *__restrict__ X,
+                                                         const int *__restrict__ base_nbr, const int *__restrict__ cstart,
+                                                         const int *__restrict__ ccount, const float *__restrict__ adj_samp,
+                                                         const float *__restrict__ band_rho,
+                                                         const float *__restrict__ band_u, float *__restrict__ adj_band) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nband) return;
+    const float4 a = band_gather(k, S, nband, X, base_nbr, cstart, ccount, adj_samp, band_rho, band_u);
+    adj_band[k] = a.x;
+    adj_band[nband + k] = a.y;
+    adj_band[2 * nband + k] = a.z;
+    adj_band[3 * nband + k] = a.w;
 }
 
 // dL/df* of a node: collision VJP with the band's IB terms and the loss's kinetic-energy term
+// (lam holds the incoming lambda_t of the node on entry)
+template <bool BAND>
+__device__ __forceinline__ void node_vjp_in(const StepParams &P, const AdjParams &A, int x, int cell, float (&fs)[27],
+                                            float (&lam)[27]) {
+#pragma unroll
+    for (int d = 0; d < 27; ++d) fs[d] += wgt(d) * P.rho0;
+    float Fx = P.Fx, Fy = P.Fy, Fz = P.Fz;
+    AdjExtra ex{0.0f, 0.0f, 0.0f, 0.0f, (x >= A.ke_x0 && x < A.ke_x1) ? A.wke : 0.0f};
+    long long b;
+    if (BAND && band_index(P, cell, b)) {
+        Fx += P.bandF[b];
+        Fy += P.bandF[P.nband + b];
+        Fz += P.bandF[2 * P.nband + b];
+        ex.drho = A.adj_band[b];
+        ex.djx = A.adj_band[P.nband + b];
+        ex.djy = A.adj_band[2 * P.nband + b];
+        ex.djz = A.adj_band[3 * P.nband + b];
+    }
+    float dFx = 0.0f, dFy = 0.0f, dFz = 0.0f;
+    collide_vjp(fs, Fx, Fy, Fz, P, ex, lam, dFx, dFy, dFz);
+}
+
 template <bool BAND>
 __device__ __forceinline__ void node_vjp(const StepParams &P, const AdjParams &A, int x, int cell, float (&fs)[27],
                                          float (&lam)[27]) {
     const long long N = P.g.ncell;
 #pragma unroll
-    for (int d = 0; d < 27; ++d) {
-        fs[d] += wgt(d) * P.rho0;
-        lam[d] = A.lam_cur[d * N + cell];
-    }
-    float Fx = P.Fx, Fy = P.Fy, Fz = P.Fz;
-    AdjExtra ex{0.0f, 0.0f, 0.0f, 0.0f, (x >= A.ke_x0 && x < A.ke_x1) ? A.wke : 0.0f};
-    if (BAND) {
-        long long b;
-        if (band_index(P, cell, b)) {
-            Fx += P.bandF[b];
-            Fy += P.bandF[P.nband + b];
-            Fz += P.bandF[2 * P.nband + b];
-            ex.drho = A.adj_band[b];
-            ex.djx = A.adj_band[P.nband + b];
-            ex.djy = A.adj_band[2 * P.nband + b];
-            ex.djz = A.adj_band[3 * P.nband + b];
+    for (int d = 0; d < 27; ++d) lam[d] = A.lam_cur[d * N + cell];
+    node_vjp_in<BAND>(P, A, x, cell, fs, lam);
+}
+
+// push of mu from a node 1 <= x <= nx - 2 of row (y, z)
+__device__ __forceinline__ void adj_push_main(const StepParams &P, const AdjParams &A, int y, int z, int cell, bool inner,
+                                              const float (&lam)[27]) {
+    const long long N = P.g.ncell;
+    if (inner) {
+#pragma unroll
+        for (int d = 0; d < 27; ++d)
+            A.lam_prev[d * N + cell - (cx(d) + cy(d) * P.g.nx + cz(d) * P.g.nxy)] = lam[d];
+    } else {
+        int off[9], mir[9];
+        bool bb[9];
+        yz_rows<-1, false>(P.g, y, z, off, bb, mir);   // free-slip faces are rejected by lbm_adjoint
+#pragma unroll
+        for (int d = 0; d < 27; ++d) {
+            if (bb[d / 3]) A.lam_prev[opp(d) * N + cell] = lam[d];
+            else A.lam_prev[d * N + cell + off[d / 3] - cx(d)] = lam[d];
         }
     }
-    float dFx = 0.0f, dFy = 0.0f, dFz = 0.0f;
-    collide_vjp(fs, Fx, Fy, Fz, P, ex, lam, dFx, dFy, dFz);
 }
 
 // Backward step of the nodes 1 <= x <= nx - 2 (one block row per (y, z); the lanes of x = 0 and
@@ -380,21 +413,7 @@ __global__ void __launch_bounds__(STEP_BX, 12) k_adj_main(StepParams P, AdjParam
     if (!NB || inner) load_interior<St, NB>(P, cell, fs);
     else load_yzface<St, false>(P, y, z, cell, fs);
     node_vjp<BAND>(P, A, x, cell, fs, lam);
-    const long long N = P.g.ncell;
-    if (inner) {
-#pragma unroll
-        for (int d = 0; d < 27; ++d)
-            A.lam_prev[d * N + cell - (cx(d) + cy(d) * P.g.nx + cz(d) * P.g.nxy)] = lam[d];
-    } else {
-        int off[9], mir[9];
-        bool bb[9];
-        yz_rows<-1, false>(P.g, y, z, off, bb, mir);   // free-slip faces are rejected by lbm_adjoint
-#pragma unroll
-        for (int d = 0; d < 27; ++d) {
-            if (bb[d / 3]) A.lam_prev[opp(d) * N + cell] = lam[d];
-            else A.lam_prev[d * N + cell + off[d / 3] - cx(d)] = lam[d];
-        }
-    }
+    adj_push_main(P, A, y, z, cell, inner, lam);
 }
 
 // Backward step of the x-face nodes x = 0 (blockIdx.y = 0) and x = nx - 1 (blockIdx.y = 1), one
@@ -569,9 +588,6 @@ extern "C" int lbm_adjoint(lbm_ctx *h, int n, int K, const lbm_loss *loss, doubl
     const int nck = (n + K - 1) / K;
     AdjBuffers B(h);
     int rc;
-    std::vector<char *> ckpt(nck);
-    // checkpoints of the segments but the last, whose states the forward pass keeps itself
-    for (int i = 0; i + 1 < nck; ++i) if ((rc = B.get(h, &ckpt[i], state_bytes))) return rc;
     float *lamA, *lamB, *dF_band = nullptr, *adj_band = nullptr, *adj_samp = nullptr;
     double *s_inlet, *dX = nullptr, *acc;
     const int fblk = force_sum_blocks(S);
@@ -606,6 +622,11 @@ extern "C" int lbm_adjoint(lbm_ctx *h, int n, int K, const lbm_loss *loss, doubl
     SegSet sets[2];
     if ((rc = get_set(sets[0], false))) return rc;
     const int nset = nck > 1 && get_set(sets[1], true) == LBM_OK ? 2 : 1;
+    // checkpoints of the segments whose states the forward pass does not keep in a set (all but
+    // the last nset)
+    const int nstored = nset;
+    std::vector<char *> ckpt(nck, nullptr);
+    for (int i = 0; i + nstored < nck; ++i) if ((rc = B.get(h, &ckpt[i], state_bytes))) return rc;
     IBArrays ib(h);
     auto point_slot = [&](const SegSet &q, long long j) {
         ib.point(q.rho + j * nb, q.u + j * 3 * nb, q.g + j * 3 * S, q.F + j * 3 * nb);
@@ -642,27 +663,35 @@ extern "C" int lbm_adjoint(lbm_ctx *h, int n, int K, const lbm_loss *loss, doubl
     if (dX) CK(cudaMemsetAsync(dX, 0, 3 * S * sizeof(double), st));
     CK(cudaMemsetAsync(lamA, 0, (size_t)27 * N * sizeof(float), st));
 
-    // forward pass: checkpoints, drag accumulation, final kinetic energy.  The last segment runs
-    // out of place through set 0 and keeps its IB values, as its recompute would (the backward
-    // pass then starts without one); its last step writes the context's state.
+    // forward pass: checkpoints, drag accumulation, final kinetic energy.  The last nstored
+    // segments run out of place through their sets and keep their IB values, as their recompute
+    // would (the backward pass then starts without one); the last step writes the context's state.
     const long long t_start = h->t;
-    const int last0 = (nck - 1) * K, last_len = n - last0;
+    const int first_kept = nck - nstored;   // first segment kept in a set
+    auto set_of = [&](int sgi) -> SegSet & { return sets[(nck - 1 - sgi) % nset]; };
     for (int i = 0; i < n; ++i) {
-        char *keep = i < last0 ? (i % K == 0 ? ckpt[i / K] : nullptr) : (i == last0 ? sets[0].f[0] : nullptr);
-        if (keep) {
-            CK(cudaMemcpyAsync(keep, h->f, pop_bytes, cudaMemcpyDeviceToDevice, st));
-            if (out_bytes) CK(cudaMemcpyAsync(keep + pop_bytes, h->outlet, out_bytes, cudaMemcpyDeviceToDevice, st));
-        }
-        if (i < last0) {
+        const int sgi = i / K, k = i % K;
+        const int len = std::min(K, n - sgi * K);
+        if (sgi < first_kept) {
+            if (k == 0) {
+                CK(cudaMemcpyAsync(ckpt[sgi], h->f, pop_bytes, cudaMemcpyDeviceToDevice, st));
+                if (out_bytes) CK(cudaMemcpyAsync(ckpt[sgi] + pop_bytes, h->outlet, out_bytes, cudaMemcpyDeviceToDevice, st));
+            }
             if ((rc = lbm_step(h, 1))) return rc;
         } else {
-            const int k = i - last0;
-            const bool inner = k + 1 < last_len;
+            SegSet &q = set_of(sgi);
+            if (i == first_kept * K) {   // the context's state enters the first kept segment
+                CK(cudaMemcpyAsync(q.f[0], h->f, pop_bytes, cudaMemcpyDeviceToDevice, st));
+                if (out_bytes) CK(cudaMemcpyAsync(q.f[0] + pop_bytes, h->outlet, out_bytes, cudaMemcpyDeviceToDevice, st));
+            }
+            const bool inner = k + 1 < len;
             if (S > 0) {
-                if (inner) point_slot(sets[0], k);
+                if (inner) point_slot(q, k);
                 else ib.restore();
             }
-            if ((rc = adj_forward_step(h, sets[0].f[k], inner ? sets[0].f[k + 1] : nullptr))) return rc;
+            // the segment's last step writes the next segment's first state, or the context's
+            char *dst = inner ? q.f[k + 1] : (sgi + 1 < nck ? set_of(sgi + 1).f[0] : nullptr);
+            if ((rc = adj_forward_step(h, q.f[k], dst))) return rc;
         }
         if (S > 0) CK(launch_sum_forces(S, h->g, step_sums + (size_t)i * fblk, st, (long long)n * fblk));
     }
@@ -719,14 +748,14 @@ extern "C" int lbm_adjoint(lbm_ctx *h, int n, int K, const lbm_loss *loss, doubl
         const int cur = (nck - 1 - sgi) % nset;
         const SegSet &q = sets[cur];
         if (nset == 2) {
-            if (sgi + 1 < nck) CK(cudaStreamWaitEvent(bs, side.done[cur], 0));
-            if (sgi >= 1) {
+            if (sgi < first_kept) CK(cudaStreamWaitEvent(bs, side.done[cur], 0));
+            if (sgi >= 1 && sgi - 1 < first_kept) {
                 const int nxt = cur ^ 1;
                 CK(cudaStreamWaitEvent(side.s, side.free_[nxt], 0));
                 if ((rc = recompute(sgi - 1, sets[nxt], side.s))) return rc;
                 CK(cudaEventRecord(side.done[nxt], side.s));
             }
-        } else if (sgi + 1 < nck) {
+        } else if (sgi < first_kept) {
             if ((rc = recompute(sgi, q, st))) return rc;
         }
         for (long long t = t0 + len; t > t0; --t) {

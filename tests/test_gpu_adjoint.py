@@ -105,10 +105,11 @@ def test_adjoint_advances_state_like_forward_steps():
 
 @pytest.mark.parametrize("K", [4, 2])
 def test_long_rows_main_and_edge_kernels(K):
-    """nx >= 65: the backward step runs the main kernel (32 <= x < nx - 32) and the two edge
-    strips, the layout of the 128^3 benchmark, against the oracle; the sphere lies in the main
-    range, the kinetic-energy slab next to the inlet (so that the inflow coefficients reach the
-    loss within the 6 steps)."""
+    """nx = 70: the backward main kernel takes 1 <= x <= 68 in two 64-node chunks per row (the
+    lanes past nx - 2 idle) and the x-face kernel the two end nodes, against the oracle; K = 2
+    recomputes the first segment on the second stream while the last two come from the forward
+    pass.  The sphere lies in the main range, the kinetic-energy slab next to the inlet (so that
+    the inflow coefficients reach the loss within the 6 steps)."""
     nx, ny, nz = 70, 6, 5
     faces = ("inlet", "outlet", "noslip", "noslip", "periodic", "periodic")
     X, A = scenes.fibonacci_sphere((37.4, 2.6, 2.3), 1.6, 30)
@@ -122,6 +123,27 @@ def test_long_rows_main_and_edge_kernels(K):
           f"rel dX {rel_l2(dxg, dxo.numpy()):.2e}")
     assert abs(Lg - Lo) <= 1e-5 * abs(Lo)
     assert np.abs(dco.numpy()).max() > 0 and np.abs(dxo.numpy()).max() > 0
+    assert rel_l2(dcg, dco.numpy()) <= 1e-3
+    assert rel_l2(dxg, dxo.numpy()) <= 1e-3
+
+
+@pytest.mark.parametrize("where", ["inlet", "outlet"])
+def test_band_at_the_x_faces(where):
+    """A sphere whose band reaches x = 0 (next to the inlet) or x = nx - 1 (next to the outlet):
+    band nodes in the x-face kernel (with the inlet's bounce-back and inflow gradient, or the
+    outlet ghost's second use), against the oracle; K = 2 with 6 steps recomputes one segment."""
+    nx, ny, nz = 16, 8, 8
+    faces = ("inlet", "outlet", "periodic", "periodic", "noslip", "noslip")
+    cx = 1.9 if where == "inlet" else nx - 2.7
+    X, A = scenes.fibonacci_sphere((cx, 3.6, 3.4), 1.2, 20)
+    rho, u = scenes.uniform_flow(nx, ny, nz, (0.04, 0, 0))
+    coef = np.random.default_rng(5).uniform(-0.004, 0.004, 16)
+    loss = Loss(1.0, 1.5, 4, 9)
+    s, (Lg, dcg, dxg), (Lo, dco, dxo) = run_both(nx, ny, nz, 0.04, 6, 2, loss, faces, rho, u, X, A, coef=coef,
+                                                 u_in=0.04, noise=0.01)
+    print(f"band at the {where}: L {Lg:.6e} vs {Lo:.6e}; rel dtheta {rel_l2(dcg, dco.numpy()):.2e}; "
+          f"rel dX {rel_l2(dxg, dxo.numpy()):.2e}")
+    assert abs(Lg - Lo) <= 1e-5 * abs(Lo)
     assert rel_l2(dcg, dco.numpy()) <= 1e-3
     assert rel_l2(dxg, dxo.numpy()) <= 1e-3
 
