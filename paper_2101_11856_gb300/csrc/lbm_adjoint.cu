@@ -226,7 +226,32 @@ struct AdjParams {
     float *dF_band;              // [3][nband] dL/dF of the band nodes
     float wke;                   // w_ke on the last step, else 0
     int ke_x0, ke_x1;
+    const float *ghost_in;       // [9][nyz] outlet ghost uses of step t + 1 (x-face kernel)
+    float *ghost_out;            // [9][nyz] outlet ghost uses of this step
 };
+
+// lambda_t of node (x, y, z) as its own backward step uses it: at x = nx - 1 next to an outlet the
+// slots the outlet ghost copied take the ghost's use of step t + 1 (ghost_in; the slot itself
+// holds the push of (nx-2, y, z)), and the slots of populations that left through the outlet
+// (no use) read as zero
+__device__ __forceinline__ void read_lambda(const StepParams &P, const AdjParams &A, int x, int y, int z, int cell,
+                                            float (&lam)[27]) {
+    const long long N = P.g.ncell;
+    const bool outlet = x == P.g.nx - 1 && P.g.face[1] == FACE_OUTLET;
+#pragma unroll
+    for (int d = 0; d < 27; ++d) {
+        lam[d] = A.lam_cur[d * N + cell];
+        if (outlet && cx(d) == 1 && neighbour<+1>(P.g, d, x, y, z).kind == CROSS_OUTLET) lam[d] = 0.0f;
+        if (outlet && cx(d) == -1) {
+            // the ghost of (nx-1, y + c_y, z + c_z) copied this slot for its f*_d
+            int yy = y + cy(d), zz = z + cz(d);
+            bool src = true;
+            if (yy < 0 || yy >= P.g.ny) { if (P.g.periodic[1]) yy += yy < 0 ? P.g.ny : -P.g.ny; else src = false; }
+            if (zz < 0 || zz >= P.g.nz) { if (P.g.periodic[2]) zz += zz < 0 ? P.g.nz : -P.g.nz; else src = false; }
+            if (src) lam[d] += A.ghost_in[(long long)(d / 3) * P.g.nyz + yy + P.g.ny * zz];
+        }
+    }
+}
 
 // dL/dF at the band nodes (collision VJP with respect to the force)
 template <typename St, bool NB>
@@ -238,9 +263,7 @@ __global__ void __launch_bounds__(128) k_adj_band_force(StepParams P, AdjParams 
     decompose(P.g, cell, x, y, z);
     float fs[27], lam[27];
     adj_load_fstar<St, NB>(P, x, y, z, cell, fs);
-    const long long N = P.g.ncell;
-#pragma unroll
-    for (int d = 0; d < 27; ++d) lam[d] = A.lam_cur[d * N + cell];
+    read_lambda(P, A, x, y, z, cell, lam);
     const float Fx = P.Fx + P.bandF[kb], Fy = P.Fy + P.bandF[P.nband + kb], Fz = P.Fz + P.bandF[2 * P.nband + kb];
     AdjExtra ex{0.0f, 0.0f, 0.0f, 0.0f, (x >= A.ke_x0 && x < A.ke_x1) ? A.wke : 0.0f};
     float dFx = 0.0f, dFy = 0.0f, dFz = 0.0f;
@@ -417,13 +440,13 @@ __global__ void __launch_bounds__(STEP_BX, 12) k_adj_main(StepParams P, AdjParam
 }
 
 // Backward step of the x-face nodes x = 0 (blockIdx.y = 0) and x = nx - 1 (blockIdx.y = 1), one
-// thread per node, launched after k_adj_main (nx >= 3).  Each mu_d goes back to the slot its
-// streamed value came from, by the pull's own per-direction rules: the wrapped neighbour
-// (periodic x), the node's reflected slot (no-slip; the inlet also feeds the inflow-coefficient
-// gradient), or, through the outlet ghost, the previous post-collision value of
-// (nx-1, y - c_y, z - c_z) that the ghost copied.  That slot (c_x = -1) already holds the push of
-// (nx-2, y, z) from k_adj_main and takes the ghost's use on top; no other thread writes it.
-// Slots of populations that left through the outlet have no use and are zeroed.
+// thread per node (nx >= 3).  Each mu_d goes back to the slot its streamed value came from, by
+// the pull's own per-direction rules: the wrapped neighbour (periodic x), the node's reflected
+// slot (no-slip; the inlet also feeds the inflow-coefficient gradient), or, through the outlet
+// ghost, the previous post-collision value of (nx-1, y - c_y, z - c_z) that the ghost copied.
+// That slot (c_x = -1) also takes the push of (nx-2, y, z) from k_adj_main, so the ghost's use
+// goes to ghost_out and the next backward step adds it where it reads the slot (read_lambda), so
+// no slot is written by both kernels and none is read back and written again.
 template <typename St, bool NB, bool BAND>
 __global__ void __launch_bounds__(128) k_adj_xface(StepParams P, AdjParams A) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -431,15 +454,11 @@ __global__ void __launch_bounds__(128) k_adj_xface(StepParams P, AdjParams A) {
     const int z = i / P.g.ny, y = i - z * P.g.ny;
     const int x = blockIdx.y ? P.g.nx - 1 : 0;
     const int cell = x + P.g.nx * (y + P.g.ny * z);
+    const long long N = P.g.ncell;
     float fs[27], lam[27];
     load_general<St, NB>(P, x, y, z, cell, fs);
-    node_vjp<BAND>(P, A, x, cell, fs, lam);
-    const long long N = P.g.ncell;
-    if (blockIdx.y && P.g.face[1] == FACE_OUTLET) {
-#pragma unroll
-        for (int d = 0; d < 27; ++d)
-            if (cx(d) == 1 && neighbour<+1>(P.g, d, x, y, z).kind == CROSS_OUTLET) A.lam_prev[d * N + cell] = 0.0f;
-    }
+    read_lambda(P, A, x, y, z, cell, lam);
+    node_vjp_in<BAND>(P, A, x, cell, fs, lam);
     float sth = 0.0f;   // this node's inflow sensitivity (accumulated over steps in FP64)
 #pragma unroll
     for (int d = 0; d < 27; ++d) {
@@ -451,7 +470,7 @@ __global__ void __launch_bounds__(128) k_adj_xface(StepParams P, AdjParams A) {
             A.lam_prev[opp(d) * N + cell] = mu;
             if (!(n.kind & CROSS_NOSLIP)) sth = fmaf(mu, 6.0f * wgt(d) * P.rho0, sth);   // inlet: c_x = +1
         } else {
-            A.lam_prev[d * N + (P.g.nx - 1) + P.g.nx * (n.y + P.g.ny * n.z)] += mu;   // outlet ghost
+            A.ghost_out[(long long)(d / 3) * P.g.nyz + y + P.g.ny * z] = mu;   // outlet ghost
         }
     }
     if (!blockIdx.y && P.g.face[0] == FACE_INLET) A.s_inlet[y + P.g.ny * z] += (double)sth;
@@ -592,8 +611,9 @@ extern "C" int lbm_adjoint(lbm_ctx *h, int n, int K, const lbm_loss *loss, doubl
     double *s_inlet, *dX = nullptr, *acc;
     const int fblk = force_sum_blocks(S);
     double *step_sums = nullptr;   // [3][n * fblk] per-step, per-block sums of the penalty forces
+    float *ghost = nullptr;   // [2][9][nyz] outlet ghost uses of alternate steps
     if ((rc = B.get(h, &lamA, (size_t)27 * N)) || (rc = B.get(h, &lamB, (size_t)27 * N)) ||
-        (rc = B.get(h, &s_inlet, (size_t)nyz)) || (rc = B.get(h, &acc, 8)))
+        (rc = B.get(h, &s_inlet, (size_t)nyz)) || (rc = B.get(h, &acc, 8)) || (rc = B.get(h, &ghost, (size_t)18 * nyz)))
         return rc;
     if (S > 0 && (rc = B.get(h, &step_sums, (size_t)3 * n * fblk))) return rc;
     if (S > 0 && ((rc = B.get(h, &dX, (size_t)3 * S)) || (rc = B.get(h, &dF_band, (size_t)3 * nb)) ||
@@ -642,12 +662,12 @@ extern "C" int lbm_adjoint(lbm_ctx *h, int n, int K, const lbm_loss *loss, doubl
         cudaStream_t s = nullptr, b = nullptr;
         cudaEvent_t done[2] = {nullptr, nullptr}, free_[2] = {nullptr, nullptr}, fork = nullptr, join = nullptr;
         ~SideStreams() {
-            if (s) cudaStreamSynchronize(s);
-            if (b) cudaStreamSynchronize(b);
+            for (cudaStream_t q : {s, b})
+                if (q) cudaStreamSynchronize(q);
             for (cudaEvent_t e : {done[0], done[1], free_[0], free_[1], fork, join})
                 if (e) cudaEventDestroy(e);
-            if (s) cudaStreamDestroy(s);
-            if (b) cudaStreamDestroy(b);
+            for (cudaStream_t q : {s, b})
+                if (q) cudaStreamDestroy(q);
         }
     } side;
     if (nset == 2) {
@@ -662,6 +682,7 @@ extern "C" int lbm_adjoint(lbm_ctx *h, int n, int K, const lbm_loss *loss, doubl
     CK(cudaMemsetAsync(acc, 0, 8 * sizeof(double), st));
     if (dX) CK(cudaMemsetAsync(dX, 0, 3 * S * sizeof(double), st));
     CK(cudaMemsetAsync(lamA, 0, (size_t)27 * N * sizeof(float), st));
+    CK(cudaMemsetAsync(ghost, 0, (size_t)18 * nyz * sizeof(float), st));
 
     // forward pass: checkpoints, drag accumulation, final kinetic energy.  The last nstored
     // segments run out of place through their sets and keep their IB values, as their recompute
@@ -774,6 +795,8 @@ extern "C" int lbm_adjoint(lbm_ctx *h, int n, int K, const lbm_loss *loss, doubl
             A.wke = (t == t_start + n) ? (float)loss->w_ke : 0.0f;
             A.ke_x0 = loss->ke_x0;
             A.ke_x1 = loss->ke_x1;
+            A.ghost_in = ghost + (size_t)((t + 1) & 1) * 9 * nyz;
+            A.ghost_out = ghost + (size_t)(t & 1) * 9 * nyz;
             const bool nbp = (t & 1) != 0;
             if (S > 0) {
                 if (!kept) {
