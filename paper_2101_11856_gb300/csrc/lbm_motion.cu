@@ -94,17 +94,16 @@ __global__ void __launch_bounds__(256) k_rel(long long S, const float *__restric
 // Phases of one kernel whose blocks are all resident (cooperative launch) and meet at grid-wide
 // barriers between the phases: pose and
 // keys (with the bitmap and run counters cleared), a stable LSD radix sort of the keys (8-bit
-// digits; the first REBUILD_SORT_BLOCKS blocks sort contiguous chunks, so the order within a digit
-// is the input order, as in sort_pairs), the samples gathered in sorted order, the band bitmap,
-// its prefix offsets and the band count, the corner band indices and band cells, the runs of
-// samples per base cell and the spreading lists (the structures lbm_set_solids builds on the host
-// for a static solid).
-constexpr int REBUILD_THREADS = 256;
-constexpr int REBUILD_SORT_BLOCKS = 32;
+// digits; every block sorts a contiguous chunk, so the order within a digit is the input order,
+// as in sort_pairs), the samples gathered in sorted order, the band bitmap, its prefix offsets and
+// the band count, the corner band indices, band cells and the runs of samples per base cell, and
+// the spreading lists (the structures lbm_set_solids builds on the host for a static solid).
+constexpr int REBUILD_THREADS = 256;   // also the largest grid (one block scans the block sums)
 
 struct RebuildArgs {
     long long S, ntiles, stride;   // samples, bitmap words, band array stride
     int bits;                      // significant bits of the keys
+    int klo[3], kdim[3];           // box of the base cells the solid can reach: origin, sizes
     Pose p;
     Lattice L;
     const float *rel, *area_in;
@@ -112,7 +111,7 @@ struct RebuildArgs {
     float *Xtmp, *X, *rel_o, *area_o, *ub;
     int *sid_o;
     uint32_t *key, *slot, *tkey, *tslot;
-    int *hist;                     // [256][REBUILD_SORT_BLOCKS]
+    int *hist;                     // [gridDim.x][256] digit counts of each block's chunk
     int *bsum;                     // [gridDim.x]
     uint32_t *mask;
     int *off, *count, *corner_band, *band_cell, *cstart, *ccount, *base_nbr;
@@ -156,7 +155,13 @@ __global__ void __launch_bounds__(REBUILD_THREADS) k_rebuild(RebuildArgs a) {
         a.Xtmp[i] = x;
         a.Xtmp[S + i] = y;
         a.Xtmp[2 * S + i] = z;
-        a.key[i] = (uint32_t)base_cell(a.L, x, y, z);
+        // sort key: the base cell's index within the solid's box (the same order as the cell
+        // index of the grid, on fewer bits)
+        const int bx = min(max((int)floorf(x), 0), a.L.nx - 2), by = min(max((int)floorf(y), 0), a.L.ny - 2),
+                  bz = min(max((int)floorf(z), 0), a.L.nz - 2);
+        const int kx = min(max(bx - a.klo[0], 0), a.kdim[0] - 1), ky = min(max(by - a.klo[1], 0), a.kdim[1] - 1),
+                  kz = min(max(bz - a.klo[2], 0), a.kdim[2] - 1);
+        a.key[i] = (uint32_t)(kx + a.kdim[0] * (ky + a.kdim[1] * kz));
         a.slot[i] = (uint32_t)i;
     }
     for (long long w = tid; w < a.ntiles; w += nthr) a.mask[w] = 0u;
@@ -166,38 +171,35 @@ __global__ void __launch_bounds__(REBUILD_THREADS) k_rebuild(RebuildArgs a) {
     // stable radix sort of (key, slot) by 8-bit digits
     __shared__ int cnt[256];
     __shared__ int wcnt[REBUILD_THREADS / 32][256];
-    const int SB = REBUILD_SORT_BLOCKS;
+    const int SB = gridDim.x;
     const long long chunk = (S + SB - 1) / SB;
     uint32_t *ka = a.key, *va = a.slot, *kb = a.tkey, *vb = a.tslot;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int shift = 0; shift < a.bits; shift += 8) {
-        const bool sorter = blockIdx.x < SB;
-        const long long c0 = blockIdx.x * chunk, c1 = c0 + chunk < S ? c0 + chunk : S;
-        if (sorter) {
-            cnt[threadIdx.x] = 0;
-            __syncthreads();
-            for (long long e = c0 + threadIdx.x; e < c1; e += blockDim.x) atomicAdd(&cnt[(ka[e] >> shift) & 255u], 1);
-            __syncthreads();
-            a.hist[threadIdx.x * SB + blockIdx.x] = cnt[threadIdx.x];
-        }
+        const long long c0 = blockIdx.x * chunk < S ? blockIdx.x * chunk : S;
+        const long long c1 = c0 + chunk < S ? c0 + chunk : S;
+        cnt[threadIdx.x] = 0;
+        __syncthreads();
+        for (long long e = c0 + threadIdx.x; e < c1; e += blockDim.x) atomicAdd(&cnt[(ka[e] >> shift) & 255u], 1);
+        __syncthreads();
+        a.hist[(long long)blockIdx.x * 256 + threadIdx.x] = cnt[threadIdx.x];
         grid.sync();
-        if (blockIdx.x == 0) {
-            // exclusive scan of the digit-major histogram: thread d owns digit d's SB entries
-            long long local = 0;
-            for (int g = 0; g < SB; ++g) local += a.hist[threadIdx.x * SB + g];
-            long long total;
-            long long run = block_exclusive(local, &total);
+        {
+            // start of digit d in this chunk: all keys of smaller digits, plus digit d's keys of
+            // the chunks before this one (thread d reads every chunk's count of digit d)
+            long long before = 0, tot = 0;
             for (int g = 0; g < SB; ++g) {
-                const int c = a.hist[threadIdx.x * SB + g];
-                a.hist[threadIdx.x * SB + g] = (int)run;
-                run += c;
+                const int c = a.hist[(long long)g * 256 + threadIdx.x];
+                if (g < (int)blockIdx.x) before += c;
+                tot += c;
             }
-        }
-        grid.sync();
-        if (sorter) {
-            // running start of each digit for this chunk, tile by tile in (warp, item, lane) order
-            cnt[threadIdx.x] = a.hist[threadIdx.x * SB + blockIdx.x];
+            long long all;
+            const long long start = block_exclusive(tot, &all);
+            cnt[threadIdx.x] = (int)(start + before);
             __syncthreads();
+        }
+        {
+            // running start of each digit for this chunk, tile by tile in (warp, item, lane) order
             const uint32_t lt = (1u << lane) - 1u;
             for (long long t0 = c0; t0 < c1; t0 += SORT_TILE) {
                 for (int k = threadIdx.x; k < (REBUILD_THREADS / 32) * 256; k += blockDim.x) (&wcnt[0][0])[k] = 0;
@@ -307,7 +309,8 @@ __global__ void __launch_bounds__(REBUILD_THREADS) k_rebuild(RebuildArgs a) {
         }
     }
     grid.sync();
-    // corner band indices and band cells
+    // corner band indices and band cells; the first sample of each run of equal base cells (sorted
+    // keys) records the run's start and length at its base cell's band node
     for (long long j = tid; j < S; j += nthr) {
         const long long b = base_cell(a.L, a.X[j], a.X[S + j], a.X[2 * S + j]);
 #pragma unroll
@@ -316,17 +319,14 @@ __global__ void __launch_bounds__(REBUILD_THREADS) k_rebuild(RebuildArgs a) {
             const int bi = band_index(a.mask, a.off, cell);
             a.corner_band[c * S + j] = bi;
             a.band_cell[bi] = (int)cell;
+            if (c == 0 && (j == 0 || ka[j - 1] != ka[j])) {
+                long long k = j;
+                while (k + 1 < S && ka[k + 1] == ka[j]) ++k;
+                a.cstart[bi] = (int)j;
+                a.ccount[bi] = (int)(k - j + 1);
+            }
         }
     }
-    grid.sync();
-    for (long long j = tid; j < S; j += nthr)
-        if (j == 0 || ka[j - 1] != ka[j]) a.cstart[a.corner_band[j]] = (int)j;
-    grid.sync();
-    for (long long j = tid; j < S; j += nthr)
-        if (j == S - 1 || ka[j + 1] != ka[j]) {
-            const int bi = a.corner_band[j];
-            a.ccount[bi] = (int)(j - a.cstart[bi] + 1);
-        }
     grid.sync();
     // spreading lists: for every band node, the band node of each of its 8 lower neighbours that
     // is the base of at least one sample
@@ -396,7 +396,7 @@ struct MotionWs {
 int motion_ws(lbm_ctx *h, MotionWs &w) {
     const long long S = h->S;
     const size_t pw = lbm::al256((size_t)4 * S);
-    const size_t need = 4 * pw + lbm::al256(sizeof(int) * ((size_t)256 * lbm::REBUILD_SORT_BLOCKS + lbm::REBUILD_THREADS));
+    const size_t need = 4 * pw + lbm::al256(sizeof(int) * ((size_t)256 * lbm::REBUILD_THREADS + lbm::REBUILD_THREADS));
     if (need > h->motion_ws_bytes) {
         if (h->motion_ws) cudaFree(h->motion_ws);
         h->motion_ws = nullptr;
@@ -458,7 +458,16 @@ int rebuild(lbm_ctx *h, long long abs_t) {
         a.S = S;
         a.ntiles = h->ntiles;
         a.stride = h->nband;
-        a.bits = lbm::bits_for(h->N);
+        // base cells within r_max of the centre, one cell of margin (the samples are FP32 roundings)
+        long long box = 1;
+        for (int k = 0; k < 3; ++k) {
+            const int lo = std::max(0, (int)std::floor(p.c[k] - h->r_max) - 1);
+            const int hi = std::min(n[k] - 2, (int)std::floor(p.c[k] + h->r_max) + 1);
+            a.klo[k] = lo;
+            a.kdim[k] = std::max(1, hi - lo + 1);
+            box *= a.kdim[k];
+        }
+        a.bits = lbm::bits_for(box);
         a.p = p;
         a.L = L;
         a.rel = h->X0;
@@ -475,7 +484,7 @@ int rebuild(lbm_ctx *h, long long abs_t) {
         a.tkey = w.tkey;
         a.tslot = w.tslot;
         a.hist = static_cast<int *>(w.sort);
-        a.bsum = a.hist + 256 * lbm::REBUILD_SORT_BLOCKS;
+        a.bsum = a.hist + 256 * lbm::REBUILD_THREADS;
         a.mask = h->tile_mask;
         a.off = h->tile_off;
         a.count = h->band_count_dev;
