@@ -51,6 +51,9 @@ struct lbm_ctx {
     double r_max = 0.0;             // largest |X0 - c0| of the reference samples
     long long posed_tau0 = 0;       // step count at lbm_set_motion (the reference pose's time)
     long long posed_tau = -1;       // time of the pose the band was last built for
+    // bitmap words [mask_w0, mask_w1) that can hold band bits of the last rebuild (all words
+    // until the first one)
+    long long mask_w0 = 0, mask_w1 = -1;
     int *band_count_dev = nullptr;
     float *X0 = nullptr, *X0_alt = nullptr, *area_alt = nullptr, *Xtmp = nullptr;
     int *sid = nullptr, *sid_alt = nullptr;
@@ -394,6 +397,8 @@ inline void free_solid(lbm_ctx *h) {
     h->ib_overlap = false;
     h->posed_tau = -1;
     h->S = h->nband = h->ntiles = 0;
+    h->mask_w0 = 0;
+    h->mask_w1 = -1;
     h->order.clear();
 }
 

@@ -102,6 +102,8 @@ constexpr int REBUILD_THREADS = 256;   // also the largest grid (one block scans
 
 struct RebuildArgs {
     long long S, ntiles, stride;   // samples, bitmap words, band array stride
+    long long clr0, clr1;          // bitmap words cleared: those the last rebuild or this one can set
+    long long scan0, scan1;        // bitmap words this rebuild can set (offsets and band count)
     int bits;                      // significant bits of the keys
     int klo[3], kdim[3];           // box of the base cells the solid can reach: origin, sizes
     Pose p;
@@ -164,7 +166,7 @@ __global__ void __launch_bounds__(REBUILD_THREADS) k_rebuild(RebuildArgs a) {
         a.key[i] = (uint32_t)(kx + a.kdim[0] * (ky + a.kdim[1] * kz));
         a.slot[i] = (uint32_t)i;
     }
-    for (long long w = tid; w < a.ntiles; w += nthr) a.mask[w] = 0u;
+    for (long long w = a.clr0 + tid; w < a.clr1; w += nthr) a.mask[w] = 0u;
     for (long long k = tid; k < a.stride; k += nthr) a.ccount[k] = 0;
     grid.sync();
 
@@ -280,10 +282,13 @@ __global__ void __launch_bounds__(REBUILD_THREADS) k_rebuild(RebuildArgs a) {
         }
     }
     grid.sync();
-    // offsets of the bitmap words (exclusive scan of their popcounts) over contiguous chunks
+    // offsets of the bitmap words (exclusive scan of their popcounts) over contiguous chunks of
+    // the words this rebuild can set (the others are zero: their offsets are never read)
     {
-        const long long wchunk = (a.ntiles + gridDim.x - 1) / gridDim.x;
-        const long long w0 = blockIdx.x * wchunk, w1 = w0 + wchunk < a.ntiles ? w0 + wchunk : a.ntiles;
+        const long long nw = a.scan1 - a.scan0;
+        const long long wchunk = (nw + gridDim.x - 1) / gridDim.x;
+        const long long w0 = a.scan0 + (blockIdx.x * wchunk < nw ? blockIdx.x * wchunk : nw);
+        const long long w1 = w0 + wchunk < a.scan1 ? w0 + wchunk : a.scan1;
         const long long per = (wchunk + blockDim.x - 1) / blockDim.x;
         const long long t0 = w0 + threadIdx.x * per, t1 = t0 + per < w1 ? t0 + per : w1;
         long long local = 0;
@@ -468,6 +473,14 @@ int rebuild(lbm_ctx *h, long long abs_t) {
             box *= a.kdim[k];
         }
         a.bits = lbm::bits_for(box);
+        // bitmap words of the box's band cells (base cells and their +1 corners)
+        const long long c0 = a.klo[0] + (long long)h->nx * (a.klo[1] + (long long)h->ny * a.klo[2]);
+        const long long c1 = (a.klo[0] + a.kdim[0]) + (long long)h->nx * ((a.klo[1] + a.kdim[1]) +
+                                                                          (long long)h->ny * (a.klo[2] + a.kdim[2]));
+        a.scan0 = c0 >> 5;
+        a.scan1 = std::min(h->ntiles, (c1 >> 5) + 1);
+        a.clr0 = h->mask_w1 < 0 ? 0 : std::min(h->mask_w0, a.scan0);
+        a.clr1 = h->mask_w1 < 0 ? h->ntiles : std::max(h->mask_w1, a.scan1);
         a.p = p;
         a.L = L;
         a.rel = h->X0;
@@ -499,6 +512,8 @@ int rebuild(lbm_ctx *h, long long abs_t) {
         std::swap(h->X0, h->X0_alt);
         std::swap(h->area, h->area_alt);
         std::swap(h->sid, h->sid_alt);
+        h->mask_w0 = a.scan0;
+        h->mask_w1 = a.scan1;
     }
     h->posed_tau = abs_t;
     return LBM_OK;
