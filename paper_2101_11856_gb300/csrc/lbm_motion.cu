@@ -170,6 +170,47 @@ __global__ void __launch_bounds__(REBUILD_THREADS) k_rebuild(RebuildArgs a) {
     for (long long k = tid; k < a.stride; k += nthr) a.ccount[k] = 0;
     grid.sync();
 
+    // The band bitmap's marks (from the unsorted positions) and its offset scan (an exclusive
+    // scan of the words' popcounts over contiguous chunks of the words this rebuild can set; the
+    // others are zero and their offsets are never read) ride along the sort's phases: marks in
+    // the first histogram phase, then one scan stage per phase; grid-wide barriers separate the
+    // stages.  Stages: 0 = block partial sums, 1 = block 0 scans them (and the band count), 2 =
+    // offsets written.
+    const long long nw = a.scan1 - a.scan0;
+    const long long wchunk = (nw + gridDim.x - 1) / gridDim.x;
+    const long long w0 = a.scan0 + (blockIdx.x * wchunk < nw ? blockIdx.x * wchunk : nw);
+    const long long w1 = w0 + wchunk < a.scan1 ? w0 + wchunk : a.scan1;
+    const long long per = (wchunk + blockDim.x - 1) / blockDim.x;
+    const long long t0w = w0 + threadIdx.x * per, t1w = t0w + per < w1 ? t0w + per : w1;
+    long long sbefore = 0;   // this thread's words' offset within the block
+    int scan_stage = 0;
+    auto scan_step = [&]() {
+        if (scan_stage == 0) {
+            long long local = 0;
+            for (long long w = t0w; w < t1w; ++w) local += __popc(a.mask[w]);
+            long long total;
+            sbefore = block_exclusive(local, &total);
+            if (threadIdx.x == 0) a.bsum[blockIdx.x] = (int)total;
+        } else if (scan_stage == 1) {
+            if (blockIdx.x == 0) {
+                const long long v = threadIdx.x < gridDim.x ? a.bsum[threadIdx.x] : 0;
+                long long all;
+                // gridDim.x <= REBUILD_THREADS (checked on the host)
+                const long long ex = block_exclusive(v, &all);
+                __syncthreads();
+                if (threadIdx.x < gridDim.x) a.bsum[threadIdx.x] = (int)ex;
+                if (threadIdx.x == 0) *a.count = (int)all;
+            }
+        } else if (scan_stage == 2) {
+            long long run = a.bsum[blockIdx.x] + sbefore;
+            for (long long w = t0w; w < t1w; ++w) {
+                a.off[w] = (int)run;
+                run += __popc(a.mask[w]);
+            }
+        }
+        ++scan_stage;
+    };
+
     // stable radix sort of (key, slot) by 8-bit digits
     __shared__ int cnt[256];
     __shared__ int wcnt[REBUILD_THREADS / 32][256];
@@ -185,6 +226,19 @@ __global__ void __launch_bounds__(REBUILD_THREADS) k_rebuild(RebuildArgs a) {
         for (long long e = c0 + threadIdx.x; e < c1; e += blockDim.x) atomicAdd(&cnt[(ka[e] >> shift) & 255u], 1);
         __syncthreads();
         a.hist[(long long)blockIdx.x * 256 + threadIdx.x] = cnt[threadIdx.x];
+        if (shift == 0) {
+            // band bitmap: the 8 corner cells of every sample's base cell
+            for (long long j = tid; j < S; j += nthr) {
+                const long long b = base_cell(a.L, a.Xtmp[j], a.Xtmp[S + j], a.Xtmp[2 * S + j]);
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    const long long cell = corner_cell(a.L, b, c);
+                    atomicOr(&a.mask[cell >> 5], 1u << (cell & 31));
+                }
+            }
+        } else if (scan_stage == 1) {
+            scan_step();
+        }
         grid.sync();
         {
             // start of digit d in this chunk: all keys of smaller digits, plus digit d's keys of
@@ -248,12 +302,18 @@ __global__ void __launch_bounds__(REBUILD_THREADS) k_rebuild(RebuildArgs a) {
                 __syncthreads();
             }
         }
+        if (scan_stage == 0 || scan_stage == 2) scan_step();
         grid.sync();
         uint32_t *t = ka; ka = kb; kb = t;
         t = va; va = vb; vb = t;
     }
+    while (scan_stage < 3) {   // fewer than two sort passes
+        scan_step();
+        grid.sync();
+    }
 
-    // samples in sorted order, rigid-body boundary velocities
+    // samples in sorted order, rigid-body boundary velocities; then (the same thread, the same
+    // sample) the corner band indices
     for (long long j = tid; j < S; j += nthr) {
         const long long i = va[j];
         double P[3];
@@ -271,49 +331,6 @@ __global__ void __launch_bounds__(REBUILD_THREADS) k_rebuild(RebuildArgs a) {
         a.area_o[j] = a.area_in[i];
         a.sid_o[j] = a.sid_in[i];
     }
-    grid.sync();
-    // band bitmap
-    for (long long j = tid; j < S; j += nthr) {
-        const long long b = base_cell(a.L, a.X[j], a.X[S + j], a.X[2 * S + j]);
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            const long long cell = corner_cell(a.L, b, c);
-            atomicOr(&a.mask[cell >> 5], 1u << (cell & 31));
-        }
-    }
-    grid.sync();
-    // offsets of the bitmap words (exclusive scan of their popcounts) over contiguous chunks of
-    // the words this rebuild can set (the others are zero: their offsets are never read)
-    {
-        const long long nw = a.scan1 - a.scan0;
-        const long long wchunk = (nw + gridDim.x - 1) / gridDim.x;
-        const long long w0 = a.scan0 + (blockIdx.x * wchunk < nw ? blockIdx.x * wchunk : nw);
-        const long long w1 = w0 + wchunk < a.scan1 ? w0 + wchunk : a.scan1;
-        const long long per = (wchunk + blockDim.x - 1) / blockDim.x;
-        const long long t0 = w0 + threadIdx.x * per, t1 = t0 + per < w1 ? t0 + per : w1;
-        long long local = 0;
-        for (long long w = t0; w < t1; ++w) local += __popc(a.mask[w]);
-        long long total;
-        const long long before = block_exclusive(local, &total);
-        if (threadIdx.x == 0) a.bsum[blockIdx.x] = (int)total;
-        grid.sync();
-        if (blockIdx.x == 0) {
-            const long long v = threadIdx.x < gridDim.x ? a.bsum[threadIdx.x] : 0;
-            long long all;
-            // gridDim.x <= REBUILD_THREADS (checked on the host)
-            const long long ex = block_exclusive(v, &all);
-            __syncthreads();
-            if (threadIdx.x < gridDim.x) a.bsum[threadIdx.x] = (int)ex;
-            if (threadIdx.x == 0) *a.count = (int)all;
-        }
-        grid.sync();
-        long long run = a.bsum[blockIdx.x] + before;
-        for (long long w = t0; w < t1; ++w) {
-            a.off[w] = (int)run;
-            run += __popc(a.mask[w]);
-        }
-    }
-    grid.sync();
     // corner band indices and band cells; the first sample of each run of equal base cells (sorted
     // keys) records the run's start and length at its base cell's band node
     for (long long j = tid; j < S; j += nthr) {
