@@ -94,11 +94,12 @@ __global__ void __launch_bounds__(256) k_rel(long long S, const float *__restric
 // Phases of one kernel whose blocks are all resident (cooperative launch) and meet at grid-wide
 // barriers between the phases: pose and
 // keys (with the bitmap and run counters cleared), a stable LSD radix sort of the keys (8-bit
-// digits; every block sorts a contiguous chunk, so the order within a digit is the input order,
-// as in sort_pairs), the samples gathered in sorted order, the band bitmap, its prefix offsets and
+// digits; the first REBUILD_SORT_BLOCKS blocks sort contiguous chunks, so the order within a
+// digit is the input order, as in sort_pairs), the samples gathered in sorted order, the band bitmap, its prefix offsets and
 // the band count, the corner band indices, band cells and the runs of samples per base cell, and
 // the spreading lists (the structures lbm_set_solids builds on the host for a static solid).
 constexpr int REBUILD_THREADS = 256;   // also the largest grid (one block scans the block sums)
+constexpr int REBUILD_SORT_BLOCKS = 32;   // blocks that sort (at most the grid; 16, 64 and all measured slower)
 
 struct RebuildArgs {
     long long S, ntiles, stride;   // samples, bitmap words, band array stride
@@ -214,18 +215,21 @@ __global__ void __launch_bounds__(REBUILD_THREADS) k_rebuild(RebuildArgs a) {
     // stable radix sort of (key, slot) by 8-bit digits
     __shared__ int cnt[256];
     __shared__ int wcnt[REBUILD_THREADS / 32][256];
-    const int SB = gridDim.x;
+    const int SB = (int)gridDim.x < REBUILD_SORT_BLOCKS ? (int)gridDim.x : REBUILD_SORT_BLOCKS;
+    const bool sorter = (int)blockIdx.x < SB;
     const long long chunk = (S + SB - 1) / SB;
     uint32_t *ka = a.key, *va = a.slot, *kb = a.tkey, *vb = a.tslot;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int shift = 0; shift < a.bits; shift += 8) {
-        const long long c0 = blockIdx.x * chunk < S ? blockIdx.x * chunk : S;
+        const long long c0 = sorter && blockIdx.x * chunk < S ? blockIdx.x * chunk : S;
         const long long c1 = c0 + chunk < S ? c0 + chunk : S;
-        cnt[threadIdx.x] = 0;
-        __syncthreads();
-        for (long long e = c0 + threadIdx.x; e < c1; e += blockDim.x) atomicAdd(&cnt[(ka[e] >> shift) & 255u], 1);
-        __syncthreads();
-        a.hist[(long long)blockIdx.x * 256 + threadIdx.x] = cnt[threadIdx.x];
+        if (sorter) {
+            cnt[threadIdx.x] = 0;
+            __syncthreads();
+            for (long long e = c0 + threadIdx.x; e < c1; e += blockDim.x) atomicAdd(&cnt[(ka[e] >> shift) & 255u], 1);
+            __syncthreads();
+            a.hist[(long long)blockIdx.x * 256 + threadIdx.x] = cnt[threadIdx.x];
+        }
         if (shift == 0) {
             // band bitmap: the 8 corner cells of every sample's base cell
             for (long long j = tid; j < S; j += nthr) {
@@ -240,7 +244,7 @@ __global__ void __launch_bounds__(REBUILD_THREADS) k_rebuild(RebuildArgs a) {
             scan_step();
         }
         grid.sync();
-        {
+        if (sorter) {
             // start of digit d in this chunk: all keys of smaller digits, plus digit d's keys of
             // the chunks before this one (thread d reads every chunk's count of digit d)
             long long before = 0, tot = 0;
@@ -254,7 +258,7 @@ __global__ void __launch_bounds__(REBUILD_THREADS) k_rebuild(RebuildArgs a) {
             cnt[threadIdx.x] = (int)(start + before);
             __syncthreads();
         }
-        {
+        if (sorter) {
             // running start of each digit for this chunk, tile by tile in (warp, item, lane) order
             const uint32_t lt = (1u << lane) - 1u;
             for (long long t0 = c0; t0 < c1; t0 += SORT_TILE) {
