@@ -95,9 +95,10 @@ __global__ void __launch_bounds__(256) k_rel(long long S, const float *__restric
 // barriers between the phases: pose and
 // keys (with the bitmap and run counters cleared), a stable LSD radix sort of the keys (8-bit
 // digits; the first REBUILD_SORT_BLOCKS blocks sort contiguous chunks, so the order within a
-// digit is the input order, as in sort_pairs), the samples gathered in sorted order, the band bitmap, its prefix offsets and
-// the band count, the corner band indices, band cells and the runs of samples per base cell, and
-// the spreading lists (the structures lbm_set_solids builds on the host for a static solid).
+// digit is the input order, as in sort_pairs), the samples gathered in sorted order, the band
+// bitmap, its prefix offsets and the band count, the corner band indices, band cells and the runs
+// of samples per base cell, and the spreading lists (the structures lbm_set_solids builds on the
+// host for a static solid).
 constexpr int REBUILD_THREADS = 256;   // also the largest grid (one block scans the block sums)
 constexpr int REBUILD_SORT_BLOCKS = 32;   // blocks that sort (at most the grid; 16, 64 and all measured slower)
 
