@@ -621,6 +621,9 @@ extern "C" int lbm_adjoint(lbm_ctx *h, int n, int K, const lbm_loss *loss, doubl
         return rc;
     float *g_last = nullptr, *F_last = nullptr;     // IB diagnostics of the last step, restored at the end
     if (S > 0 && ((rc = B.get(h, &g_last, (size_t)3 * S)) || (rc = B.get(h, &F_last, (size_t)3 * nb)))) return rc;
+    // cell sums of the IB stages the backward stream runs, apart from those of the recompute beside it
+    float *cellS_b = nullptr;
+    if (h->nocc > 0 && (rc = B.get(h, &cellS_b, (size_t)24 * h->nocc))) return rc;
     // Segment sets: the states f_{t0 + k} of a segment and the IB values of its recomputed steps
     // (slot j: the step from state t0 + j; the last step of a segment keeps none).  With two sets
     // the recompute of segment s - 1 runs on a second stream beside the backward pass of segment
@@ -800,9 +803,9 @@ extern "C" int lbm_adjoint(lbm_ctx *h, int n, int K, const lbm_loss *loss, doubl
             const bool nbp = (t & 1) != 0;
             if (S > 0) {
                 if (!kept) {
-                    CK(launch_band_moments(h->storage, P, h->band_cell, h->band_rho, h->band_u, bs));
-                    CK(launch_ib_interp(P, S, h->X, h->area, h->ub_zero ? nullptr : h->ub, h->band_rho, h->band_u, h->g, bs));
-                    CK(launch_ib_spread(S, nb, nullptr, h->X, h->g, h->base_nbr, h->cstart, h->ccount, h->bandF, bs));
+                    // the forward step's IB values, recomputed by the same kernels
+                    const int r = ib_stage(h, P, bs, cellS_b);
+                    if (r) return r;
                 }
                 CK(with_storage(h->storage, [&](auto tag) {
                     using St = decltype(tag);

@@ -26,10 +26,21 @@ int fail(lbm_ctx *h, int code, const std::string &msg) {
     return code;
 }
 
-// the three immersed-boundary kernels of step P.t on stream st
-int ib_stage(lbm_ctx *h, const StepParams &P, cudaStream_t st) {
+// the three immersed-boundary kernels of step P.t on stream st: band moments, then for a static
+// solid the two-phase interpolation / spreading over the occupied base cells and the band nodes
+// (cellS: the cells' per-corner sums, the context's buffer when NULL; work queued on two streams
+// at once needs one buffer each), for a moving one (band rebuilt on the device every step) per
+// sample and per band node
+int ib_stage(lbm_ctx *h, const StepParams &P, cudaStream_t st, float *cellS) {
+    if (!cellS) cellS = h->cellS;
     { Timed tm(h, LBM_KERNEL_BAND, 1, st); CK(launch_band_moments(h->storage, P, h->band_cell, h->band_rho, h->band_u, st)); }
-    { Timed tm(h, LBM_KERNEL_INTERP, 1, st); CK(launch_ib_interp(P, h->S, h->X, h->area, h->ub_zero ? nullptr : h->ub, h->band_rho, h->band_u, h->g, st)); }
+    const float *ub = h->ub_zero ? nullptr : h->ub;
+    if (h->nocc > 0 && !h->band_count_dev) {
+        { Timed tm(h, LBM_KERNEL_INTERP, 1, st); CK(launch_ib_cells(P, h->S, h->nocc, h->occ_bi, h->band_cell, h->cstart, h->ccount, h->X, h->area, ub, h->band_rho, h->band_u, h->g, cellS, st)); }
+        { Timed tm(h, LBM_KERNEL_SPREAD, 1, st); CK(launch_ib_gather(h->nband, h->nocc, h->occ_nbr, cellS, h->bandF, st)); }
+        return LBM_OK;
+    }
+    { Timed tm(h, LBM_KERNEL_INTERP, 1, st); CK(launch_ib_interp(P, h->S, h->X, h->area, ub, h->band_rho, h->band_u, h->g, st)); }
     { Timed tm(h, LBM_KERNEL_SPREAD, 1, st); CK(launch_ib_spread(h->S, h->nband, h->band_count_dev, h->X, h->g, h->base_nbr, h->cstart, h->ccount, h->bandF, st)); }
     return LBM_OK;
 }
@@ -376,6 +387,15 @@ int lbm_set_solids(lbm_ctx *h, const float *samples, long long count, const floa
             bnbr[(size_t)c * nb + k] = v;
         }
     }
+    // occupied base cells (ascending band index = sample order) and their index per band node corner
+    std::vector<int> obi, onbr((size_t)8 * nb, -1), occ_of(nb, -1);
+    for (long long k = 0; k < nb; ++k)
+        if (ccnt[k] > 0) {
+            occ_of[k] = (int)obi.size();
+            obi.push_back((int)k);
+        }
+    for (size_t e = 0; e < (size_t)8 * nb; ++e)
+        if (bnbr[e] >= 0) onbr[e] = occ_of[bnbr[e]];
     std::vector<int> cb((size_t)8 * S);
     std::vector<float> Xs(3 * S), As(S), Us(3 * S);
     for (size_t i = 0; i < S; ++i) {
@@ -399,16 +419,19 @@ int lbm_set_solids(lbm_ctx *h, const float *samples, long long count, const floa
         return x >= XEDGE && x < h->nx - XEDGE;
     });
     h->ntiles = ntiles;
+    h->nocc = (long long)obi.size();
     h->order = ord;
     if ((rc = upload(h, &h->X, Xs)) || (rc = upload(h, &h->area, As)) || (rc = upload(h, &h->ub, Us)) ||
         (rc = upload(h, &h->corner_band, cb)) || (rc = upload(h, &h->band_cell, bcell)) ||
         (rc = upload(h, &h->base_nbr, bnbr)) || (rc = upload(h, &h->cstart, cst)) || (rc = upload(h, &h->ccount, ccnt)) ||
-        (rc = upload(h, &h->tile_mask, mask)) || (rc = upload(h, &h->tile_off, toff))) {
+        (rc = upload(h, &h->tile_mask, mask)) || (rc = upload(h, &h->tile_off, toff)) ||
+        (rc = upload(h, &h->occ_bi, obi)) || (rc = upload(h, &h->occ_nbr, onbr))) {
         free_solid(h);
         return rc;
     }
     if ((rc = dev_alloc(h, &h->g, 3 * S)) || (rc = dev_alloc(h, &h->band_rho, (size_t)nb)) ||
-        (rc = dev_alloc(h, &h->band_u, (size_t)3 * nb)) || (rc = dev_alloc(h, &h->bandF, (size_t)3 * nb))) {
+        (rc = dev_alloc(h, &h->band_u, (size_t)3 * nb)) || (rc = dev_alloc(h, &h->bandF, (size_t)3 * nb)) ||
+        (rc = dev_alloc(h, &h->cellS, (size_t)24 * obi.size()))) {
         free_solid(h);
         return rc;
     }

@@ -39,6 +39,12 @@ struct lbm_ctx {
     int *corner_band = nullptr, *band_cell = nullptr, *base_nbr = nullptr, *cstart = nullptr, *ccount = nullptr;
     float *band_rho = nullptr, *band_u = nullptr, *bandF = nullptr;
     bool ub_zero = false;           // every boundary velocity is 0 (the interpolation skips ub)
+    // two-phase IB of a static solid: the occupied base cells (band index of each, ascending),
+    // the occupied-cell index of the base cell x_k - c of every band node ([8][nband], -1 if
+    // none) and the cells' per-corner force sums ([24][nocc])
+    long long nocc = 0;
+    int *occ_bi = nullptr, *occ_nbr = nullptr;
+    float *cellS = nullptr;
     uint32_t *tile_mask = nullptr;
     int *tile_off = nullptr;
     std::vector<long long> order;   // sorted position -> caller's sample index
@@ -265,6 +271,11 @@ inline void point_states(lbm::StepParams &P, const lbm_ctx *h, void *src, void *
 // destination; defined in lbm_api.cu
 int step_with(lbm_ctx *h, const lbm::StepParams &P);
 
+// the immersed-boundary stage of step P.t (band moments, interpolation and penalty, spreading)
+// on stream st, with the per-corner cell sums in cellS ([24][nocc] floats; NULL: the context's
+// buffer); defined in lbm_api.cu
+int ib_stage(lbm_ctx *h, const lbm::StepParams &P, cudaStream_t st, float *cellS = nullptr);
+
 // move the smoke tracers by one step in the velocity field the step wrote (lbm_tracers.cu)
 int advect_tracers(lbm_ctx *h, long long t);
 
@@ -386,6 +397,8 @@ inline void free_solid(lbm_ctx *h) {
     dev_free(h->cstart); dev_free(h->ccount);
     dev_free(h->band_rho); dev_free(h->band_u); dev_free(h->bandF);
     dev_free(h->tile_mask); dev_free(h->tile_off);
+    dev_free(h->occ_bi); dev_free(h->occ_nbr); dev_free(h->cellS);
+    h->nocc = 0;
     dev_free(h->band_count_dev);
     dev_free(h->X0); dev_free(h->X0_alt); dev_free(h->area_alt); dev_free(h->Xtmp);
     dev_free(h->sid); dev_free(h->sid_alt);

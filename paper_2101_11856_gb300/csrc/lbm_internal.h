@@ -64,6 +64,13 @@ cudaError_t launch_ib_interp(const StepParams &P, long long S, const float *X, c
 // count of band nodes (moving solids) or nullptr
 cudaError_t launch_ib_spread(long long S, long long nband, const int *count, const float *X, const float *g,
                              const int *base_nbr, const int *cstart, const int *ccount, float *bandF, cudaStream_t st);
+// two-phase immersed boundary of a static solid: per occupied base cell (interpolation, penalty,
+// the cell's per-corner force sums cellS [24][nocc]), then per band node (gather of those sums)
+cudaError_t launch_ib_cells(const StepParams &P, long long S, long long nocc, const int *occ_bi, const int *band_cell,
+                            const int *cstart, const int *ccount, const float *X, const float *area, const float *ub,
+                            const float *band_rho, const float *band_u, float *g, float *cellS, cudaStream_t st);
+cudaError_t launch_ib_gather(long long nband, long long nocc, const int *occ_nbr, const float *cellS, float *bandF,
+                             cudaStream_t st);
 int force_sum_blocks(long long S);
 // per-block force sums (force_sum_blocks(S) blocks); component k of block b at
 // partial[k * stride + b], stride = the block count when 0

@@ -255,6 +255,87 @@ __global__ void __launch_bounds__(256) k_ib_spread(long long S, long long nband,
     bandF[2 * nband + k] = fz;
 }
 
+// Two-phase immersed boundary of a static solid (Eqs. 6-8 in Algorithm 2's order).
+// Phase 1, one thread per occupied base cell i (band index occ_bi[i]): the cell's samples share
+// their 8 stencil nodes, so the thread reads those nodes' moments once, interpolates and forms the
+// penalty force of each sample with the arithmetic of k_ib_interp (the same g_s bit for bit), and
+// sums K_c g_s over its samples per corner c into cellS[3 c + a][i] (each sample's weights once).
+__global__ void __launch_bounds__(256) k_ib_cells(StepParams P, long long S, long long nocc, const int *__restrict__ occ_bi,
+                                                  const int *__restrict__ band_cell, const int *__restrict__ cstart,
+                                                  const int *__restrict__ ccount, const float *__restrict__ X,
+                                                  const float *__restrict__ area, const float *__restrict__ ub,
+                                                  const float *__restrict__ band_rho, const float *__restrict__ band_u,
+                                                  float *__restrict__ g, float *__restrict__ cellS) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nocc) return;
+    const long long nband = P.nband;
+    const int bi = occ_bi[i];
+    const long long base = band_cell[bi];
+    const int s0 = cstart[bi], s1 = s0 + ccount[bi];
+    float r[8], vx[8], vy[8], vz[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const long long cell = base + (c & 1) + ((c & 2) ? P.g.nx : 0) + ((c & 4) ? (long long)P.g.nxy : 0);
+        const int b = band_of(P, cell);
+        r[c] = band_rho[b];
+        vx[c] = band_u[b];
+        vy[c] = band_u[nband + b];
+        vz[c] = band_u[2 * nband + b];
+    }
+    float acc[24];
+#pragma unroll
+    for (int k = 0; k < 24; ++k) acc[k] = 0.0f;
+    for (int s = s0; s < s1; ++s) {
+        const float x = X[s], y = X[S + s], z = X[2 * S + s];
+        const float wx = x - floorf(x), wy = y - floorf(y), wz = z - floorf(z);
+        float rs = 0.0f, us = 0.0f, vs = 0.0f, ws = 0.0f;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const float K = corner_weight(c, wx, wy, wz);
+            rs = fmaf(K, r[c], rs);
+            us = fmaf(K, vx[c], us);
+            vs = fmaf(K, vy[c], vs);
+            ws = fmaf(K, vz[c], ws);
+        }
+        const float a = rs * area[s];
+        const float bx = ub ? ub[s] : 0.0f, by = ub ? ub[S + s] : 0.0f, bz = ub ? ub[2 * S + s] : 0.0f;
+        const float gx = a * (bx - us), gy = a * (by - vs), gz = a * (bz - ws);
+        g[s] = gx;
+        g[S + s] = gy;
+        g[2 * S + s] = gz;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const float K = corner_weight(c, wx, wy, wz);
+            acc[3 * c] = fmaf(K, gx, acc[3 * c]);
+            acc[3 * c + 1] = fmaf(K, gy, acc[3 * c + 1]);
+            acc[3 * c + 2] = fmaf(K, gz, acc[3 * c + 2]);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 24; ++k) cellS[k * nocc + i] = acc[k];
+}
+
+// Phase 2, one thread per band node k: the spread force (Eq. 8) is the sum over the 8 base cells
+// x_k - c (corner c of that cell is node k; occ_nbr[c][k] = its occupied-cell index or -1) of the
+// cells' corner-c sums, in corner order: a fixed order, no atomics.
+__global__ void __launch_bounds__(256) k_ib_gather(long long nband, long long nocc, const int *__restrict__ occ_nbr,
+                                                   const float *__restrict__ cellS, float *__restrict__ bandF) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nband) return;
+    float fx = 0.0f, fy = 0.0f, fz = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const int o = occ_nbr[(long long)c * nband + k];
+        if (o < 0) continue;
+        fx += cellS[(long long)(3 * c) * nocc + o];
+        fy += cellS[(long long)(3 * c + 1) * nocc + o];
+        fz += cellS[(long long)(3 * c + 2) * nocc + o];
+    }
+    bandF[k] = fx;
+    bandF[nband + k] = fy;
+    bandF[2 * nband + k] = fz;
+}
+
 // FP64 block partial sums of the penalty forces (drag = -sum g)
 // per-block FP64 sums of the three force components; component k of block b at
 // partial[k * stride + b]
@@ -393,6 +474,20 @@ cudaError_t launch_ib_interp(const StepParams &P, long long S, const float *X, c
 cudaError_t launch_ib_spread(long long S, long long nband, const int *count, const float *X, const float *g,
                              const int *base_nbr, const int *cstart, const int *ccount, float *bandF, cudaStream_t st) {
     k_ib_spread<<<blocks_for(nband, 256), 256, 0, st>>>(S, nband, count, X, g, base_nbr, cstart, ccount, bandF);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ib_cells(const StepParams &P, long long S, long long nocc, const int *occ_bi, const int *band_cell,
+                            const int *cstart, const int *ccount, const float *X, const float *area, const float *ub,
+                            const float *band_rho, const float *band_u, float *g, float *cellS, cudaStream_t st) {
+    k_ib_cells<<<blocks_for(nocc, 256), 256, 0, st>>>(P, S, nocc, occ_bi, band_cell, cstart, ccount, X, area, ub, band_rho,
+                                                      band_u, g, cellS);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ib_gather(long long nband, long long nocc, const int *occ_nbr, const float *cellS, float *bandF,
+                             cudaStream_t st) {
+    k_ib_gather<<<blocks_for(nband, 256), 256, 0, st>>>(nband, nocc, occ_nbr, cellS, bandF);
     return cudaGetLastError();
 }
 
