@@ -31,7 +31,7 @@ extern "C" {
 #define LBM_ENOMEM    -2   /* a device or host allocation failed                                      */
 #define LBM_ECUDA     -3   /* a CUDA runtime call failed                                              */
 #define LBM_EUNSTABLE -4   /* non-finite density or velocity detected by lbm_check                   */
-#define LBM_ETIMEOUT  -5   /* a host-side wait exceeded its wall-clock limit                         */
+#define LBM_ETIMEOUT  -5   /* a host-side wait exceeded its wall-clock limit, or a step kernel's bounded wait ran out */
 #define LBM_ESTATE    -6   /* called in the wrong state (e.g. step before set_state)                 */
 
 /* ---- population storage ---------------------------------------------------------- */
@@ -317,6 +317,19 @@ int lbm_tracer_density(lbm_ctx *h, int s, float *out);
  * context whose -x face is an inlet; takes effect from the next step (lbm_step, lbm_adjoint).
  * Errors: LBM_EINVAL (no inlet, NULL or non-finite coef), LBM_ENOMEM. */
 int lbm_set_inflow(lbm_ctx *h, const double coef[16]);
+
+/* Which kernel runs the main range of a step with 16-bit storage (LBM_STORE_F16 / _BF16), the
+ * method's collision and nx even.  bulk = 0 (the default): one node pair per thread, each thread
+ * loading its 27 pair values itself.  bulk = 1 (used when nx % 8 == 0): a persistent kernel in
+ * which one thread of each CTA issues tiled tensor copies (cp.async.bulk.tensor over a 4-D map
+ * (x, y, z, direction plane) of the population array, completion counted on an mbarrier) of a
+ * 240-node row tile's 27 source segments into a three-stage shared-memory ring, two tiles ahead of
+ * the threads that collide the node pairs from there; every wait for a copy is bounded (about a
+ * second of SM clocks), and a wait that runs out makes the next lbm_synchronize or lbm_check return
+ * LBM_ETIMEOUT.  Both give bit-identical results (the same values in the same FP32 arithmetic); on
+ * GB300 the first is faster (the second keeps 4 warps per CTA in step with its tiles).  Takes
+ * effect from the next step.  Errors: LBM_EINVAL for NULL h. */
+int lbm_set_pair_kernel(lbm_ctx *h, int bulk);
 
 /* Number of band nodes (nodes within the 2x2x2 stencil of a sample) of the solid. */
 long long lbm_band_size(const lbm_ctx *h);

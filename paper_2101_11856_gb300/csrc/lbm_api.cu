@@ -214,7 +214,14 @@ int lbm_create(lbm_ctx **out, int nx, int ny, int nz, double nu, const double fo
         }
     }
     if (upload_inflow(h) != LBM_OK) return bail(LBM_ENOMEM);
-    if (dev_alloc(h, &h->red, 8) != LBM_OK || dev_alloc(h, &h->flag, 1) != LBM_OK) return bail(LBM_ENOMEM);
+    if (dev_alloc(h, &h->red, 8) != LBM_OK || dev_alloc(h, &h->flag, 1) != LBM_OK ||
+        dev_alloc(h, &h->wait_err, 1) != LBM_OK)
+        return bail(LBM_ENOMEM);
+    if (cudaMemsetAsync(h->wait_err, 0, sizeof(int), h->stream) != cudaSuccess || cudaStreamSynchronize(h->stream) != cudaSuccess) {
+        cudaGetLastError();
+        h->err = "cudaMemsetAsync failed";
+        return bail(LBM_ECUDA);
+    }
     *out = h;
     return LBM_OK;
 }
@@ -233,6 +240,7 @@ int lbm_destroy(lbm_ctx *h) {
     dev_free(h->partial);
     dev_free(h->red);
     dev_free(h->flag);
+    dev_free(h->wait_err);
     for (auto &r : h->recs) {
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);
@@ -587,6 +595,12 @@ int lbm_velocity(int i, int c[3]) {
 
 long long lbm_time(const lbm_ctx *h) { return h ? h->t : -1; }
 
+int lbm_set_pair_kernel(lbm_ctx *h, int bulk) {
+    if (!h) return fail(nullptr, LBM_EINVAL, "null context");
+    h->pair_bulk = bulk != 0;
+    return LBM_OK;
+}
+
 int lbm_set_inflow(lbm_ctx *h, const double coef[16]) {
     if (!h) return fail(nullptr, LBM_EINVAL, "null context");
     if (!coef) return fail(h, LBM_EINVAL, "coef is NULL");
@@ -622,6 +636,16 @@ long long lbm_band_size(const lbm_ctx *h) {
     return n;
 }
 
+// LBM_ETIMEOUT when a step kernel's bounded device-side wait ran out since the last check (the
+// flag is cleared); call after the context's stream finished
+static int wait_error(lbm_ctx *h) {
+    int w = 0;
+    CK(cudaMemcpy(&w, h->wait_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (!w) return LBM_OK;
+    CK(cudaMemset(h->wait_err, 0, sizeof(int)));
+    return fail(h, LBM_ETIMEOUT, "a step kernel's wait for its asynchronous copies ran out; the state is invalid");
+}
+
 int lbm_check(lbm_ctx *h) {
     int rc = require_state(h);
     if (rc) return rc;
@@ -634,6 +658,7 @@ int lbm_check(lbm_ctx *h) {
     int bad = 0;
     CK(cudaMemcpyAsync(&bad, h->flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
+    if ((rc = wait_error(h))) return rc;
     if (bad) return fail(h, LBM_EUNSTABLE, "non-finite density or velocity at step " + std::to_string(h->t));
     return LBM_OK;
 }
@@ -675,7 +700,7 @@ int lbm_synchronize(lbm_ctx *h, double timeout_s) {
         std::this_thread::sleep_for(std::chrono::microseconds(50));
     }
     destroy();
-    return LBM_OK;
+    return wait_error(h);
 }
 
 // checkpoint layout: header (8 int64) | populations (27 planes of N elements) | outlet plane;

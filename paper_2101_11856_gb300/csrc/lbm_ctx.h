@@ -86,6 +86,11 @@ struct lbm_ctx {
     size_t partial_cap = 0;         // doubles
     double *red = nullptr;          // 8 doubles
     int *flag = nullptr;
+    // set by a step kernel whose bounded wait for its asynchronous copies ran out
+    int *wait_err = nullptr;
+    // 16-bit storage: the main range in the tensor-copy fed kernel (lbm_set_pair_kernel; off by
+    // default: measured slower than the register-fed pair kernel on GB300)
+    bool pair_bulk = false;
 
     // profiling
     bool prof = false;
@@ -251,6 +256,8 @@ inline lbm::StepParams make_params(const lbm_ctx *h, long long t) {
     P.bandF = h->bandF;
     P.nband = h->nband;
     P.band_count = h->band_count_dev;
+    P.pair_bulk = h->pair_bulk ? 1 : 0;
+    P.err = h->wait_err;
     return P;
 }
 

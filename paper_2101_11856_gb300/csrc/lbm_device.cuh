@@ -110,6 +110,9 @@ struct StepParams {
     float *u_out;                // [3][ncell] Guo-shifted velocity of the step, or nullptr
     int inner_rows;              // 1: the step kernels skip the rows on a y/z face (run by the
                                  // free-slip kernels of the same step)
+    int pair_bulk;               // 16-bit storage, node pairs: 1 = the tensor-copy fed main kernel
+                                 // (k_step_pair_tma, nx % 8 == 0), 0 = k_step_pair
+    int *err;                    // device flag set by a kernel whose bounded wait ran out
 };
 
 // ---- inlet noise: counter-based SplitMix64 (Steele, Lea, Flood 2014) ------------------

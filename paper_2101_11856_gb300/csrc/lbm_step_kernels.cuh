@@ -7,6 +7,7 @@
 
 #include "lbm_models.cuh"
 #include "lbm_step.cuh"
+#include "lbm_step_tma.cuh"
 
 namespace lbm {
 
@@ -209,7 +210,27 @@ cudaError_t launch_step_tt(const StepParams &P, int part, cudaStream_t st) {
         if constexpr (FS) {
             return cudaErrorInvalidValue;
         } else if constexpr (pair_storage<St, COLL>()) {
-            if (pair_grid(g)) {
+            CUtensorMap m27, m3;
+            if (pair_grid(g) && P.pair_bulk && g.nx % 8 == 0) {
+                // requested explicitly: a layout the tensor-map encoder refuses is an error, not a fallback
+                if (!encode_population_map(&m27, P.fp[0], g, 27) || !encode_population_map(&m3, P.fp[0], g, 3))
+                    return cudaErrorNotSupported;
+                // persistent, fed by tensor copies: as many CTAs as fit on the GPU at once
+                static int grid_max = 0;
+                if (!grid_max) {
+                    int dev = 0, sms = 0, per_sm = 0;
+                    cudaGetDevice(&dev);
+                    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+                    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_pair_tma<St, NB, BAND, VOUT>, TMA_THREADS,
+                                                                  TMA_SMEM);
+                    grid_max = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+                }
+                const long long tiles = tma_tiles(g, P.inner_rows).count;
+                if (tiles > 0) {
+                    const unsigned grid = (unsigned)(tiles < grid_max ? tiles : grid_max);
+                    k_step_pair_tma<St, NB, BAND, VOUT><<<grid, TMA_THREADS, TMA_SMEM, st>>>(m27, m3, P, P.err);
+                }
+            } else if (pair_grid(g)) {
                 // one-warp blocks: at 94-96 registers a 64-thread block leaves part of the SM's
                 // registers unused (10 blocks, 20 warps), one-warp blocks fit 21 (measured 0.7 % faster)
                 const int pairs = range / 2, pthreads = 32;

@@ -72,6 +72,7 @@ _SIGS = {
     "lbm_profile": (C.c_int, [C.c_void_p, C.c_int]),
     "lbm_kernel_times": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
     "lbm_band_size": (C.c_longlong, [C.c_void_p]),
+    "lbm_set_pair_kernel": (C.c_int, [C.c_void_p, C.c_int]),
     "lbm_solid_count": (C.c_longlong, [C.c_void_p]),
     "lbm_dims": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
     "lbm_set_inflow": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
@@ -279,6 +280,10 @@ def lbm_band_size(h):
     return library().lbm_band_size(h)
 
 
+def lbm_set_pair_kernel(h, bulk):
+    _check(library().lbm_set_pair_kernel(h, 1 if bulk else 0), h)
+
+
 def lbm_solid_count(h):
     return library().lbm_solid_count(h)
 
@@ -442,6 +447,10 @@ class Solver:
 
     def step(self, n=1):
         lbm_step(self.h, n)
+
+    def set_pair_kernel(self, bulk):
+        """16-bit storage: main range in the tensor-copy fed kernel (True) or one pair per thread (False, default)."""
+        lbm_set_pair_kernel(self.h, bulk)
 
     def macroscopic(self):
         """(rho (nz, ny, nx), u (3, nz, ny, nx)) as float32 numpy arrays."""
