@@ -228,6 +228,7 @@ struct AdjParams {
     int ke_x0, ke_x1;
     const float *ghost_in;       // [9][nyz] outlet ghost uses of step t + 1 (x-face kernel)
     float *ghost_out;            // [9][nyz] outlet ghost uses of this step
+    int row_y0, row_z0;          // k_adj_main covers the rows (row_y0 + blockIdx.y, row_z0 + blockIdx.z)
 };
 
 // lambda_t of node (x, y, z) as its own backward step uses it: at x = nx - 1 next to an outlet the
@@ -429,7 +430,7 @@ template <typename St, bool NB, bool BAND>
 __global__ void __launch_bounds__(STEP_BX, 12) k_adj_main(StepParams P, AdjParams A) {
     const int x = blockIdx.x * STEP_BX + threadIdx.x;
     if (x < 1 || x > P.g.nx - 2) return;
-    const int y = blockIdx.y, z = blockIdx.z;
+    const int y = blockIdx.y + A.row_y0, z = blockIdx.z + A.row_z0;
     const int cell = x + P.g.nx * (y + P.g.ny * z);
     const bool inner = y >= 1 && y <= P.g.ny - 2 && z >= 1 && z <= P.g.nz - 2;   // uniform per block
     float fs[27], lam[27];
@@ -571,18 +572,32 @@ struct AdjBuffers {
     }
 };
 
+// a block of rows (y, z) of the main backward kernel: y0 <= y < y0 + ny, z0 <= z < z0 + nz
+struct RowBox {
+    int y0, ny, z0, nz;
+};
+
+// the main backward kernel over the rows of box r (nothing for an empty box), then (xface) the
+// x-face kernel
 template <typename St, bool NB, bool BAND>
-cudaError_t launch_adj_step_tt(const StepParams &P, const AdjParams &A, cudaStream_t st) {
+cudaError_t launch_adj_step_tt(const StepParams &P, AdjParams A, const RowBox &r, bool xface, cudaStream_t st) {
     const Geometry &g = P.g;
-    k_adj_main<St, NB, BAND><<<dim3(nblocks(g.nx - 1, STEP_BX), g.ny, g.nz), STEP_BX, 0, st>>>(P, A);
-    k_adj_xface<St, NB, BAND><<<dim3(nblocks(g.nyz, 128), 2), 128, 0, st>>>(P, A);
+    if (r.ny > 0 && r.nz > 0) {
+        A.row_y0 = r.y0;
+        A.row_z0 = r.z0;
+        k_adj_main<St, NB, BAND><<<dim3(nblocks(g.nx - 1, STEP_BX), r.ny, r.nz), STEP_BX, 0, st>>>(P, A);
+    }
+    if (xface) k_adj_xface<St, NB, BAND><<<dim3(nblocks(g.nyz, 128), 2), 128, 0, st>>>(P, A);
     return cudaGetLastError();
 }
 
 template <typename St>
-cudaError_t launch_adj_step(const StepParams &P, const AdjParams &A, bool nb, bool band, cudaStream_t st) {
-    if (nb) return band ? launch_adj_step_tt<St, true, true>(P, A, st) : launch_adj_step_tt<St, true, false>(P, A, st);
-    return band ? launch_adj_step_tt<St, false, true>(P, A, st) : launch_adj_step_tt<St, false, false>(P, A, st);
+cudaError_t launch_adj_step(const StepParams &P, const AdjParams &A, bool nb, bool band, const RowBox &r, bool xface,
+                            cudaStream_t st) {
+    if (nb) return band ? launch_adj_step_tt<St, true, true>(P, A, r, xface, st)
+                        : launch_adj_step_tt<St, true, false>(P, A, r, xface, st);
+    return band ? launch_adj_step_tt<St, false, true>(P, A, r, xface, st)
+                : launch_adj_step_tt<St, false, false>(P, A, r, xface, st);
 }
 
 }  // namespace
@@ -696,12 +711,20 @@ extern "C" int lbm_adjoint(lbm_ctx *h, int n, int K, const lbm_loss *loss, doubl
     for (int i = 0; i < n; ++i) {
         const int sgi = i / K, k = i % K;
         const int len = std::min(K, n - sgi * K);
+        if (S > 0) {
+            // this step's per-block drag sums, launched right after its IB stage on that stage's stream
+            h->fsum = step_sums + (size_t)i * fblk;
+            h->fsum_stride = (long long)n * fblk;
+        }
         if (sgi < first_kept) {
             if (k == 0) {
                 CK(cudaMemcpyAsync(ckpt[sgi], h->f, pop_bytes, cudaMemcpyDeviceToDevice, st));
                 if (out_bytes) CK(cudaMemcpyAsync(ckpt[sgi] + pop_bytes, h->outlet, out_bytes, cudaMemcpyDeviceToDevice, st));
             }
-            if ((rc = lbm_step(h, 1))) return rc;
+            if ((rc = lbm_step(h, 1))) {
+                h->fsum = nullptr;
+                return rc;
+            }
         } else {
             SegSet &q = set_of(sgi);
             if (i == first_kept * K) {   // the context's state enters the first kept segment
@@ -715,9 +738,11 @@ extern "C" int lbm_adjoint(lbm_ctx *h, int n, int K, const lbm_loss *loss, doubl
             }
             // the segment's last step writes the next segment's first state, or the context's
             char *dst = inner ? q.f[k + 1] : (sgi + 1 < nck ? set_of(sgi + 1).f[0] : nullptr);
-            if ((rc = adj_forward_step(h, q.f[k], dst))) return rc;
+            if ((rc = adj_forward_step(h, q.f[k], dst))) {
+                h->fsum = nullptr;
+                return rc;
+            }
         }
-        if (S > 0) CK(launch_sum_forces(S, h->g, step_sums + (size_t)i * fblk, st, (long long)n * fblk));
     }
     if (S > 0) {
         k_finalize_add<<<1, 256, 0, st>>>(step_sums, (long long)n * fblk, 3, acc);
@@ -755,6 +780,46 @@ extern "C" int lbm_adjoint(lbm_ctx *h, int n, int K, const lbm_loss *loss, doubl
         }
         return LBM_OK;
     };
+
+    // The rows of the main backward kernel: the box of rows holding band nodes, which waits for the
+    // IB chain of each backward step (band forces, samples, band gather), and up to four boxes of
+    // rows around it, which run beside that chain on a stream of the highest priority.
+    RowBox band_box{0, h->ny, 0, h->nz}, free_box[4];
+    int nfree = 0;
+    // With no band node on an x face the x-face kernel needs no IB term either: it runs on a third
+    // stream of the highest priority beside both (xs), its blocks placed first as SMs free up.
+    struct FreeStream {
+        cudaStream_t s = nullptr, xs = nullptr;
+        cudaEvent_t fork = nullptr, joined = nullptr, xjoined = nullptr;
+        ~FreeStream() {
+            for (cudaStream_t q : {s, xs})
+                if (q) cudaStreamSynchronize(q);
+            for (cudaEvent_t e : {fork, joined, xjoined})
+                if (e) cudaEventDestroy(e);
+            for (cudaStream_t q : {s, xs})
+                if (q) cudaStreamDestroy(q);
+        }
+    } bfree;
+    if (S > 0 && h->band_y1 >= h->band_y0) {
+        const int y0 = h->band_y0, y1 = h->band_y1, z0 = h->band_z0, z1 = h->band_z1;
+        band_box = RowBox{y0, y1 - y0 + 1, z0, z1 - z0 + 1};
+        if (y0 > 0) free_box[nfree++] = RowBox{0, y0, 0, h->nz};
+        if (y1 < h->ny - 1) free_box[nfree++] = RowBox{y1 + 1, h->ny - 1 - y1, 0, h->nz};
+        if (z0 > 0) free_box[nfree++] = RowBox{y0, y1 - y0 + 1, 0, z0};
+        if (z1 < h->nz - 1) free_box[nfree++] = RowBox{y0, y1 - y0 + 1, z1 + 1, h->nz - 1 - z1};
+        if (nfree > 0) {
+            int lo = 0, hi = 0;
+            CK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+            CK(cudaStreamCreateWithPriority(&bfree.s, cudaStreamNonBlocking, hi));
+            CK(cudaEventCreateWithFlags(&bfree.fork, cudaEventDisableTiming));
+            CK(cudaEventCreateWithFlags(&bfree.joined, cudaEventDisableTiming));
+            if (h->band_x0 > 0 && h->band_x1 < h->nx - 1) {
+                CK(cudaStreamCreateWithPriority(&bfree.xs, cudaStreamNonBlocking, hi));
+                CK(cudaEventCreateWithFlags(&bfree.xjoined, cudaEventDisableTiming));
+            }
+        }
+    }
+    const RowBox no_rows{0, 0, 0, 0};
 
     // backward pass over the segments, last first; segment sgi uses set (nck - 1 - sgi) % nset
     float *lam_cur = lamA, *lam_prev = lamB;
@@ -801,6 +866,24 @@ extern "C" int lbm_adjoint(lbm_ctx *h, int n, int K, const lbm_loss *loss, doubl
             A.ghost_in = ghost + (size_t)((t + 1) & 1) * 9 * nyz;
             A.ghost_out = ghost + (size_t)(t & 1) * 9 * nyz;
             const bool nbp = (t & 1) != 0;
+            if (nfree > 0) {
+                // rows without band nodes: their backward step needs no IB term, so it starts at once
+                CK(cudaEventRecord(bfree.fork, bs));
+                if (bfree.xs) {
+                    CK(cudaStreamWaitEvent(bfree.xs, bfree.fork, 0));
+                    CK(with_storage(h->storage, [&](auto tag) {
+                        using St = decltype(tag);
+                        return launch_adj_step<St>(P, A, nbp, false, no_rows, true, bfree.xs);
+                    }));
+                    CK(cudaEventRecord(bfree.xjoined, bfree.xs));
+                }
+                CK(cudaStreamWaitEvent(bfree.s, bfree.fork, 0));
+                for (int r = 0; r < nfree; ++r)
+                    CK(with_storage(h->storage, [&](auto tag) {
+                        using St = decltype(tag);
+                        return launch_adj_step<St>(P, A, nbp, false, free_box[r], false, bfree.s);
+                    }));
+            }
             if (S > 0) {
                 if (!kept) {
                     // the forward step's IB values, recomputed by the same kernels
@@ -819,10 +902,22 @@ extern "C" int lbm_adjoint(lbm_ctx *h, int n, int K, const lbm_loss *loss, doubl
                                                                     adj_samp, h->band_rho, h->band_u, adj_band);
                 CK(cudaGetLastError());
             }
-            CK(with_storage(h->storage, [&](auto tag) {
-                using St = decltype(tag);
-                return launch_adj_step<St>(P, A, nbp, S > 0, bs);
-            }));
+            if (nfree > 0) {
+                // the band's rows read the IB chain's terms; the other rows run beside it (launched
+                // below on the band-free stream, which joins before the next step reads lambda)
+                CK(with_storage(h->storage, [&](auto tag) {
+                    using St = decltype(tag);
+                    return launch_adj_step<St>(P, A, nbp, true, band_box, !bfree.xs, bs);
+                }));
+                CK(cudaEventRecord(bfree.joined, bfree.s));
+                CK(cudaStreamWaitEvent(bs, bfree.joined, 0));
+                if (bfree.xs) CK(cudaStreamWaitEvent(bs, bfree.xjoined, 0));
+            } else {
+                CK(with_storage(h->storage, [&](auto tag) {
+                    using St = decltype(tag);
+                    return launch_adj_step<St>(P, A, nbp, S > 0, RowBox{0, h->ny, 0, h->nz}, true, bs);
+                }));
+            }
             std::swap(lam_cur, lam_prev);
         }
         if (nset == 2) CK(cudaEventRecord(side.free_[cur], bs));

@@ -45,6 +45,15 @@ int ib_stage(lbm_ctx *h, const StepParams &P, cudaStream_t st, float *cellS) {
     return LBM_OK;
 }
 
+// the per-block force sums a caller asked of this step (h->fsum), on the IB stage's stream
+static int step_force_sum(lbm_ctx *h, cudaStream_t st) {
+    if (!h->fsum) return LBM_OK;
+    double *out = h->fsum;
+    h->fsum = nullptr;
+    CK(launch_sum_forces(h->S, h->g, out, st, h->fsum_stride));
+    return LBM_OK;
+}
+
 int step_with(lbm_ctx *h, const StepParams &P) {
     const bool band = h->S > 0;
     int rc;
@@ -57,6 +66,7 @@ int step_with(lbm_ctx *h, const StepParams &P) {
         CK(cudaEventRecord(h->ib_in, h->stream));
         CK(cudaStreamWaitEvent(h->ibs, h->ib_in, 0));
         if ((rc = ib_stage(h, P, h->ibs))) return rc;
+        if ((rc = step_force_sum(h, h->ibs))) return rc;
         CK(cudaEventRecord(h->ib_done, h->ibs));
         {
             Timed tm(h, LBM_KERNEL_BOUNDARY, step_launches(P, STEP_STRIPS));
@@ -69,6 +79,7 @@ int step_with(lbm_ctx *h, const StepParams &P) {
         }
     } else {
         if (band && (rc = ib_stage(h, P, h->stream))) return rc;
+        if (band && (rc = step_force_sum(h, h->stream))) return rc;
         Timed tm(h, LBM_KERNEL_BOUNDARY, step_launches(P, STEP_BOUNDARY));
         CK(launch_step(h->storage, P, band, STEP_BOUNDARY, h->cfg.collision, h->stream));
     }
@@ -426,6 +437,14 @@ int lbm_set_solids(lbm_ctx *h, const float *samples, long long count, const floa
         const int x = c % h->nx;
         return x >= XEDGE && x < h->nx - XEDGE;
     });
+    h->band_y0 = h->ny; h->band_y1 = -1; h->band_z0 = h->nz; h->band_z1 = -1;
+    h->band_x0 = h->nx; h->band_x1 = -1;
+    for (const int c : bcell) {
+        const int y = (int)((c / h->nx) % h->ny), z = (int)(c / ((long long)h->nx * h->ny));
+        h->band_x0 = std::min(h->band_x0, c % h->nx); h->band_x1 = std::max(h->band_x1, c % h->nx);
+        h->band_y0 = std::min(h->band_y0, y); h->band_y1 = std::max(h->band_y1, y);
+        h->band_z0 = std::min(h->band_z0, z); h->band_z1 = std::max(h->band_z1, z);
+    }
     h->ntiles = ntiles;
     h->nocc = (long long)obi.size();
     h->order = ord;

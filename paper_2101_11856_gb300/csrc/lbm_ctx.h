@@ -118,8 +118,17 @@ struct lbm_ctx {
     // with no band node in the strips: ib_overlap): ib_in = the step's inputs are ready, ib_done =
     // band forces written; made on first use
     bool ib_overlap = false;
+    // rows (y, z) holding band nodes of a static solid: y in [band_y0, band_y1], z in [band_z0,
+    // band_z1] (the adjoint's backward step runs the other rows beside its IB chain)
+    int band_y0 = 0, band_y1 = -1, band_z0 = 0, band_z1 = -1;
+    int band_x0 = 0, band_x1 = -1;   // x range of the band nodes
     cudaStream_t ibs = nullptr;
     cudaEvent_t ib_in = nullptr, ib_done = nullptr;
+    // per-block FP64 sums of the next step's penalty forces, written by that step right after its
+    // IB stage on the IB stage's stream (component k of block b at fsum[k * fsum_stride + b]);
+    // nullptr: none.  Consumed by the step.
+    double *fsum = nullptr;
+    long long fsum_stride = 0;
 
     std::string err;
 };
@@ -417,6 +426,8 @@ inline void free_solid(lbm_ctx *h) {
     h->ib_overlap = false;
     h->posed_tau = -1;
     h->S = h->nband = h->ntiles = 0;
+    h->band_y0 = 0; h->band_y1 = -1; h->band_z0 = 0; h->band_z1 = -1;
+    h->band_x0 = 0; h->band_x1 = -1;
     h->mask_w0 = 0;
     h->mask_w1 = -1;
     h->order.clear();
