@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--no-models", action="store_true", help="skip the BGK / raw-MRT comparison runs")
     ap.add_argument("--no-tracers", action="store_true", help="skip the smoke-tracer run")
     ap.add_argument("--no-moving", action="store_true", help="skip the rotating-torus run")
+    ap.add_argument("--pair-kernel", default="pairs", choices=["pairs", "tma"],
+                    help="16-bit storage main range: node pairs loading their own values (default) or fed by tensor copies")
     ap.add_argument("--tracers", type=int, default=4_000_000, help="smoke tracers of the tracer run")
     ap.add_argument("--adjoint-only", action="store_true", help="time only the adjoint workload")
     ap.add_argument("--adjoint-steps", type=int, default=200, help="steps of the adjoint workload")
@@ -517,6 +519,7 @@ def main():
     def make(storage, collision="acm"):
         s = Solver(nx, ny, nz, d["nu"], storage=storage, faces=d["faces"], u_in=d["u_in"], noise=d["noise"], seed=2101,
                    collision=collision)
+        s.set_pair_kernel(args.pair_kernel == "tma")
         s.set_state(rho0, u0)
         s.set_solids(X, A)
         return s

@@ -327,8 +327,12 @@ int lbm_set_inflow(lbm_ctx *h, const double coef[16]);
  * the threads that collide the node pairs from there; every wait for a copy is bounded (about a
  * second of SM clocks), and a wait that runs out makes the next lbm_synchronize or lbm_check return
  * LBM_ETIMEOUT.  Both give bit-identical results (the same values in the same FP32 arithmetic); on
- * GB300 the first is faster (the second keeps 4 warps per CTA in step with its tiles).  Takes
- * effect from the next step.  Errors: LBM_EINVAL for NULL h. */
+ * GB300 the first is faster (the second keeps 4 warps per CTA in step with its tiles).  bulk = 2
+ * is a self-test of the bounded wait: the second kernel with every barrier waiting for 16 bytes
+ * that no copy delivers, so every wait runs out (about a second), no tile is updated and the next
+ * lbm_synchronize or lbm_check returns LBM_ETIMEOUT; the state is invalid afterwards (call
+ * lbm_set_state or lbm_load).  Takes effect from the next step.  Errors: LBM_EINVAL for NULL h or
+ * bulk outside 0..2. */
 int lbm_set_pair_kernel(lbm_ctx *h, int bulk);
 
 /* Number of band nodes (nodes within the 2x2x2 stencil of a sample) of the solid. */

@@ -616,7 +616,8 @@ long long lbm_time(const lbm_ctx *h) { return h ? h->t : -1; }
 
 int lbm_set_pair_kernel(lbm_ctx *h, int bulk) {
     if (!h) return fail(nullptr, LBM_EINVAL, "null context");
-    h->pair_bulk = bulk != 0;
+    if (bulk < 0 || bulk > 2) return fail(h, LBM_EINVAL, "lbm_set_pair_kernel takes 0, 1 or 2");
+    h->pair_bulk = bulk;
     return LBM_OK;
 }
 

@@ -90,7 +90,7 @@ struct lbm_ctx {
     int *wait_err = nullptr;
     // 16-bit storage: the main range in the tensor-copy fed kernel (lbm_set_pair_kernel; off by
     // default: measured slower than the register-fed pair kernel on GB300)
-    bool pair_bulk = false;
+    int pair_bulk = 0;
 
     // profiling
     bool prof = false;
@@ -265,7 +265,7 @@ inline lbm::StepParams make_params(const lbm_ctx *h, long long t) {
     P.bandF = h->bandF;
     P.nband = h->nband;
     P.band_count = h->band_count_dev;
-    P.pair_bulk = h->pair_bulk ? 1 : 0;
+    P.pair_bulk = h->pair_bulk;
     P.err = h->wait_err;
     return P;
 }

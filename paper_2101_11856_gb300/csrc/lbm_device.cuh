@@ -111,7 +111,8 @@ struct StepParams {
     int inner_rows;              // 1: the step kernels skip the rows on a y/z face (run by the
                                  // free-slip kernels of the same step)
     int pair_bulk;               // 16-bit storage, node pairs: 1 = the tensor-copy fed main kernel
-                                 // (k_step_pair_tma, nx % 8 == 0), 0 = k_step_pair
+                                 // (k_step_pair_tma, nx % 8 == 0), 0 = k_step_pair, 2 = the former's
+                                 // wait-limit self-test
     int *err;                    // device flag set by a kernel whose bounded wait ran out
 };
 

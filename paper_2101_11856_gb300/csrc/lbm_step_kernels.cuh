@@ -228,7 +228,9 @@ cudaError_t launch_step_tt(const StepParams &P, int part, cudaStream_t st) {
                 const long long tiles = tma_tiles(g, P.inner_rows).count;
                 if (tiles > 0) {
                     const unsigned grid = (unsigned)(tiles < grid_max ? tiles : grid_max);
-                    k_step_pair_tma<St, NB, BAND, VOUT><<<grid, TMA_THREADS, TMA_SMEM, st>>>(m27, m3, P, P.err);
+                    // pair_bulk 2: the wait-limit self-test (every barrier waits for 16 bytes no copy delivers)
+                    k_step_pair_tma<St, NB, BAND, VOUT><<<grid, TMA_THREADS, TMA_SMEM, st>>>(m27, m3, P, P.err,
+                                                                                          P.pair_bulk == 2 ? 16 : 0);
                 }
             } else if (pair_grid(g)) {
                 // one-warp blocks: at 94-96 registers a 64-thread block leaves part of the SM's

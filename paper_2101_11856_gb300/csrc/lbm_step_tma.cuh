@@ -99,12 +99,14 @@ __device__ __forceinline__ void tma_tile(const Geometry &g, const TmaTiles &T, l
 // odd steps, for each (c_y, c_z) row j, planes 24 - 3j .. 26 - 3j (the opposite directions of
 // d = 3j + 2 .. 3j) of the source row into segments 3j .. 3j + 2, or the node's own planes
 // 3j .. 3j + 2 when the source row lies across a no-slip face (bounce-back reads the own slot).
+// tx_extra: bytes the barrier waits for beyond the copies (0; 16 in the wait-limit self-test,
+// where no tile's data ever counts as complete)
 template <bool NB>
 __device__ __forceinline__ void tma_issue(const CUtensorMap *m27, const CUtensorMap *m3, const Geometry &g,
-                                          const TmaTiles &T, long long k, uint32_t buf, uint32_t bar) {
+                                          const TmaTiles &T, long long k, uint32_t buf, uint32_t bar, int tx_extra) {
     int y, z, x0, wt;
     tma_tile(g, T, k, y, z, x0, wt);
-    mbar_expect_tx(bar, (uint32_t)TMA_STAGE_BYTES);
+    mbar_expect_tx(bar, (uint32_t)(TMA_STAGE_BYTES + tx_extra));
     if constexpr (!NB) {
         tma_load4(buf, m27, x0 - 8, y, z, 0, bar);
     } else {
@@ -130,7 +132,7 @@ __device__ __forceinline__ void tma_issue(const CUtensorMap *m27, const CUtensor
 template <typename St, bool NB, bool BAND, bool VOUT>
 __global__ void __launch_bounds__(TMA_THREADS, 5) k_step_pair_tma(const __grid_constant__ CUtensorMap m27,
                                                                   const __grid_constant__ CUtensorMap m3, StepParams P,
-                                                                  int *err) {
+                                                                  int *err, int tx_extra) {
     extern __shared__ unsigned char tma_smem_raw[];
     // 128-byte aligned stages (the copies' destinations), then the barriers
     const uint32_t base = (smem_addr(tma_smem_raw) + 127u) & ~127u;
@@ -149,7 +151,8 @@ __global__ void __launch_bounds__(TMA_THREADS, 5) k_step_pair_tma(const __grid_c
     if (tid == 0)
         for (int s = 0; s < TMA_STAGES; ++s) {
             const long long k = blockIdx.x + (long long)s * gridDim.x;
-            if (k < T.count) tma_issue<NB>(&m27, &m3, P.g, T, k, base + (uint32_t)(s * TMA_STAGE_BYTES), bars + 8u * s);
+            if (k < T.count)
+                tma_issue<NB>(&m27, &m3, P.g, T, k, base + (uint32_t)(s * TMA_STAGE_BYTES), bars + 8u * s, tx_extra);
         }
     for (long long i = 0;; ++i) {
         const long long k = blockIdx.x + i * gridDim.x;
@@ -237,7 +240,7 @@ __global__ void __launch_bounds__(TMA_THREADS, 5) k_step_pair_tma(const __grid_c
             const long long kn = k + (long long)TMA_STAGES * gridDim.x;
             if (kn < T.count) {
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                tma_issue<NB>(&m27, &m3, P.g, T, kn, base + (uint32_t)(s * TMA_STAGE_BYTES), bars + 8u * s);
+                tma_issue<NB>(&m27, &m3, P.g, T, kn, base + (uint32_t)(s * TMA_STAGE_BYTES), bars + 8u * s, tx_extra);
             }
         }
     }

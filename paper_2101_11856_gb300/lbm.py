@@ -281,7 +281,8 @@ def lbm_band_size(h):
 
 
 def lbm_set_pair_kernel(h, bulk):
-    _check(library().lbm_set_pair_kernel(h, 1 if bulk else 0), h)
+    """bulk: False / 0 (pair kernel), True / 1 (tensor-copy fed kernel), 2 (its wait-limit self-test)."""
+    _check(library().lbm_set_pair_kernel(h, int(bulk)), h)
 
 
 def lbm_solid_count(h):

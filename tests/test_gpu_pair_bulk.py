@@ -102,3 +102,25 @@ def test_bulk_wait_flag_clear():
     s.synchronize(30.0)
     from paper_2101_11856_gb300 import lbm
     assert lbm.lbm_check(s.h) == lbm.LBM_OK
+
+
+def test_bulk_wait_limit_expires():
+    """The bounded wait of the tensor-copy kernel runs out (self-test mode: every barrier waits for
+    16 bytes no copy delivers): LBM_ETIMEOUT reaches the host, the kernel ends by itself, and the
+    context keeps working once a state is set again."""
+    from paper_2101_11856_gb300 import lbm
+    dims = (64, 6, 5)
+    s = _run(True, dims, ("periodic",) * 6, "f16", ())
+    s.set_pair_kernel(2)
+    s.step(1)
+    with pytest.raises(lbm.LBMError) as e:
+        s.synchronize(60.0)
+    assert e.value.code == lbm.LBM_ETIMEOUT
+    assert lbm.lbm_check(s.h) == lbm.LBM_OK   # the flag was reported once and cleared
+    s.set_pair_kernel(1)
+    rho, u = scenes.uniform_flow(*dims, (0.04, 0.0, 0.0))
+    s.set_state(rho, u)
+    s.step(3)
+    s.synchronize(60.0)
+    ref = _run(False, dims, ("periodic",) * 6, "f16", (3,))
+    _same(s, ref)
