@@ -117,8 +117,11 @@ int lbm_set_solids(lbm_ctx *h, const float *samples, long long count,
  * with forcing, domain faces), asynchronously on the context's stream.  Each step is one
  * fused stream+collide kernel over the nodes 16 <= x < nx-16, one over the two 16-node
  * edge strips of every row (the inlet/outlet/x-periodic rules), and three small
- * immersed-boundary kernels when a solid is installed (plus the re-pose of a moving solid
- * and the tracer advection when those are set).  On a grid with a free-slip face the rows
+ * immersed-boundary kernels when a solid is installed: the band moments, then for a static
+ * solid the interpolation and penalty per occupied base cell with each cell's spreading sums
+ * and the gather of those sums per band node, for a moving one the interpolation per sample and
+ * the spreading per band node (plus the re-pose of a moving solid and the tracer advection
+ * when those are set).  On a grid with a free-slip face the rows
  * on a y or z face run in two more kernels (strips and main range) that carry the mirror
  * rule, and the first two skip them.
  * Errors: LBM_ESTATE before lbm_set_state, LBM_ECUDA. */
