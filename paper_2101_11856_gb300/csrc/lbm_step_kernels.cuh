@@ -5,6 +5,8 @@
 // parallel.
 #pragma once
 
+#include <type_traits>
+
 #include "lbm_models.cuh"
 #include "lbm_step.cuh"
 #include "lbm_step_tma.cuh"
@@ -100,8 +102,12 @@ __global__ void __launch_bounds__(STEP_BX) k_step_main(StepParams P) {
 // (x, x + 1), x = XEDGE + 2 i, the packed FP32 collision (collide_v<F2>: bit for bit the same
 // arithmetic as one node at a time) and 32-bit accesses for both nodes wherever the AA addressing
 // keeps the pair aligned (load_pair / store_pair).  Rows as k_step_main without FS.
+// FP16: at most 80 registers (24 resident one-warp blocks per SM instead of 21 at 94-96, a few
+// spilled values); BF16: at most 96 (its conversions need the registers; with no bound at all the
+// compiler takes 140-160 and halves the resident warps)
+template <typename St> constexpr int pair_min_blocks() { return std::is_same<St, __half>::value ? 12 : 10; }
 template <typename St, bool NB, bool BAND, bool VOUT>
-__global__ void __launch_bounds__(STEP_BX) k_step_pair(StepParams P) {
+__global__ void __launch_bounds__(STEP_BX, pair_min_blocks<St>()) k_step_pair(StepParams P) {
     const int y = blockIdx.y, z = blockIdx.z;
     const bool inner = y >= 1 && y <= P.g.ny - 2 && z >= 1 && z <= P.g.nz - 2;   // uniform per block
     if (P.inner_rows && !inner) return;
