@@ -35,7 +35,7 @@ PAPER_MLUPS = 1200 * 250 * 840 / 1.21 / 1e6                # Table 3, Fig. 1 sce
 # DRAM bytes per cell of the main-range kernel from one ncu capture of the current kernel, mean of
 # the two AA parities: k_step_main for FP32 (profiles/k_step_main_box_city_480x100x336.md),
 # k_step_pair for FP16 (profiles/k_step_pair_box_city_480x100x336.md); absent once a kernel changes
-TRAFFIC_PER_CELL = {"f32": 221.3, "f16": 109.4}
+TRAFFIC_PER_CELL = {"f32": 221.3, "f16": 110.3}
 
 
 def parse():
