@@ -666,6 +666,11 @@ extern "C" int lbm_adjoint(lbm_ctx *h, int n, int K, const lbm_loss *loss, doubl
     std::vector<char *> ckpt(nck, nullptr);
     for (int i = 0; i + nstored < nck; ++i) if ((rc = B.get(h, &ckpt[i], state_bytes))) return rc;
     IBArrays ib(h);
+    // the forward pass asks each step for its drag sums (h->fsum); no request outlives this call
+    struct FsumClear {
+        lbm_ctx *h;
+        ~FsumClear() { h->fsum = nullptr; }
+    } fsum_clear{h};
     auto point_slot = [&](const SegSet &q, long long j) {
         ib.point(q.rho + j * nb, q.u + j * 3 * nb, q.g + j * 3 * S, q.F + j * 3 * nb);
     };
@@ -721,10 +726,7 @@ extern "C" int lbm_adjoint(lbm_ctx *h, int n, int K, const lbm_loss *loss, doubl
                 CK(cudaMemcpyAsync(ckpt[sgi], h->f, pop_bytes, cudaMemcpyDeviceToDevice, st));
                 if (out_bytes) CK(cudaMemcpyAsync(ckpt[sgi] + pop_bytes, h->outlet, out_bytes, cudaMemcpyDeviceToDevice, st));
             }
-            if ((rc = lbm_step(h, 1))) {
-                h->fsum = nullptr;
-                return rc;
-            }
+            if ((rc = lbm_step(h, 1))) return rc;
         } else {
             SegSet &q = set_of(sgi);
             if (i == first_kept * K) {   // the context's state enters the first kept segment
@@ -738,10 +740,7 @@ extern "C" int lbm_adjoint(lbm_ctx *h, int n, int K, const lbm_loss *loss, doubl
             }
             // the segment's last step writes the next segment's first state, or the context's
             char *dst = inner ? q.f[k + 1] : (sgi + 1 < nck ? set_of(sgi + 1).f[0] : nullptr);
-            if ((rc = adj_forward_step(h, q.f[k], dst))) {
-                h->fsum = nullptr;
-                return rc;
-            }
+            if ((rc = adj_forward_step(h, q.f[k], dst))) return rc;
         }
     }
     if (S > 0) {
