@@ -640,9 +640,10 @@ extern "C" int lbm_adjoint(lbm_ctx *h, int n, int K, const lbm_loss *loss, doubl
     float *cellS_b = nullptr;
     if (h->nocc > 0 && (rc = B.get(h, &cellS_b, (size_t)24 * h->nocc))) return rc;
     // Segment sets: the states f_{t0 + k} of a segment and the IB values of its recomputed steps
-    // (slot j: the step from state t0 + j; the last step of a segment keeps none).  With two sets
-    // the recompute of segment s - 1 runs on a second stream beside the backward pass of segment
-    // s; a second set that does not fit in device memory leaves one, and the two alternate.
+    // (slot j: the step from state t0 + j; the last step of a segment keeps none).  With two or
+    // more sets the recompute of segment s - 1 runs on a second stream beside the backward pass of
+    // segment s, into the set of the segment nset - 1 after s; a second set that does not fit in
+    // device memory leaves one, and the recompute and the backward pass alternate.
     struct SegSet {
         std::vector<char *> f;
         float *rho = nullptr, *u = nullptr, *g = nullptr, *F = nullptr;
@@ -657,9 +658,33 @@ extern "C" int lbm_adjoint(lbm_ctx *h, int n, int K, const lbm_loss *loss, doubl
             return rc;
         return LBM_OK;
     };
-    SegSet sets[2];
+    // Up to kMaxSets sets: the forward pass keeps the last nset segments in them (no recompute);
+    // an extra set replaces a checkpoint, so a set is added only while the device memory free now
+    // (plus this context's unclaimed workspace) holds it with the checkpoints still needed and a
+    // margin; a set that does not fit after all ends the list.
+    constexpr int kMaxSets = 4;
+    SegSet sets[kMaxSets];
     if ((rc = get_set(sets[0], false))) return rc;
-    const int nset = nck > 1 && get_set(sets[1], true) == LBM_OK ? 2 : 1;
+    int want = 1;
+    {
+        size_t free_b = 0, total_b = 0;
+        if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+            cudaGetLastError();
+            free_b = total_b = 0;
+        }
+        size_t held = 0;   // workspace slots this call has not claimed yet
+        for (size_t i = B.next; i < h->adj_ws.size(); ++i) held += h->adj_ws[i].second;
+        const size_t avail = free_b + held, margin = ((size_t)1 << 30) + total_b / 20;
+        const size_t set_bytes = (size_t)K * state_bytes + (S > 0 ? nslot * (7 * (size_t)nb + 3 * (size_t)S) * 4 : 0);
+        for (int m = 2; m <= std::min(kMaxSets, nck); ++m) {
+            // sets 1..m-1 and the checkpoints of the other nck - m segments (set 0 is held)
+            const size_t need = (size_t)(m - 1) * set_bytes + (size_t)(nck - m) * state_bytes;
+            if (need + margin <= avail) want = m;
+        }
+        if (nck > 1 && want < 2) want = 2;   // the second set is always tried (the recompute beside the backward)
+    }
+    int nset = 1;
+    while (nset < want && get_set(sets[nset], true) == LBM_OK) ++nset;
     // checkpoints of the segments whose states the forward pass does not keep in a set (all but
     // the last nset)
     const int nstored = nset;
@@ -683,23 +708,29 @@ extern "C" int lbm_adjoint(lbm_ctx *h, int n, int K, const lbm_loss *loss, doubl
     // events between them and the context's stream
     struct SideStreams {
         cudaStream_t s = nullptr, b = nullptr;
-        cudaEvent_t done[2] = {nullptr, nullptr}, free_[2] = {nullptr, nullptr}, fork = nullptr, join = nullptr;
+        cudaEvent_t done[kMaxSets] = {}, free_[kMaxSets] = {}, fork = nullptr, join = nullptr;
         ~SideStreams() {
             for (cudaStream_t q : {s, b})
                 if (q) cudaStreamSynchronize(q);
-            for (cudaEvent_t e : {done[0], done[1], free_[0], free_[1], fork, join})
+            for (int k = 0; k < kMaxSets; ++k)
+                for (cudaEvent_t e : {done[k], free_[k]})
+                    if (e) cudaEventDestroy(e);
+            for (cudaEvent_t e : {fork, join})
                 if (e) cudaEventDestroy(e);
             for (cudaStream_t q : {s, b})
                 if (q) cudaStreamDestroy(q);
         }
     } side;
-    if (nset == 2) {
+    if (nset >= 2) {
         int lo = 0, hi = 0;
         CK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
         CK(cudaStreamCreateWithPriority(&side.s, cudaStreamNonBlocking, lo));
         CK(cudaStreamCreateWithPriority(&side.b, cudaStreamNonBlocking, kBackwardPriority ? hi : lo));
-        for (cudaEvent_t *e : {&side.done[0], &side.done[1], &side.free_[0], &side.free_[1], &side.fork, &side.join})
-            CK(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+        for (int k = 0; k < nset; ++k) {
+            CK(cudaEventCreateWithFlags(&side.done[k], cudaEventDisableTiming));
+            CK(cudaEventCreateWithFlags(&side.free_[k], cudaEventDisableTiming));
+        }
+        for (cudaEvent_t *e : {&side.fork, &side.join}) CK(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
     }
     CK(cudaMemsetAsync(s_inlet, 0, nyz * sizeof(double), st));
     CK(cudaMemsetAsync(acc, 0, 8 * sizeof(double), st));
@@ -824,8 +855,8 @@ extern "C" int lbm_adjoint(lbm_ctx *h, int n, int K, const lbm_loss *loss, doubl
     float *lam_cur = lamA, *lam_prev = lamB;
     const float drag_w = (float)(-loss->w_drag / n);
     cudaStream_t bs = st;   // stream of the backward pass
-    if (nset == 2) {
-        CK(cudaEventRecord(side.free_[1], st));   // checkpoints written, set 1 unused
+    if (nset >= 2) {
+        for (int k = 1; k < nset; ++k) CK(cudaEventRecord(side.free_[k], st));   // checkpoints written
         CK(cudaEventRecord(side.fork, st));
         CK(cudaStreamWaitEvent(side.b, side.fork, 0));
         bs = side.b;
@@ -835,10 +866,11 @@ extern "C" int lbm_adjoint(lbm_ctx *h, int n, int K, const lbm_loss *loss, doubl
         const int len = (int)std::min<long long>(K, t_start + n - t0);
         const int cur = (nck - 1 - sgi) % nset;
         const SegSet &q = sets[cur];
-        if (nset == 2) {
+        if (nset >= 2) {
             if (sgi < first_kept) CK(cudaStreamWaitEvent(bs, side.done[cur], 0));
             if (sgi >= 1 && sgi - 1 < first_kept) {
-                const int nxt = cur ^ 1;
+                // the set of segment sgi - 1 last held segment sgi + nset - 1, whose backward is done
+                const int nxt = (cur + 1) % nset;
                 CK(cudaStreamWaitEvent(side.s, side.free_[nxt], 0));
                 if ((rc = recompute(sgi - 1, sets[nxt], side.s))) return rc;
                 CK(cudaEventRecord(side.done[nxt], side.s));
@@ -919,9 +951,9 @@ extern "C" int lbm_adjoint(lbm_ctx *h, int n, int K, const lbm_loss *loss, doubl
             }
             std::swap(lam_cur, lam_prev);
         }
-        if (nset == 2) CK(cudaEventRecord(side.free_[cur], bs));
+        if (nset >= 2) CK(cudaEventRecord(side.free_[cur], bs));
     }
-    if (nset == 2) {
+    if (nset >= 2) {
         CK(cudaEventRecord(side.join, bs));
         CK(cudaStreamWaitEvent(st, side.join, 0));
     }

@@ -103,13 +103,14 @@ def test_adjoint_advances_state_like_forward_steps():
     assert np.allclose(a.reductions()[2], b.reductions()[2], rtol=0, atol=0)
 
 
-@pytest.mark.parametrize("K", [4, 2])
+@pytest.mark.parametrize("K", [4, 2, 1])
 def test_long_rows_main_and_edge_kernels(K):
     """nx = 70: the backward main kernel takes 1 <= x <= 68 in two 64-node chunks per row (the
     lanes past nx - 2 idle) and the x-face kernel the two end nodes, against the oracle; K = 2
-    recomputes the first segment on the second stream while the last two come from the forward
-    pass.  The sphere lies in the main range, the kinetic-energy slab next to the inlet (so that
-    the inflow coefficients reach the loss within the 6 steps)."""
+    keeps all three segments from the forward pass (up to four segment sets fit), K = 1 keeps the
+    last four and recomputes the first two on the second stream.  The sphere lies in the main
+    range, the kinetic-energy slab next to the inlet (so that the inflow coefficients reach the
+    loss within the 6 steps)."""
     nx, ny, nz = 70, 6, 5
     faces = ("inlet", "outlet", "noslip", "noslip", "periodic", "periodic")
     X, A = scenes.fibonacci_sphere((37.4, 2.6, 2.3), 1.6, 30)
