@@ -131,3 +131,10 @@ def test_static_force_sum_binding_validates_before_the_call():
             lbm_sum_forces_static(*args)
     with pytest.raises(ValueError):                 # host tensors of the right shapes
         lbm_sum_forces_static(g, out)
+
+
+def test_context_setters_reject_a_null_context_without_the_gpu(lib):
+    """The per-context switches validate their context before anything else."""
+    assert lib.lbm_set_pair_kernel(None, 1) == -1     # LBM_EINVAL
+    assert lib.lbm_set_pair_kernel(None, 0) == -1
+    assert lib.lbm_set_inflow(None, None) == -1
