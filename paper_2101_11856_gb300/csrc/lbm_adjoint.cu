@@ -572,11 +572,6 @@ struct AdjBuffers {
     }
 };
 
-// a block of rows (y, z) of the main backward kernel: y0 <= y < y0 + ny, z0 <= z < z0 + nz
-struct RowBox {
-    int y0, ny, z0, nz;
-};
-
 // the main backward kernel over the rows of box r (nothing for an empty box), then (xface) the
 // x-face kernel
 template <typename St, bool NB, bool BAND>
@@ -831,12 +826,7 @@ extern "C" int lbm_adjoint(lbm_ctx *h, int n, int K, const lbm_loss *loss, doubl
         }
     } bfree;
     if (S > 0 && h->band_y1 >= h->band_y0) {
-        const int y0 = h->band_y0, y1 = h->band_y1, z0 = h->band_z0, z1 = h->band_z1;
-        band_box = RowBox{y0, y1 - y0 + 1, z0, z1 - z0 + 1};
-        if (y0 > 0) free_box[nfree++] = RowBox{0, y0, 0, h->nz};
-        if (y1 < h->ny - 1) free_box[nfree++] = RowBox{y1 + 1, h->ny - 1 - y1, 0, h->nz};
-        if (z0 > 0) free_box[nfree++] = RowBox{y0, y1 - y0 + 1, 0, z0};
-        if (z1 < h->nz - 1) free_box[nfree++] = RowBox{y0, y1 - y0 + 1, z1 + 1, h->nz - 1 - z1};
+        nfree = band_row_boxes(h->ny, h->nz, h->band_y0, h->band_y1, h->band_z0, h->band_z1, band_box, free_box);
         if (nfree > 0) {
             int lo = 0, hi = 0;
             CK(cudaDeviceGetStreamPriorityRange(&lo, &hi));

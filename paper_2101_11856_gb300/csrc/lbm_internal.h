@@ -48,6 +48,23 @@ __host__ __device__ inline void face_row(const Geometry &g, long long r, int &y,
     y = (r % w) ? g.ny - 1 : 0;
 }
 __host__ __device__ inline int edge_per_row(const Geometry &g) { return has_interior(g) ? 2 * XEDGE : g.nx; }
+// A block of rows (y, z): y0 <= y < y0 + ny, z0 <= z < z0 + nz.  band_row_boxes splits the rows of
+// a gny x gnz grid into the box [by0, by1] x [bz0, bz1] holding the band's rows and up to four
+// boxes around it (rows y < by0 and y > by1 of every z, then the rows of the band's y range with
+// z < bz0 and z > bz1), each row in exactly one box; returns the number of boxes around the band.
+struct RowBox {
+    int y0, ny, z0, nz;
+};
+__host__ __device__ inline int band_row_boxes(int gny, int gnz, int by0, int by1, int bz0, int bz1, RowBox &band,
+                                              RowBox (&around)[4]) {
+    band = RowBox{by0, by1 - by0 + 1, bz0, bz1 - bz0 + 1};
+    int n = 0;
+    if (by0 > 0) around[n++] = RowBox{0, by0, 0, gnz};
+    if (by1 < gny - 1) around[n++] = RowBox{by1 + 1, gny - 1 - by1, 0, gnz};
+    if (bz0 > 0) around[n++] = RowBox{by0, by1 - by0 + 1, 0, bz0};
+    if (bz1 < gnz - 1) around[n++] = RowBox{by0, by1 - by0 + 1, bz1 + 1, gnz - 1 - bz1};
+    return n;
+}
 cudaError_t launch_init(int storage, const StepParams &P, const float *rho, const float *u, cudaStream_t st);
 long long macro_blocks(const StepParams &P);
 // rows of the k_macro partial sums: mass, momentum x/y/z, slab kinetic energy

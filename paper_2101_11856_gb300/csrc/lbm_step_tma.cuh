@@ -83,7 +83,7 @@ __host__ __device__ inline TmaTiles tma_tiles(const Geometry &g, int inner_rows)
 }
 
 // tile k: row (y, z), first node x0, nodes wt (a multiple of 8: nx % 8 == 0)
-__device__ __forceinline__ void tma_tile(const Geometry &g, const TmaTiles &T, long long k, int &y, int &z, int &x0, int &wt) {
+__host__ __device__ inline void tma_tile(const Geometry &g, const TmaTiles &T, long long k, int &y, int &z, int &x0, int &wt) {
     const int c = (int)(k % T.per_row);
     const long long r = k / T.per_row;
     y = T.y0 + (int)(r % T.rows_y);
