@@ -21,6 +21,10 @@ float64 with plain PyTorch CPU tensor operations:
   collide) and the diagnostics (macroscopic fields, mass/momentum/drag).
 * ``adjoint``    -- the loss of the adjoint problem and its exact gradients, obtained
   by reverse-mode differentiation of the FP64 forward step.
+* ``motion``     -- prescribed rigid motion of a solid (rotation and translation of its
+  samples, boundary velocity), for the moving-solid steps.
+* ``tracers``    -- smoke tracers: midpoint-rule advection in the interpolated velocity,
+  re-injection, and the cloud-in-cell density projection.
 
 Parity status: every function is pinned by tests in ``tests/test_oracle_*.py`` except
 the *adaptive* high-order relaxation rates of ACM-MRT, whose definition lives in
