@@ -925,7 +925,7 @@ extern "C" int lbm_adjoint(lbm_ctx *h, int n, int K, const lbm_loss *loss, doubl
             }
             if (nfree > 0) {
                 // the band's rows read the IB chain's terms; the other rows run beside it (launched
-                // below on the band-free stream, which joins before the next step reads lambda)
+                // above on the band-free streams, which join before the next step reads lambda)
                 CK(with_storage(h->storage, [&](auto tag) {
                     using St = decltype(tag);
                     return launch_adj_step<St>(P, A, nbp, true, band_box, !bfree.xs, bs);
